@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Throughput of the fast SE(2) convolution (arXiv 2504.05149, Algorithm 3 at
+N = L) on GB300: SE(2) convolutions per second at N = 256, M = 64, FP32.
+
+Default arm: a batch of independent problems per GPU (seeded synthetic f1 =
+16 bumps; its own radial kernel per problem, whose coefficient spectrum is
+computed once by se2_coeffs before timing), one step = one se2_convolve call
+over the batch.  Inputs (f, coefficients, out: 808 MB per step) are larger
+than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(numpy FFT route) on the host instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_DEF, M_DEF, B_DEF = 256, 64, 16
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=B_DEF)
+    ap.add_argument("--N", type=int, default=N_DEF)
+    ap.add_argument("--M", type=int, default=M_DEF)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_inputs(N, M, B, rank):
+    """Seeded synthetic batch: f1 (16 bumps) and one kernel per problem."""
+    import synth
+    Fs, Ps = [], []
+    for b in range(B):
+        prob = synth.make_problem(2, 100 * rank + b, N, M, n_bumps=16, n_kernels=1)
+        Fs.append(synth.sample_bumps(N, M, prob.bumps).astype(np.float32))
+        Ps.append(synth.sample_kernel(N, M, prob.kernels[0]).astype(np.float32))
+    return np.stack(Fs), np.stack(Ps)
+
+
+def peaks():
+    try:
+        with open(MEASURED) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             + ",".join("clocks_event_reasons." + r for r in REASONS))
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 6 + len(REASONS):
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [p for (t, p) in self.rows if t0 <= t <= t1] or [p for (_, p) in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(p[2]) for p in rows if p[2].replace(".", "").isdigit()]
+        mx = [float(p[3]) for p in rows if p[3].replace(".", "").isdigit()]
+        reasons = set()
+        for p in rows:
+            for i, r in enumerate(REASONS):
+                if p[6 + i].lower().startswith("active"):
+                    reasons.add(r)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(N, M, seconds=12.0):
+    """The FP64 oracle (numpy FFT route, as it stands) on host cores: single
+    convolutions of the same workload with precomputed kernel spectra."""
+    from oracle import se2_oracle as O
+    import synth
+    prob = synth.make_problem(2, 0, N, M, n_bumps=16, n_kernels=1)
+    F = synth.sample_bumps(N, M, prob.bumps)
+    C = O.coeffs_full(synth.sample_kernel(N, M, prob.kernels[0]))
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        O.convolve_chain(F, None, coeffs=[C])
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= 64:
+            break
+    return {"value": n / el, "unit": "conv/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} single convolutions N={N} M={M} (numpy FFT route, FP64, precomputed kernel spectrum), {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import se2_oracle as O
+    import synth
+    N, M = args.N, args.M
+    prob = synth.make_problem(2, 0, N, M, n_bumps=16, n_kernels=1)
+    F = synth.sample_bumps(N, M, prob.bumps)
+    C = O.coeffs_full(synth.sample_kernel(N, M, prob.kernels[0]))
+    for _ in range(args.warmup):
+        O.convolve_chain(F, None, coeffs=[C])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.convolve_chain(F, None, coeffs=[C])
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {"metric": "SE(2) convolutions/s at N=256, M=64", "value": v, "unit": "conv/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"single SE(2) convolution N={N} M={M}, one problem per step (bounded sample)",
+                       "l2": "host"},
+            "cpu_baseline": {"value": v, "unit": "conv/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single convolutions, numpy FFT route, FP64"},
+            "e2e": {"value": v, "unit": "conv/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_2504_05149_gb300 as se2
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, M, B = args.N, args.M, args.batch
+    L = N * N * M
+
+    F, P = workload_inputs(N, M, B, rank)
+    plan = se2.Plan(N, M, batch=B, precision="f32", device=local)
+    f = torch.from_numpy(F).to(dev)
+    C, _ = se2.coeffs(plan, torch.from_numpy(P).to(dev))
+    out = torch.empty_like(f)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up, then ~0.5 s more untimed work so the clock sampler sees load
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(vis.split(",")[local].strip() if vis else local)
+    sampler.start()
+    for _ in range(args.warmup):
+        se2.convolve(plan, f, C, out=out)
+    barrier()
+    t_settle = time.time()
+    while time.time() - t_settle < 0.6:
+        se2.convolve(plan, f, C, out=out)
+        torch.cuda.synchronize(dev)
+
+    barrier()
+    t_wall0 = time.time()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        se2.convolve(plan, f, C, out=out)
+    e1.record(stream)
+    barrier()
+    t_wall1 = time.time()
+    ms = e0.elapsed_time(e1)
+    sampler.stop()
+    clocks = sampler.summary(t_settle, t_wall1)
+
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms = float(tmax.item())
+    ms_step = ms / args.steps
+    convs = B * args.steps * world
+    value = convs / (ms / 1e3)
+
+    # end to end through the public API: pinned host f -> device, convolve, device -> host out
+    hf = torch.from_numpy(F).pin_memory()
+    hout = torch.empty(F.shape, dtype=torch.float32).pin_memory()
+    df = torch.empty_like(f)
+    for _ in range(2):
+        df.copy_(hf, non_blocking=True)
+        se2.convolve(plan, df, C, out=out)
+        hout.copy_(out, non_blocking=True)
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    ke = max(3, min(args.steps, 10))
+    e2.record(stream)
+    for _ in range(ke):
+        df.copy_(hf, non_blocking=True)
+        se2.convolve(plan, df, C, out=out)
+        hout.copy_(out, non_blocking=True)
+    e3.record(stream)
+    barrier()
+    me = torch.tensor([e2.elapsed_time(e3)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(me, op=dist.ReduceOp.MAX)
+    e2e_val = B * ke * world / (float(me.item()) / 1e3)
+    assert np.isfinite(hout.numpy()).all()
+
+    hbm, src = peaks()
+    alg_bytes = B * (4 * L + 4 * L + 8 * M * N * (N // 2 + 1))   # read f, write out, read half spectrum
+    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    chunks = math.ceil(B / plan_chunk(plan, N, M, B))
+    launches_per_step = chunks * 3
+
+    line = None
+    if rank == 0:
+        base = None if args.no_cpu_baseline or world > 1 else cpu_baseline(N, M)
+        line = {
+            "metric": "SE(2) convolutions/s at N=256, M=64 (FP32) and fraction of HBM roofline",
+            "value": value, "unit": "conv/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"se2_convolve, batch of {B} independent problems per GPU, N={N}, M={M}, "
+                                   f"one radial kernel per problem (precomputed spectra), 16-bump f1",
+                       "global_batch": B * world, "grid": [M, N, N], "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB moved per step)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                         "scope": "whole se2_convolve step (all kernels)",
+                         "alg_bytes_per_conv": alg_bytes / B},
+            "cpu_baseline": base,
+            "e2e": {"value": e2e_val, "unit": "conv/s", "h2d_bytes_per_step": int(F.nbytes),
+                    "d2h_bytes_per_step": int(F.nbytes)},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def plan_chunk(plan, N, M, B):
+    """Problems per scratch pass (mirrors the library's choice: up to 1 GiB)."""
+    tp = ((N // 2 + 1) + 15) // 16 * 16
+    per = M * N * tp * 8
+    env = os.environ.get("SE2_MAX_CHUNK")
+    c = max(1, (1 << 30) // per)
+    if env and 1 <= int(env) < c:
+        c = int(env)
+    return min(c, B)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,137 @@
+/*
+ * se2.h -- C ABI of the GB300 (sm_103a) library for fast SE(2) convolutions
+ * on the coset space Z^2\SE(2) (arXiv 2504.05149).
+ *
+ * The operation.  For f on Z^2\SE(2) and a kernel rho radial in translations,
+ * the SE(2) convolution reduces to an abelian 3-D periodic convolution
+ * (Theorem f*gP, Section 5.1), and its convolutional finite Fourier series on
+ * the sampling grid Omega_L (Eq. OmL) is, at output grid N = L (Section 6.1,
+ * closed form below Eq. MatSKfgonG; Algorithm 3):
+ *
+ *     out = iDFT( W . DFT(F) . C ),      C = DFT(P) / |L|,
+ *
+ * with F, P the samples of f and rho, W(k) = (-1)^(k1+k2) (Eq. W), |L| = N*N*M,
+ * and DFT / iDFT as in Eqs. 3DFT / 3iDFT.  A chain of k kernels uses
+ * W^k . DFT(F) . C_1 ... C_k (Eq. MatSqKfgG; Algorithms 4 and 6).
+ *
+ * Layout (all row-major, x fastest):
+ *   real grid   [M][N][N]        = [theta_l][y_j][x_i], x_i = -1/2 + i/N,
+ *                                  y_j = -1/2 + j/N, theta_l = 2 pi l / M
+ *   spectrum    [M][N][N/2+1]    complex, interleaved (re, im); bins 0..N/2
+ *                                  along x (the rest is the Hermitian mirror),
+ *                                  all bins along y and theta.
+ *   A batch of B problems is B such arrays back to back.
+ *   Real type: double for SE2_F64, float for SE2_F32; complex = 2 of those.
+ *
+ * Sizes: N in {8, 16, ..., 512}, M in {2, 4, ..., 128} (powers of two), B >= 1.
+ *
+ * Ownership and streams.  The caller owns every data buffer (device memory,
+ * e.g. from PyTorch).  A plan owns only its twiddle tables and a scratch
+ * workspace, allocated in se2_plan_create; no call below allocates.  Every
+ * compute call is asynchronous on the caller's CUDA stream (`stream` is a
+ * cudaStream_t; NULL = legacy default stream).
+ *
+ * Errors.  Every call returns an se2_status and never aborts or traps.
+ * Argument errors are found on the host before anything is launched.
+ * se2_last_error() returns a thread-local description of the last failure.
+ */
+#ifndef SE2_H
+#define SE2_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct se2_plan_s* se2_plan_t;
+
+typedef enum {
+    SE2_OK = 0,
+    SE2_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, bad size, bad count */
+    SE2_ERR_UNSUPPORTED = 2,  /* valid but not implemented (size, precision)  */
+    SE2_ERR_OOM = 3,          /* plan allocation failed (nothing leaked)      */
+    SE2_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed         */
+    SE2_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up           */
+    SE2_ERR_NUMERIC = 6       /* reserved: non-finite result detected         */
+} se2_status;
+
+typedef enum {
+    SE2_F64 = 0,              /* double storage and arithmetic                */
+    SE2_F32 = 1               /* float storage and arithmetic, FP64 tables    */
+} se2_precision;
+
+/* Plan flags */
+#define SE2_SHARED_KERNEL 0x1u  /* one coefficient array serves the whole batch */
+
+/*
+ * se2_plan_create -- validate sizes, build FP64-accurate twiddle tables and
+ * allocate the scratch workspace for batches of up to `batch` problems.
+ *   plan   out: the new plan (NULL on failure)
+ *   N, M   grid sizes (see above); batch >= 1
+ *   device the CUDA device the plan and every buffer given to it live on
+ * Synchronous.  Returns SE2_ERR_OOM if device memory runs out.
+ */
+se2_status se2_plan_create(se2_plan_t* plan, int N, int M, int batch,
+                           se2_precision precision, unsigned flags, int device);
+
+/* Frees the plan's tables and workspace (synchronises the device first). */
+se2_status se2_plan_destroy(se2_plan_t plan);
+
+/* Bytes of device workspace the plan holds (tables + scratch). */
+size_t se2_plan_workspace_bytes(se2_plan_t plan);
+
+/*
+ * se2_coeffs -- scaled kernel spectra C = DFT(P) / |L| of n kernels
+ * (Section 4.1, Eq. FkLv: C is W times the finite Fourier coefficients of
+ * the kernel), for Algorithms 3, 4 and 6.
+ *   samples   device, [n][M][N][N] real: P sampled on Omega_L
+ *   n         number of kernels, >= 1 (processed in chunks of `batch`)
+ *   coeffs    device, [n][M][N][N/2+1] complex, written
+ *   log_scale device, [n] double, or NULL.  If non-NULL, coeffs are stored
+ *             divided by s = mean(|P|) (so |C| <= 1) and log_scale[i] = ln s;
+ *             s = 0 stores C unscaled and log_scale = 0.  Convolution calls
+ *             multiply the result back by exp(sum of the log scales) in FP64,
+ *             which keeps long chains inside the range of the real type.
+ */
+se2_status se2_coeffs(se2_plan_t plan, const void* samples, int n, void* coeffs,
+                      double* log_scale, void* stream);
+
+/*
+ * se2_convolve -- S_K[f, rho] on Omega_L for a batch (Algorithm 3 at N = L):
+ *   out_b = iDFT( W . DFT(F_b) . C_b ) * exp(log_scale_b)
+ *   f         device, [B][M][N][N] real, B <= plan batch
+ *   B         number of problems in this call
+ *   coeffs    device, [B][M][N][N/2+1] complex (from se2_coeffs), or one
+ *             [M][N][N/2+1] array for all problems with SE2_SHARED_KERNEL
+ *   log_scale device, [B] (or [1]) double, or NULL (= 0)
+ *   out       device, [B][M][N][N] real; may not alias f or coeffs
+ */
+se2_status se2_convolve(se2_plan_t plan, const void* f, int B, const void* coeffs,
+                        const double* log_scale, void* out, void* stream);
+
+/*
+ * se2_convolve_chain -- f * rho_1 * ... * rho_k (Eq. MatSqKfgG with the
+ * Hadamard power replaced by the product of k coefficient arrays; with k
+ * equal kernels this is Algorithm 4, and the result equals the last V_k of
+ * Algorithm 6):
+ *   out_b = iDFT( W^k . DFT(F_b) . C_1,b ... C_k,b ) * exp(sum_i log_scale_i,b)
+ *   coeffs     host array of k device pointers, each laid out as in se2_convolve
+ *   log_scales host array of k device pointers ([B] or [1] doubles), or NULL;
+ *              individual entries may be NULL
+ *   k          1 <= k <= 32
+ */
+se2_status se2_convolve_chain(se2_plan_t plan, const void* f, int B,
+                              const void* const* coeffs, const double* const* log_scales,
+                              int k, void* out, void* stream);
+
+/* Thread-local text of the last error (never NULL). */
+const char* se2_last_error(void);
+
+/* Library version string. */
+const char* se2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SE2_H */

@@ -1,0 +1,181 @@
+"""Fast SE(2) convolutions on Z^2\\SE(2) for GB300 -- Python binding.
+
+A thin ctypes layer over the C ABI of libse2.so (include/se2.h): it checks
+tensor shapes/dtypes/devices, passes raw device pointers and the current
+CUDA stream, and raises on any non-OK status.  Every step of the path runs in
+the library's CUDA kernels; PyTorch only provides device memory and streams.
+There is no CPU fallback: if the library is missing this module raises.
+
+The operation (arXiv 2504.05149, Algorithm 3 at output grid N = L):
+    out = iDFT( W . DFT(f) . C ),   C = DFT(P) / |L|
+for f, P sampled on the grid Omega_L ([M][N][N] = [theta][y][x]).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libse2.so")
+
+F64 = 0
+F32 = 1
+SHARED_KERNEL = 0x1
+
+_STATUS = {0: "SE2_OK", 1: "SE2_ERR_INVALID_ARG", 2: "SE2_ERR_UNSUPPORTED", 3: "SE2_ERR_OOM",
+           4: "SE2_ERR_CUDA", 5: "SE2_ERR_TIMEOUT", 6: "SE2_ERR_NUMERIC"}
+
+_lib = None
+
+
+class SE2Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libse2.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libse2.so not found at {path}; run paper_2504_05149_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.se2_plan_create.argtypes = [ctypes.POINTER(vp), ip, ip, ip, ip, ctypes.c_uint, ip]
+    lib.se2_plan_destroy.argtypes = [vp]
+    lib.se2_plan_workspace_bytes.argtypes = [vp]
+    lib.se2_plan_workspace_bytes.restype = ctypes.c_size_t
+    lib.se2_coeffs.argtypes = [vp, vp, ip, vp, vp, vp]
+    lib.se2_convolve.argtypes = [vp, vp, ip, vp, vp, vp, vp]
+    lib.se2_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp, vp]
+    lib.se2_last_error.restype = ctypes.c_char_p
+    lib.se2_version.restype = ctypes.c_char_p
+    for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_chain"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise SE2Error(status, load_library().se2_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Plan:
+    """Twiddle tables and scratch for batches of up to `batch` N x N x M grids."""
+
+    def __init__(self, N: int, M: int, batch: int = 1, precision: str = "f32", flags: int = 0,
+                 device: Optional[int] = None):
+        lib = load_library()
+        if precision not in ("f32", "f64"):
+            raise ValueError("precision must be 'f32' or 'f64'")
+        self.N, self.M, self.batch, self.flags = N, M, batch, flags
+        self.precision = precision
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.dtype = torch.float32 if precision == "f32" else torch.float64
+        self.cdtype = torch.complex64 if precision == "f32" else torch.complex128
+        h = ctypes.c_void_p()
+        _check(lib.se2_plan_create(ctypes.byref(h), N, M, batch, F32 if precision == "f32" else F64,
+                                   flags, self.device))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        return int(load_library().se2_plan_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().se2_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- shape helpers -------------------------------------------------------
+    def grid_shape(self, B: int):
+        return (B, self.M, self.N, self.N)
+
+    def spec_shape(self, B: int):
+        return (B, self.M, self.N, self.N // 2 + 1)
+
+    def _check_grid(self, t: torch.Tensor, name: str) -> int:
+        if t.dim() != 4 or tuple(t.shape[1:]) != (self.M, self.N, self.N):
+            raise ValueError(f"{name}: expected [B, {self.M}, {self.N}, {self.N}], got {tuple(t.shape)}")
+        if t.dtype != self.dtype or not t.is_cuda or t.device.index != self.device or not t.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous {self.dtype} tensor on cuda:{self.device}")
+        return t.shape[0]
+
+    def _check_spec(self, t: torch.Tensor, name: str, B: int):
+        shared = bool(self.flags & SHARED_KERNEL)
+        want = (1 if shared else B, self.M, self.N, self.N // 2 + 1)
+        if t.dim() == 3 and shared:
+            t = t.unsqueeze(0)
+        if tuple(t.shape) != want:
+            raise ValueError(f"{name}: expected {want}, got {tuple(t.shape)}")
+        if t.dtype != self.cdtype or not t.is_cuda or t.device.index != self.device or not t.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous {self.cdtype} tensor on cuda:{self.device}")
+        return t
+
+
+def coeffs(plan: Plan, samples: torch.Tensor, normalize: bool = False):
+    """C = DFT(P)/|L| of each kernel in `samples` ([n, M, N, N] real).
+    Returns (C [n, M, N, N/2+1] complex, log_scale [n] float64 or None)."""
+    n = plan._check_grid(samples, "samples")
+    C = torch.empty(plan.spec_shape(n), dtype=plan.cdtype, device=samples.device)
+    ls = torch.empty(n, dtype=torch.float64, device=samples.device) if normalize else None
+    _check(load_library().se2_coeffs(plan.handle, _ptr(samples), n, _ptr(C), _ptr(ls), _stream(samples.device)))
+    return C, ls
+
+
+def convolve(plan: Plan, f: torch.Tensor, C: torch.Tensor, log_scale: Optional[torch.Tensor] = None,
+             out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """S_K[f, rho] on Omega_L for a batch f [B, M, N, N]."""
+    return convolve_chain(plan, f, [C], None if log_scale is None else [log_scale], out)
+
+
+def convolve_chain(plan: Plan, f: torch.Tensor, Cs: Sequence[torch.Tensor],
+                   log_scales: Optional[Sequence[Optional[torch.Tensor]]] = None,
+                   out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """f * rho_1 * ... * rho_k via W^k . DFT(f) . C_1 ... C_k."""
+    B = plan._check_grid(f, "f")
+    if out is None:
+        out = torch.empty_like(f)
+    else:
+        plan._check_grid(out, "out")
+    k = len(Cs)
+    Cs = [plan._check_spec(C, f"coeffs[{i}]", B) for i, C in enumerate(Cs)]
+    cp = (ctypes.c_void_p * k)(*[C.data_ptr() for C in Cs])
+    if log_scales is not None:
+        if len(log_scales) != k:
+            raise ValueError("log_scales must have one entry per kernel")
+        for ls in log_scales:
+            if ls is not None and (ls.dtype != torch.float64 or not ls.is_cuda or not ls.is_contiguous()):
+                raise ValueError("log_scale: need a contiguous float64 CUDA tensor")
+        lp = (ctypes.c_void_p * k)(*[0 if ls is None else ls.data_ptr() for ls in log_scales])
+    else:
+        lp = None
+    _check(load_library().se2_convolve_chain(plan.handle, _ptr(f), B, cp, lp, k, _ptr(out), _stream(f.device)))
+    return out
+
+
+__all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_chain", "load_library", "LIB_PATH",
+           "SHARED_KERNEL"]

@@ -1,0 +1,51 @@
+// Internal declarations shared by the C-ABI implementation and the kernel
+// instantiation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "se2_kernels.cuh"
+
+namespace se2 {
+
+constexpr size_t kMaxDynSmem = 226 * 1024;   // opt-in limit per block minus static use
+
+template <typename T>
+struct KTable {
+    using XK = void (*)(XArgs<T>);
+    using LK = void (*)(LArgs<T>);
+    XK fwd_xt = nullptr, inv_tx = nullptr;   // fused x+theta (null: use split path)
+    size_t smem_xt = 0;
+    XK fwd_x = nullptr, inv_x = nullptr;     // split path, x only
+    size_t smem_x = 0;
+    LK y_conv = nullptr, y_coef = nullptr;   // lines of length N along y
+    size_t smem_y = 0;
+    int lines_y = 0;                          // lines per block
+    LK t_fwd = nullptr, t_inv = nullptr;     // lines of length M along theta
+    size_t smem_t = 0;
+    int lines_t = 0;
+    int teams_x = 0;                          // row pairs per block (split fwd_x/inv_x)
+};
+
+// Fills the kernel table for (N, M); false if the size is unsupported.
+template <typename T>
+bool get_kernels(int N, int M, KTable<T>* kt);
+
+// FP64 twiddle generation (sincospi), rounded to T.
+template <typename T>
+cudaError_t make_twiddles(c2<T>* tw, int L, cudaStream_t st);
+
+template <typename T, int N, int M>
+constexpr size_t fused_smem() {
+    return ((size_t)M * slab_pitch<N>() + (size_t)(kThreads / team_size<N>()) * xbuf_elems<N>()) * sizeof(c2<T>);
+}
+template <typename T, int N>
+constexpr size_t xsplit_smem() {
+    return (size_t)(kThreads / team_size<N>()) * xbuf_elems<N>() * sizeof(c2<T>);
+}
+template <typename T, int L>
+constexpr size_t lines_smem() {   // no exchange buffer when one lane holds a line
+    return Fac<L>::R2 == 1 ? 0 : (size_t)(kThreads / team_size<L>()) * ((Fac<L>::R1 * (Fac<L>::R2 + 1)) | 1) * sizeof(c2<T>);
+}
+
+}  // namespace se2

@@ -1,0 +1,67 @@
+"""The C-ABI library loads, exports every symbol include/se2.h declares, and
+rejects bad arguments on the host before touching a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_05149_gb300 import build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(se2_\w+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"se2_plan_create", "se2_coeffs", "se2_convolve", "se2_convolve_chain"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_version_and_error_text(lib):
+    lib.se2_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.se2_version()
+    lib.se2_last_error.restype = ctypes.c_char_p
+    assert lib.se2_last_error() is not None
+
+
+@pytest.mark.parametrize("N,M,B,prec,status", [
+    (7, 16, 1, 1, 2),     # N not a power of two -> UNSUPPORTED
+    (1024, 16, 1, 1, 2),  # N too large
+    (32, 3, 1, 1, 2),     # M not a power of two
+    (32, 256, 1, 1, 2),   # M too large
+    (32, 16, 0, 1, 1),    # batch < 1 -> INVALID_ARG
+    (32, 16, 1, 9, 2),    # unknown precision -> UNSUPPORTED
+])
+def test_plan_create_rejects_bad_sizes_on_host(lib, N, M, B, prec, status):
+    h = ctypes.c_void_p(1)
+    lib.se2_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_uint, ctypes.c_int]
+    assert lib.se2_plan_create(ctypes.byref(h), N, M, B, prec, 0, 0) == status
+    assert not h.value  # NULL on failure
+
+
+def test_null_plan_and_null_pointers_rejected(lib):
+    vp = ctypes.c_void_p
+    lib.se2_convolve.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
+    lib.se2_coeffs.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp]
+    assert lib.se2_convolve(None, None, 1, None, None, None, None) == 1
+    assert lib.se2_coeffs(None, None, 1, None, None, None) == 1
+    assert lib.se2_plan_create(None, 32, 16, 1, 1, 0, 0) == 1
+    lib.se2_plan_destroy.argtypes = [vp]
+    assert lib.se2_plan_destroy(None) == 0

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs are the seeded synth arrays rounded to the path's real type; the
+oracle gets those exact values upcast to FP64.  Errors are normwise:
+max-rel = max|gpu - oracle| / max|oracle|.  Bars: 1e-10 (FP64), 1e-5 (FP32).
+"""
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth  # noqa: E402
+from oracle import closed_forms as cf  # noqa: E402
+from oracle import direct  # noqa: E402
+from oracle import se2_oracle as O  # noqa: E402
+
+TOL = {"f32": 1e-5, "f64": 1e-10}
+NP = {"f32": np.float32, "f64": np.float64}
+
+
+@pytest.fixture(scope="module")
+def se2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_05149_gb300 import build as b
+    b.build()
+    import paper_2504_05149_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _problem(cfg, idx, N, M, nb, kernels):
+    prob = synth.make_problem(cfg, idx, N, M, n_bumps=nb)
+    F = synth.sample_bumps(N, M, prob.bumps)
+    Ps = [synth.sample_kernel(N, M, k) for k in kernels]
+    return prob, F, Ps
+
+
+def _dev(x, prec):
+    return torch.from_numpy(np.ascontiguousarray(x.astype(NP[prec]))).cuda()
+
+
+def _run(se2, prec, F_list, P_lists, normalize=False, flags=0):
+    """F_list: B grids; P_lists: B lists of k kernels (or one list if shared)."""
+    N, M = F_list[0].shape[1], F_list[0].shape[0]
+    B = len(F_list)
+    plan = se2.Plan(N, M, batch=B, precision=prec, flags=flags)
+    f = _dev(np.stack(F_list), prec)
+    k = len(P_lists[0])
+    Cs, Ls = [], []
+    for i in range(k):
+        P = np.stack([pl[i] for pl in P_lists])
+        C, ls = se2.coeffs(plan, _dev(P, prec), normalize=normalize)
+        Cs.append(C)
+        Ls.append(ls)
+    out = se2.convolve_chain(plan, f, Cs, Ls if normalize else None)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy(), [C.cpu().numpy() for C in Cs], [None if l is None else l.cpu().numpy() for l in Ls]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_c1_single_convolution(se2, prec):
+    """N=32, M=16, 3 bumps, kernel sigma=0.05, sigma_theta=0.3."""
+    N, M = 32, 16
+    kp = synth.KernelParams(0.05, 0.3)
+    prob, F, (P,) = _problem(1, 0, N, M, 3, [kp])
+    F = F.astype(NP[prec]).astype(np.float64)
+    P = P.astype(NP[prec]).astype(np.float64)
+    out, (C,), _ = _run(se2, prec, [F], [[P]])
+    assert _rel(C[0], O.coeffs_half(P)) < TOL[prec]
+    want = O.convolve(F, P)
+    assert _rel(out[0], want) < TOL[prec]
+    # and the brute-force direct sum
+    assert _rel(out[0], direct.direct_conv(F, P)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_c1_brute_force_16x16x8(se2, prec):
+    N, M = 16, 8
+    kp = synth.KernelParams(0.05, 0.3)
+    prob, F, (P,) = _problem(1, 0, N, M, 3, [kp])
+    F = F.astype(NP[prec]).astype(np.float64)
+    P = P.astype(NP[prec]).astype(np.float64)
+    out, _, _ = _run(se2, prec, [F], [[P]])
+    assert _rel(out[0], direct.direct_conv(F, P)) < TOL[prec]
+
+
+def test_c2_single_and_8_chain_fp32(se2):
+    """N=256, M=64, 16 bumps: single convolution and an 8-fold chain with
+    sigma ~ U[.01,.04], sigma_theta ~ U[.1,.5], against the oracle; the chain
+    also against the continuous closed form (variances add)."""
+    N, M = 256, 64
+    prob = synth.make_problem(2, 0, N, M, n_bumps=16, n_kernels=8)
+    F = synth.sample_bumps(N, M, prob.bumps).astype(np.float32).astype(np.float64)
+    Ps = [synth.sample_kernel(N, M, k).astype(np.float32).astype(np.float64) for k in prob.kernels]
+    out1, _, _ = _run(se2, "f32", [F], [[Ps[0]]])
+    assert _rel(out1[0], O.convolve(F, Ps[0])) < 1e-5
+    out8, _, _ = _run(se2, "f32", [F], [Ps])
+    want8 = O.convolve_chain(F, Ps)
+    assert _rel(out8[0], want8) < 1e-5
+    cont = cf.continuous_output(N, M, prob.bumps, prob.kernels)
+    assert _rel(out8[0], cont) < 1e-4     # FP32 rounding of inputs + aliasing
+
+
+@pytest.mark.parametrize("N,M", [(8, 2), (8, 4), (16, 16), (32, 8), (64, 32), (128, 16), (256, 8),
+                                 (512, 8), (32, 128), (128, 128)])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_sizes_random_inputs(se2, N, M, prec):
+    """Unstructured inputs over the supported size range (both fused and
+    split passes), B = 3 with distinct kernels."""
+    rng = np.random.default_rng(N * 1000 + M)
+    Fs = [rng.standard_normal((M, N, N)) for _ in range(3)]
+    Ps = [[rng.random((M, N, N))] for _ in range(3)]
+    Fs = [x.astype(NP[prec]).astype(np.float64) for x in Fs]
+    Ps = [[x[0].astype(NP[prec]).astype(np.float64)] for x in Ps]
+    out, _, _ = _run(se2, prec, Fs, Ps)
+    for b in range(3):
+        want = O.convolve(Fs[b], Ps[b][0])
+        assert _rel(out[b], want) < TOL[prec] * (3 if prec == "f32" else 1)
+
+
+def test_largest_size_split_path_fp32(se2):
+    N, M = 512, 128
+    prob, F, (P,) = _problem(3, 0, N, M, 8, [synth.KernelParams(0.02, 0.3)])
+    F = F.astype(np.float32).astype(np.float64)
+    P = P.astype(np.float32).astype(np.float64)
+    out, _, _ = _run(se2, "f32", [F], [[P]])
+    assert _rel(out[0], O.convolve(F, P)) < 1e-5
+
+
+def test_normalised_coeffs_and_log_scale(se2):
+    """se2_coeffs with log_scale: C / mean|P| and ln(mean|P|); the chain
+    multiplies back exp(sum ln s) in FP64."""
+    N, M = 64, 16
+    rng = np.random.default_rng(7)
+    F = rng.random((M, N, N))
+    Ps = [rng.random((M, N, N)) * s for s in (1e-3, 50.0, 2.0)]
+    Fq = F.astype(np.float32).astype(np.float64)
+    Pq = [P.astype(np.float32).astype(np.float64) for P in Ps]
+    out, Cs, Ls = _run(se2, "f32", [Fq], [Pq], normalize=True)
+    for P, C, ls in zip(Pq, Cs, Ls):
+        s = np.mean(np.abs(P))
+        assert abs(ls[0] - math.log(s)) < 1e-6
+        assert _rel(C[0], O.coeffs_half(P) / s) < 1e-5
+    assert _rel(out[0], O.convolve_chain(Fq, Pq)) < 1e-5
+
+
+def test_shared_kernel_flag(se2):
+    N, M, B = 64, 32, 4
+    rng = np.random.default_rng(11)
+    Fs = [rng.standard_normal((M, N, N)).astype(np.float32).astype(np.float64) for _ in range(B)]
+    P = rng.random((M, N, N)).astype(np.float32).astype(np.float64)
+    plan = se2.Plan(N, M, batch=B, precision="f32", flags=se2.SHARED_KERNEL)
+    C, _ = se2.coeffs(plan, _dev(P[None], "f32"))
+    out = se2.convolve(plan, _dev(np.stack(Fs), "f32"), C).double().cpu().numpy()
+    for b in range(B):
+        assert _rel(out[b], O.convolve(Fs[b], P)) < 1e-5
+
+
+def test_equal_kernels_chain_is_hadamard_power(se2):
+    """Algorithm 4 (Hadamard power, W only for odd q) from k equal kernels."""
+    N, M = 32, 16
+    kp = synth.KernelParams(0.04, 0.4, 0.3)
+    prob, F, (P,) = _problem(1, 4, N, M, 3, [kp])
+    F = F.astype(np.float32).astype(np.float64)
+    P = P.astype(np.float32).astype(np.float64)
+    for q in (2, 3, 5):
+        out, _, _ = _run(se2, "f32", [F], [[P] * q])
+        assert _rel(out[0], O.convolve_power(F, P, q)) < 1e-5
+
+
+def _sub(env, code):
+    r = subprocess.run([sys.executable, "-c", code], env={**os.environ, **env}, capture_output=True, text=True,
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    assert r.returncode == 0, r.stdout + r.stderr
+    return r.stdout
+
+
+_RAGGED = r"""
+import numpy as np, torch, sys
+sys.path.insert(0, '.')
+import paper_2504_05149_gb300 as se2
+from oracle import se2_oracle as O
+N, M, B = 64, 16, 5
+rng = np.random.default_rng(3)
+F = rng.standard_normal((B, M, N, N)).astype(np.float32)
+P = rng.random((B, M, N, N)).astype(np.float32)
+plan = se2.Plan(N, M, batch=B)
+C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
+out = se2.convolve(plan, torch.from_numpy(F).cuda(), C).double().cpu().numpy()
+err = max(np.abs(out[b] - O.convolve(F[b].astype(float), P[b].astype(float))).max()
+          / np.abs(O.convolve(F[b].astype(float), P[b].astype(float))).max() for b in range(B))
+assert err < 1e-5, err
+print("ok", err)
+"""
+
+
+def test_ragged_chunks_and_forced_split_path(se2):
+    """B = 5 through a scratch of 2 problems (chunks 2, 2, 1), on the fused
+    and on the split pass structure."""
+    _sub({"SE2_MAX_CHUNK": "2"}, _RAGGED)
+    _sub({"SE2_MAX_CHUNK": "2", "SE2_FORCE_SPLIT": "1"}, _RAGGED)
+
+
+def test_invalid_arguments_on_gpu_plan(se2):
+    plan = se2.Plan(32, 16, batch=2)
+    f = torch.zeros((3, 16, 32, 32), device="cuda")
+    C = torch.zeros((3, 16, 32, 17), dtype=torch.complex64, device="cuda")
+    import ctypes
+    lib = se2.load_library()
+    # B larger than the plan batch
+    st = lib.se2_convolve(plan.handle, ctypes.c_void_p(f.data_ptr()), 3, ctypes.c_void_p(C.data_ptr()), None,
+                          ctypes.c_void_p(f.data_ptr() + 4), None)
+    assert st == 1
+    # misaligned coefficient pointer
+    st = lib.se2_convolve(plan.handle, ctypes.c_void_p(f.data_ptr()), 1, ctypes.c_void_p(C.data_ptr() + 4), None,
+                          ctypes.c_void_p(f.data_ptr() + 4 * 16 * 32 * 32), None)
+    assert st == 1
+    # out aliases f
+    st = lib.se2_convolve(plan.handle, ctypes.c_void_p(f.data_ptr()), 1, ctypes.c_void_p(C.data_ptr()), None,
+                          ctypes.c_void_p(f.data_ptr()), None)
+    assert st == 1
+    with pytest.raises(ValueError):
+        se2.convolve(plan, f[:1].double(), C[:1])
