@@ -125,6 +125,63 @@ se2_status se2_convolve_chain(se2_plan_t plan, const void* f, int B,
                               const void* const* coeffs, const double* const* log_scales,
                               int k, void* out, void* stream);
 
+/*
+ * se2_backward -- adjoint of se2_convolve (not in the paper; derived from it):
+ * for a loss with gradient G_b = dLoss/dout_b of out_b = iDFT(W . DFT(F_b) . C_b)
+ * * exp(ls_b),
+ *   grad_f_b  = iDFT( W . conj(C_b) . DFT(G_b) ) * exp(ls_b)     (a correlation)
+ *   grad_params[i] += sum_b (1/|L|) sum_k W(k) dC_i,b(k) conj(DFT(G_b)(k)) DFT(F_b)(k)
+ * (the sum over all bins, real; evaluated on the half spectrum with weights 1
+ * at x bins 0 and N/2, 2 elsewhere).
+ *   grad_out     device, [B][M][N][N] real (G)
+ *   f            device, [B][M][N][N] real (needed when n_params > 0)
+ *   coeffs, log_scale  as in se2_convolve (single kernel)
+ *   n_params     0..4 kernel parameters
+ *   dcoeffs      host array of n_params device pointers: DFT(dP/dp_i)/|L|, the
+ *                derivative of the effective kernel spectrum exp(ls) C (use
+ *                se2_coeffs without log_scale on the sampled derivative), laid
+ *                out like coeffs
+ *   grad_params  device, [n_params] double, ACCUMULATED (zero it first)
+ *   grad_f       device, [B][M][N][N] real, or NULL (parameters only)
+ */
+se2_status se2_backward(se2_plan_t plan, const void* grad_out, const void* f, int B,
+                        const void* coeffs, const double* log_scale, int n_params,
+                        const void* const* dcoeffs, double* grad_params, void* grad_f,
+                        void* stream);
+
+/*
+ * se2_sample_radial_gaussian -- the radial kernel family used for
+ * differentiation, sampled on Omega_L: a Gaussian of width sigma in x
+ * (normalised over R^2, periodised over Z^2) times 2 pi times a wrapped normal
+ * of width sigma_theta centred at nu (unit mass under the Haar measure Eq. dg),
+ * the radial Gaussians of Section 6.2.  Writes [M][N][N] arrays of the plan's
+ * real type: P and its derivatives in sigma and sigma_theta (any may be NULL).
+ * The 1-D factors are evaluated in FP64.
+ */
+se2_status se2_sample_radial_gaussian(se2_plan_t plan, double sigma, double sigma_theta, double nu,
+                                      void* P, void* dP_dsigma, void* dP_dsigma_theta, void* stream);
+
+/*
+ * se2_plan_status -- synchronise `stream`, then report and clear the plan's
+ * device error word.  The persistent convolution kernel waits on counters
+ * that other blocks of the same launch update; each wait is bounded (about a
+ * second).  A wait that gives up sets the error word, the launch stops taking
+ * work, and its output is undefined.  Returns SE2_ERR_TIMEOUT in that case,
+ * SE2_OK otherwise.  Until it is read, later launches on the plan also stop
+ * at once.
+ */
+se2_status se2_plan_status(se2_plan_t plan, void* stream);
+
+/*
+ * se2_debug_wait_timeout -- test hook for the bounded-wait path: launches the
+ * persistent kernel on one problem (f, coeffs, out as in se2_convolve) with a
+ * dependency that is never met, so that its wait runs out after a few
+ * thousand polls.  Afterwards se2_plan_status returns SE2_ERR_TIMEOUT.
+ * SE2_ERR_UNSUPPORTED if the plan does not use the persistent kernel.
+ */
+se2_status se2_debug_wait_timeout(se2_plan_t plan, const void* f, const void* coeffs, void* out,
+                                  void* stream);
+
 /* Thread-local text of the last error (never NULL). */
 const char* se2_last_error(void);
 

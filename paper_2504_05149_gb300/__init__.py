@@ -53,9 +53,14 @@ def load_library(path: str = LIB_PATH):
     lib.se2_coeffs.argtypes = [vp, vp, ip, vp, vp, vp]
     lib.se2_convolve.argtypes = [vp, vp, ip, vp, vp, vp, vp]
     lib.se2_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp, vp]
+    lib.se2_plan_status.argtypes = [vp, vp]
+    lib.se2_backward.argtypes = [vp, vp, vp, ip, vp, vp, ip, ctypes.POINTER(vp), vp, vp, vp]
+    lib.se2_sample_radial_gaussian.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
+    lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
     lib.se2_last_error.restype = ctypes.c_char_p
     lib.se2_version.restype = ctypes.c_char_p
-    for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_chain"):
+    for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_chain",
+                 "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -98,6 +103,11 @@ class Plan:
 
     def workspace_bytes(self) -> int:
         return int(load_library().se2_plan_workspace_bytes(self._h))
+
+    def status(self):
+        """Synchronise the current stream and raise SE2Error if a bounded
+        device-side wait of the persistent kernel gave up since the last call."""
+        _check(load_library().se2_plan_status(self._h, _stream(self.device)))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -177,5 +187,69 @@ def convolve_chain(plan: Plan, f: torch.Tensor, Cs: Sequence[torch.Tensor],
     return out
 
 
-__all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_chain", "load_library", "LIB_PATH",
-           "SHARED_KERNEL"]
+def backward(plan: Plan, grad_out: torch.Tensor, C: torch.Tensor, f: Optional[torch.Tensor] = None,
+             dCs: Sequence[torch.Tensor] = (), log_scale: Optional[torch.Tensor] = None,
+             want_grad_f: bool = True):
+    """Adjoint of convolve: returns (grad_f or None, grad_params [len(dCs)] float64)."""
+    B = plan._check_grid(grad_out, "grad_out")
+    C = plan._check_spec(C, "coeffs", B)
+    n = len(dCs)
+    dCs = [plan._check_spec(d, f"dcoeffs[{i}]", B) for i, d in enumerate(dCs)]
+    if n > 0:
+        if f is None:
+            raise ValueError("parameter gradients need f")
+        plan._check_grid(f, "f")
+    gf = torch.empty_like(grad_out) if want_grad_f else None
+    gp = torch.zeros(max(n, 1), dtype=torch.float64, device=grad_out.device)
+    dp = (ctypes.c_void_p * max(n, 1))(*([d.data_ptr() for d in dCs] or [0]))
+    _check(load_library().se2_backward(plan.handle, _ptr(grad_out), _ptr(f), B, _ptr(C), _ptr(log_scale), n,
+                                       dp if n else None, _ptr(gp) if n else None, _ptr(gf),
+                                       _stream(grad_out.device)))
+    return gf, gp[:n]
+
+
+def sample_radial_gaussian(plan: Plan, sigma: float, sigma_theta: float, nu: float = 0.0, derivs: bool = False):
+    """The radial Gaussian x wrapped-normal kernel on the plan's grid
+    ([1, M, N, N]); with derivs=True also d/dsigma and d/dsigma_theta."""
+    dev = torch.device("cuda", plan.device)
+    shape = plan.grid_shape(1)
+    P = torch.empty(shape, dtype=plan.dtype, device=dev)
+    dPs = torch.empty(shape, dtype=plan.dtype, device=dev) if derivs else None
+    dPt = torch.empty(shape, dtype=plan.dtype, device=dev) if derivs else None
+    _check(load_library().se2_sample_radial_gaussian(plan.handle, float(sigma), float(sigma_theta), float(nu),
+                                                     _ptr(P), _ptr(dPs), _ptr(dPt), _stream(dev)))
+    return (P, dPs, dPt) if derivs else P
+
+
+class SE2Conv(torch.autograd.Function):
+    """out = f * rho(sigma, sigma_theta) for a batch f [B, M, N, N] and the
+    radial Gaussian x wrapped-normal kernel shared by the batch, differentiable
+    in f and in params = tensor([sigma, sigma_theta]) (float64).  The plan must
+    have the SHARED_KERNEL flag."""
+
+    @staticmethod
+    def forward(ctx, f, params, plan):
+        if not plan.flags & SHARED_KERNEL:
+            raise ValueError("SE2Conv needs a plan with SHARED_KERNEL")
+        sigma, sigma_t = (float(v) for v in params.detach().cpu().tolist())
+        P, dPs, dPt = sample_radial_gaussian(plan, sigma, sigma_t, 0.0, derivs=True)
+        C, _ = coeffs(plan, P)
+        dCs, _ = coeffs(plan, dPs)
+        dCt, _ = coeffs(plan, dPt)
+        out = convolve(plan, f.contiguous(), C)
+        ctx.plan = plan
+        ctx.save_for_backward(f, C, dCs, dCt)
+        ctx.params_dtype = params.dtype
+        ctx.params_device = params.device
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        f, C, dCs, dCt = ctx.saved_tensors
+        gf, gp = backward(ctx.plan, grad_out.contiguous(), C, f, [dCs, dCt],
+                          want_grad_f=ctx.needs_input_grad[0])
+        return gf, gp.to(ctx.params_device, ctx.params_dtype), None
+
+
+__all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_chain", "backward", "sample_radial_gaussian",
+           "SE2Conv", "load_library", "LIB_PATH", "SHARED_KERNEL"]

@@ -31,8 +31,23 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+SIZES = (8, 16, 32, 64, 128, 256, 512)
+
+
+def units():
+    """(source, object name, extra flags): se2_inst.cu once per (type, N)."""
+    out = []
+    for f in sorted(os.listdir(CSRC)):
+        if not f.endswith(".cu"):
+            continue
+        src = os.path.join(CSRC, f)
+        if f == "se2_inst.cu":
+            for t in ("float", "double"):
+                for n in SIZES:
+                    out.append((src, f"se2_inst_{t}_{n}.o", [f"-DSE2_T={t}", f"-DSE2_N={n}"]))
+        else:
+            out.append((src, f + ".o", []))
+    return out
 
 
 def _headers_mtime() -> float:
@@ -41,9 +56,10 @@ def _headers_mtime() -> float:
     return max(ts) if ts else 0.0
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
-    cmd = [_nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+def _compile(unit, extra) -> str:
+    src, name, defs = unit
+    obj = os.path.join(OBJDIR, name)
+    cmd = [_nvcc(), *ARCH, *FLAGS, *defs, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -54,14 +70,19 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OBJDIR, exist_ok=True)
     hdr = _headers_mtime()
     todo, objs = [], []
-    for s in sources():
-        obj = os.path.join(OBJDIR, os.path.basename(s) + ".o")
+    for u in units():
+        obj = os.path.join(OBJDIR, u[1])
         objs.append(obj)
-        if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(s), hdr):
-            todo.append(s)
+        if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(u[0]), hdr):
+            todo.append(u)
+    # drop objects of units that no longer exist
+    keep = {os.path.basename(o) for o in objs}
+    for f in os.listdir(OBJDIR):
+        if f.endswith(".o") and f not in keep:
+            os.remove(os.path.join(OBJDIR, f))
     if todo:
         with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
-            for obj in ex.map(lambda s: _compile(s, list(extra)), todo):
+            for obj in ex.map(lambda u: _compile(u, list(extra)), todo):
                 if verbose:
                     print("built", obj, file=sys.stderr)
     if todo or not os.path.exists(LIB):

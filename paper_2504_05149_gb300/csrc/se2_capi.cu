@@ -65,6 +65,14 @@ struct se2_plan_s {
     void* twM = nullptr;
     double* abs_sum = nullptr;  // [chunk]
     size_t ws_bytes = 0;
+    // persistent path
+    bool persist = false;
+    int slots = 0;              // scratch slots in the persistent ring
+    int persist_grid = 0;       // blocks of the persistent launch
+    unsigned* ctr = nullptr;    // [1 + 3 * batch] work counter + unit counters
+    int* err = nullptr;         // sticky device error word
+    int nslots = 0;             // problem slots in the scratch (>= 2)
+    double* tab = nullptr;      // [2N + 2M] FP64 tables of the Gaussian kernel family
     KTable<float> kf;
     KTable<double> kd;
     bool fused = false;
@@ -85,6 +93,7 @@ se2_status set_smem(const KTable<T>& kt) {
         {(const void*)kt.fwd_xt, kt.smem_xt}, {(const void*)kt.inv_tx, kt.smem_xt},
         {(const void*)kt.fwd_x, kt.smem_x},   {(const void*)kt.inv_x, kt.smem_x},
         {(const void*)kt.y_conv, kt.smem_y},  {(const void*)kt.y_coef, kt.smem_y},
+        {(const void*)kt.y_adj, kt.smem_y},
         {(const void*)kt.t_fwd, kt.smem_t},   {(const void*)kt.t_inv, kt.smem_t},
     };
     for (auto& e : list) {
@@ -106,6 +115,20 @@ se2_status plan_init(se2_plan_s* p) {
     p->fused = kt.fwd_xt != nullptr && !(split && split[0] == '1');
     se2_status st = set_smem<T>(kt);
     if (st != SE2_OK) return st;
+    const char* nop = getenv("SE2_NO_PERSIST");
+    p->persist = p->fused && kt.persist != nullptr && !(nop && nop[0] == '1');
+    if (p->persist) {
+        cudaError_t r = cudaFuncSetAttribute((const void*)kt.persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kt.smem_persist);
+        if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
+        int per_sm = 0, nsm = 0;
+        r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kt.persist, kThreads, kt.smem_persist);
+        if (r != cudaSuccess) return cuda_fail(r, "occupancy");
+        r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev);
+        if (r != cudaSuccess) return cuda_fail(r, "device attribute");
+        if (per_sm < 1) p->persist = false;
+        p->persist_grid = per_sm * nsm;
+    }
     p->elem = sizeof(c2<T>);
     cudaError_t e;
     if ((e = cudaMalloc(&p->twN, sizeof(c2<T>) * p->N)) != cudaSuccess) return fail(SE2_ERR_OOM, "twiddles: %s", cudaGetErrorString(e));
@@ -116,6 +139,12 @@ se2_status plan_init(se2_plan_s* p) {
 }
 
 void plan_free(se2_plan_s* p) {
+    if (p->ctr) cudaFree(p->ctr);
+    if (p->err) cudaFree(p->err);
+    if (p->tab) cudaFree(p->tab);
+    p->ctr = nullptr;
+    p->err = nullptr;
+    p->tab = nullptr;
     if (p->scratch) cudaFree(p->scratch);
     if (p->twN) cudaFree(p->twN);
     if (p->twM) cudaFree(p->twM);
@@ -126,13 +155,17 @@ void plan_free(se2_plan_s* p) {
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
+// Polls before a device-side wait gives up (each poll sleeps ~64 ns plus an
+// L2 round trip, so this is of the order of a second).
+constexpr long long kSpinLimit = 1ll << 21;
+
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
 template <typename T>
-XArgs<T> xargs(se2_plan_s* p) {
+XArgs<T> xargs(se2_plan_s* p, int slot0 = 0) {
     XArgs<T> a{};
-    a.s = (c2<T>*)p->scratch;
+    a.s = (c2<T>*)p->scratch + (size_t)slot0 * p->s_pstride;
     a.s_pstride = p->s_pstride;
     a.tp = p->tp;
     a.M = p->M;
@@ -144,9 +177,9 @@ XArgs<T> xargs(se2_plan_s* p) {
 
 // Forward x and theta transforms of nb real grids into the scratch.
 template <typename T>
-void launch_forward(se2_plan_s* p, const T* f, int nb, double* abs_sum, cudaStream_t st) {
+void launch_forward(se2_plan_s* p, const T* f, int nb, double* abs_sum, cudaStream_t st, int slot0 = 0) {
     KTable<T>& kt = table<T>(p);
-    XArgs<T> a = xargs<T>(p);
+    XArgs<T> a = xargs<T>(p, slot0);
     a.f = f;
     a.abs_sum = abs_sum;
     if (p->fused) {
@@ -155,7 +188,7 @@ void launch_forward(se2_plan_s* p, const T* f, int nb, double* abs_sum, cudaStre
         const int pairs = p->M / 2;
         kt.fwd_x<<<dim3(p->N, (pairs + kt.teams_x - 1) / kt.teams_x, nb), kThreads, kt.smem_x, st>>>(a);
         LArgs<T> l{};
-        l.s = (c2<T>*)p->scratch;
+        l.s = a.s;
         l.s_pstride = p->s_pstride;
         l.outer_stride = p->tp;                      // outer = y
         l.elem_stride = (long long)p->N * p->tp;     // along theta
@@ -169,15 +202,15 @@ void launch_forward(se2_plan_s* p, const T* f, int nb, double* abs_sum, cudaStre
 }
 
 template <typename T>
-void launch_inverse(se2_plan_s* p, T* out, int nb, cudaStream_t st) {
+void launch_inverse(se2_plan_s* p, T* out, int nb, cudaStream_t st, int slot0 = 0) {
     KTable<T>& kt = table<T>(p);
-    XArgs<T> a = xargs<T>(p);
+    XArgs<T> a = xargs<T>(p, slot0);
     a.out = out;
     if (p->fused) {
         kt.inv_tx<<<dim3(p->N, nb), kThreads, kt.smem_xt, st>>>(a);
     } else {
         LArgs<T> l{};
-        l.s = (c2<T>*)p->scratch;
+        l.s = a.s;
         l.s_pstride = p->s_pstride;
         l.outer_stride = p->tp;
         l.elem_stride = (long long)p->N * p->tp;
@@ -216,9 +249,49 @@ unsigned y_blocks(se2_plan_s* p) {
 }
 
 template <typename T>
+se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* coeffs,
+                       const double* const* log_scales, int k, void* out, cudaStream_t st,
+                       unsigned dep_extra, long long spin_limit) {
+    KTable<T>& kt = table<T>(p);
+    const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
+    const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
+    PArgs<T> a{};
+    a.x = xargs<T>(p);
+    a.x.f = (const T*)f;
+    a.x.out = (T*)out;
+    a.l = yargs<T>(p);
+    a.l.k = k;
+    a.l.c_pstride = cps;
+    a.l.ls_pstride = lps;
+    for (int i = 0; i < k; ++i) {
+        a.l.C[i] = (const c2<T>*)coeffs[i];
+        a.l.ls[i] = (log_scales && log_scales[i]) ? log_scales[i] : nullptr;
+    }
+    a.B = B;
+    a.D = p->slots;
+    a.nA = p->N;
+    a.nC = p->N;
+    a.nB = (int)y_blocks<T>(p);
+    a.work = p->ctr;
+    a.cnt = p->ctr + 1;
+    a.err = p->err;
+    a.spin_limit = spin_limit;
+    a.dep_extra = dep_extra;
+    cudaError_t e = cudaMemsetAsync(p->ctr, 0, sizeof(unsigned) * (1 + 3 * (size_t)B), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const long long units = (long long)B * (a.nA + a.nB + a.nC);
+    const int grid = (int)(units < p->persist_grid ? units : p->persist_grid);
+    kt.persist<<<grid, kThreads, kt.smem_persist, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
+}
+
+template <typename T>
 se2_status run_chain(se2_plan_s* p, const void* f, int B, const void* const* coeffs,
                      const double* const* log_scales, int k, void* out, cudaStream_t st) {
     KTable<T>& kt = table<T>(p);
+    if (p->persist) return run_persist<T>(p, f, B, coeffs, log_scales, k, out, st, 0, kSpinLimit);
     const size_t g = (size_t)p->N * p->N * p->M;
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
     const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
@@ -261,6 +334,38 @@ se2_status run_coeffs(se2_plan_s* p, const void* samples, int n, void* coeffs, d
         l.log_scale = log_scale;
         l.problem0 = c0;
         kt.y_coef<<<dim3(y_blocks<T>(p), nb), kThreads, kt.smem_y, st>>>(l);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
+}
+
+template <typename T>
+se2_status run_backward(se2_plan_s* p, const void* g, const void* f, int B, const void* coeffs,
+                        const double* log_scale, int n_params, const void* const* dcoeffs,
+                        double* grad_params, void* grad_f, cudaStream_t st) {
+    KTable<T>& kt = table<T>(p);
+    const size_t gs = (size_t)p->N * p->N * p->M;
+    const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
+    const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
+    const int per_pass = n_params > 0 ? p->nslots / 2 : p->nslots;
+    for (int c0 = 0; c0 < B; c0 += per_pass) {
+        const int nb = (B - c0 < per_pass) ? (B - c0) : per_pass;
+        launch_forward<T>(p, (const T*)g + c0 * gs, nb, nullptr, st, 0);
+        if (n_params > 0) launch_forward<T>(p, (const T*)f + c0 * gs, nb, nullptr, st, nb);
+        LArgs<T> l = yargs<T>(p);
+        l.s2 = n_params > 0 ? (c2<T>*)p->scratch + (size_t)nb * p->s_pstride : nullptr;
+        l.want_grad = grad_f != nullptr;
+        l.k = 1;
+        l.c_pstride = cps;
+        l.ls_pstride = lps;
+        l.C[0] = (const c2<T>*)coeffs + c0 * cps;
+        l.ls[0] = log_scale ? log_scale + c0 * lps : nullptr;
+        l.n_params = n_params;
+        for (int i = 0; i < n_params; ++i) l.dC[i] = (const c2<T>*)dcoeffs[i] + c0 * cps;
+        l.grad_params = grad_params;
+        kt.y_adj<<<dim3(y_blocks<T>(p), nb), kThreads, kt.smem_y, st>>>(l);
+        if (grad_f) launch_inverse<T>(p, (T*)grad_f + c0 * gs, nb, st, 0);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -317,15 +422,30 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
         if (v >= 1 && (size_t)v < chunk) chunk = (size_t)v;
     }
     if (chunk < 1) chunk = 1;
+    if (p->persist) {
+        // a ring of 4 slots: problems in flight between a unit A and its C
+        chunk = 4;
+        p->slots = 4;
+    }
     if (chunk > (size_t)batch) chunk = batch;
     p->chunk = (int)chunk;
-    e = cudaMalloc(&p->scratch, per * chunk);
-    if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "scratch (%zu bytes): %s", per * chunk, cudaGetErrorString(e)); }
+    if (p->persist && p->slots > (int)chunk) p->slots = (int)chunk;
+    // at least two slots: the adjoint transforms grad_out and f side by side
+    p->nslots = chunk < 2 ? 2 : (int)chunk;
+    e = cudaMalloc(&p->scratch, per * p->nslots);
+    if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "scratch (%zu bytes): %s", per * p->nslots, cudaGetErrorString(e)); }
+    e = cudaMalloc((void**)&p->tab, sizeof(double) * 2 * ((size_t)N + M));
+    if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "tables: %s", cudaGetErrorString(e)); }
     e = cudaMalloc((void**)&p->abs_sum, sizeof(double) * chunk);
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "accumulators: %s", cudaGetErrorString(e)); }
+    e = cudaMalloc((void**)&p->ctr, sizeof(unsigned) * (1 + 3 * (size_t)batch));
+    if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "counters: %s", cudaGetErrorString(e)); }
+    e = cudaMalloc((void**)&p->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
+    if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "error word: %s", cudaGetErrorString(e)); }
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { plan_free(p); delete p; return cuda_fail(e, "plan setup"); }
-    p->ws_bytes = per * chunk + p->elem * (N + M) + sizeof(double) * chunk;
+    p->ws_bytes = per * p->nslots + sizeof(double) * 2 * ((size_t)N + M) + p->elem * (N + M) + sizeof(double) * chunk + sizeof(unsigned) * (1 + 3 * (size_t)batch) + sizeof(int);
     *out = p;
     return SE2_OK;
 }
@@ -375,6 +495,82 @@ se2_status se2_convolve_chain(se2_plan_t p, const void* f, int B, const void* co
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == SE2_F32 ? run_chain<float>(p, f, B, coeffs, log_scales, k, out, s)
                               : run_chain<double>(p, f, B, coeffs, log_scales, k, out, s);
+}
+
+se2_status se2_backward(se2_plan_t p, const void* grad_out, const void* f, int B, const void* coeffs,
+                        const double* log_scale, int n_params, const void* const* dcoeffs,
+                        double* grad_params, void* grad_f, void* stream) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    if (grad_out == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "grad_out/coeffs is NULL");
+    if (B < 1 || B > p->batch) return fail(SE2_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, p->batch);
+    if (n_params < 0 || n_params > kMaxParams) return fail(SE2_ERR_INVALID_ARG, "n_params=%d outside [0, %d]", n_params, kMaxParams);
+    if (n_params > 0 && (f == nullptr || dcoeffs == nullptr || grad_params == nullptr))
+        return fail(SE2_ERR_INVALID_ARG, "parameter gradients need f, dcoeffs and grad_params");
+    if (n_params == 0 && grad_f == nullptr) return fail(SE2_ERR_INVALID_ARG, "nothing to compute");
+    const size_t re = p->elem / 2;
+    if (!aligned(grad_out, re) || (f && !aligned(f, re)) || (grad_f && !aligned(grad_f, re)) ||
+        !aligned(coeffs, p->elem) || (log_scale && !aligned(log_scale, 8)) || (grad_params && !aligned(grad_params, 8)))
+        return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    for (int i = 0; i < n_params; ++i)
+        if (dcoeffs[i] == nullptr || !aligned(dcoeffs[i], p->elem)) return fail(SE2_ERR_INVALID_ARG, "dcoeffs[%d] NULL or misaligned", i);
+    if (grad_f != nullptr && (grad_f == grad_out || grad_f == f)) return fail(SE2_ERR_INVALID_ARG, "grad_f aliases an input");
+    DeviceGuard guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == SE2_F32
+               ? run_backward<float>(p, grad_out, f, B, coeffs, log_scale, n_params, dcoeffs, grad_params, grad_f, s)
+               : run_backward<double>(p, grad_out, f, B, coeffs, log_scale, n_params, dcoeffs, grad_params, grad_f, s);
+}
+
+se2_status se2_sample_radial_gaussian(se2_plan_t p, double sigma, double sigma_theta, double nu, void* P,
+                                      void* dP_dsigma, void* dP_dsigma_theta, void* stream) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    if (!(sigma > 0) || !(sigma_theta > 0)) return fail(SE2_ERR_INVALID_ARG, "sigma and sigma_theta must be > 0");
+    if (P == nullptr && dP_dsigma == nullptr && dP_dsigma_theta == nullptr) return fail(SE2_ERR_INVALID_ARG, "no output");
+    const size_t re = p->elem / 2;
+    if ((P && !aligned(P, re)) || (dP_dsigma && !aligned(dP_dsigma, re)) || (dP_dsigma_theta && !aligned(dP_dsigma_theta, re)))
+        return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    DeviceGuard guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    k_gauss_tables<<<(p->N + p->M + 127) / 128, 128, 0, s>>>(p->tab, p->N, p->M, sigma, sigma_theta, nu);
+    const long long total = (long long)p->N * p->N * p->M;
+    const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    if (p->prec == SE2_F32)
+        k_gauss_fill<float><<<blocks, 256, 0, s>>>(p->tab, p->N, p->M, (float*)P, (float*)dP_dsigma, (float*)dP_dsigma_theta);
+    else
+        k_gauss_fill<double><<<blocks, 256, 0, s>>>(p->tab, p->N, p->M, (double*)P, (double*)dP_dsigma, (double*)dP_dsigma_theta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
+}
+
+se2_status se2_plan_status(se2_plan_t p, void* stream) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    DeviceGuard guard(p->dev);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int h = 0;
+    e = cudaMemcpy(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    if (h != 0) {
+        e = cudaMemset(p->err, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+        return fail(SE2_ERR_TIMEOUT, "a device-side wait of the persistent kernel gave up (code %d)", h);
+    }
+    return SE2_OK;
+}
+
+se2_status se2_debug_wait_timeout(se2_plan_t p, const void* f, const void* coeffs, void* out, void* stream) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    if (!p->persist) return fail(SE2_ERR_UNSUPPORTED, "plan does not use the persistent kernel");
+    if (f == nullptr || coeffs == nullptr || out == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    DeviceGuard guard(p->dev);
+    const void* c[1] = {coeffs};
+    // one problem whose A->B wait can never be met; 4096 polls end it quickly
+    return run_persist<float>(p, f, 1, c, nullptr, 1, out, (cudaStream_t)stream, 1u, 4096);
 }
 
 se2_status se2_convolve(se2_plan_t p, const void* f, int B, const void* coeffs, const double* log_scale,

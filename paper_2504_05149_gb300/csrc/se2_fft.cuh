@@ -95,8 +95,11 @@ template <> struct Fac<64>  { static constexpr int R1 = 8,  R2 = 8; };
 template <> struct Fac<128> { static constexpr int R1 = 16, R2 = 8; };
 template <> struct Fac<256> { static constexpr int R1 = 16, R2 = 16; };
 template <> struct Fac<512> { static constexpr int R1 = 32, R2 = 16; };
-template <int L> __host__ __device__ constexpr int team_size() { return Fac<L>::R1 > Fac<L>::R2 ? Fac<L>::R1 : Fac<L>::R2; }
-template <int L> __host__ __device__ constexpr int reg_count() { return team_size<L>(); }
+// Lanes per line: one lane holds a whole line when R2 == 1.
+template <int L> __host__ __device__ constexpr int team_size() {
+    return Fac<L>::R2 == 1 ? 1 : (Fac<L>::R1 > Fac<L>::R2 ? Fac<L>::R1 : Fac<L>::R2);
+}
+template <int L> __host__ __device__ constexpr int reg_count() { return Fac<L>::R1 > Fac<L>::R2 ? Fac<L>::R1 : Fac<L>::R2; }
 // Exchange buffer (complex elements) one team needs: R1 rows of pitch R2+1,
 // at least L for linear scratch, plus one so that consecutive buffers start
 // in different banks.
@@ -155,6 +158,106 @@ __device__ __forceinline__ void team_fft(T* re, T* im, int lane, c2<T>* xb,
             fft_reg<R2, DIR>(re, im);
         }
         sync();
+    }
+}
+
+// Same as team_fft, with this lane's step-A twiddles e^{DIR 2 pi i lane k / L}
+// (k < R1) already in registers (wr, wi), so loops over several lines do not
+// reload them.
+template <int R1, int R2, int DIR, typename T, typename Sync>
+__device__ __forceinline__ void team_fft_r(T* re, T* im, int lane, c2<T>* xb,
+                                           const T* wr, const T* wi, Sync sync) {
+    if constexpr (R2 == 1) {
+        fft_reg<R1, DIR>(re, im);
+    } else {
+        if (lane < R2) {
+            fft_reg<R1, DIR>(re, im);
+#pragma unroll
+            for (int k1 = 1; k1 < R1; ++k1) {
+                const T r = re[k1] * wr[k1] - im[k1] * wi[k1];
+                im[k1] = re[k1] * wi[k1] + im[k1] * wr[k1];
+                re[k1] = r;
+            }
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) xb[k1 * (R2 + 1) + lane] = mk<T>(re[k1], im[k1]);
+        }
+        sync();
+        if (lane < R1) {
+#pragma unroll
+            for (int t = 0; t < R2; ++t) {
+                const c2<T> v = xb[lane * (R2 + 1) + t];
+                re[t] = v.x;
+                im[t] = v.y;
+            }
+            fft_reg<R2, DIR>(re, im);
+        }
+        sync();
+    }
+}
+
+// Load this lane's step-A twiddles for a length-L team FFT.
+template <int L, int DIR, typename T>
+__device__ __forceinline__ void load_twiddles(const c2<T>* __restrict__ tw, int lane, T* wr, T* wi) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
+    const int l = lane < R2 ? lane : 0;
+#pragma unroll
+    for (int k = 0; k < R1; ++k) {
+        const c2<T> w = tw[(l * k) % L];
+        wr[k] = w.x;
+        wi[k] = (DIR < 0) ? w.y : -w.y;
+    }
+}
+
+// Row offset (complex elements) of row r in a column-transformed slab of pitch
+// SP: rows are shifted by 2 elements per group of R1 rows, so that the strided
+// row accesses of column_fft fall in distinct shared-memory banks.
+template <int L> __host__ __device__ constexpr int row_group() { return Fac<L>::R2 == 1 ? (1 << 30) : Fac<L>::R1; }
+template <int L, int SP> __device__ __forceinline__ constexpr int rowoff(int r) { return r * SP + (r / row_group<L>()) * 2; }
+template <int L, int SP> __host__ __device__ constexpr int slab_elems() { return L * SP + (L / row_group<L>() + 1) * 2; }
+
+// In-place FFT of the column c of an L-row slab in shared memory (row r at
+// rowoff<L, SP>(r) + c), natural order in and out, by a team of
+// team_size<L>() lanes with their step-A twiddles in (wr, wi).  Step A places
+// A[t][k1] at row k1 + R1 t, step B reads rows s + R1 t and writes X[s + R1 k]
+// back to the same rows.  `act` = false lanes only synchronise.
+template <int L, int SP, int DIR, typename T, typename Sync>
+__device__ __forceinline__ void column_fft_r(c2<T>* S, int c, int lane, bool act,
+                                             const T* wr, const T* wi, Sync sync) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2, RM = reg_count<L>();
+    T re[RM], im[RM];
+    if constexpr (R2 == 1) {
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < L; ++r) { const c2<T> v = S[rowoff<L, SP>(r) + c]; re[r] = v.x; im[r] = v.y; }
+            fft_reg<L, DIR>(re, im);
+#pragma unroll
+            for (int r = 0; r < L; ++r) S[rowoff<L, SP>(r) + c] = mk<T>(re[r], im[r]);
+        }
+    } else {
+        if (act && lane < R2) {
+#pragma unroll
+            for (int j = 0; j < R1; ++j) { const c2<T> v = S[rowoff<L, SP>(lane + R2 * j) + c]; re[j] = v.x; im[j] = v.y; }
+            fft_reg<R1, DIR>(re, im);
+#pragma unroll
+            for (int k1 = 1; k1 < R1; ++k1) {
+                const T r = re[k1] * wr[k1] - im[k1] * wi[k1];
+                im[k1] = re[k1] * wi[k1] + im[k1] * wr[k1];
+                re[k1] = r;
+            }
+        }
+        sync();     // every step-A load is done before any step-A store
+        if (act && lane < R2) {
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) S[rowoff<L, SP>(k1 + R1 * lane) + c] = mk<T>(re[k1], im[k1]);
+        }
+        sync();
+        if (act && lane < R1) {
+#pragma unroll
+            for (int t = 0; t < R2; ++t) { const c2<T> v = S[rowoff<L, SP>(lane + R1 * t) + c]; re[t] = v.x; im[t] = v.y; }
+            fft_reg<R2, DIR>(re, im);
+#pragma unroll
+            for (int k = 0; k < R2; ++k) S[rowoff<L, SP>(lane + R1 * k) + c] = mk<T>(re[k], im[k]);
+        }
     }
 }
 

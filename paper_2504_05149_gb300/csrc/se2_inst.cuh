@@ -24,10 +24,16 @@ cudaError_t make_twiddles(c2<T>* tw, int L, cudaStream_t st) {
 template <typename T, int N, int M>
 void fill_fused(KTable<T>* kt) {
     constexpr size_t sm = fused_smem<T, N, M>();
+    kt->persist = nullptr;
+    kt->smem_persist = 0;
     if constexpr (N >= 32 && M >= 8 && sm <= kMaxDynSmem) {
         kt->fwd_xt = k_fwd_xt<T, N, M>;
         kt->inv_tx = k_inv_tx<T, N, M>;
         kt->smem_xt = sm;
+        if constexpr (sizeof(T) == 4) {
+            kt->persist = k_conv_persist<T, N, M>;
+            kt->smem_persist = sm > lines_smem<T, N>() ? sm : lines_smem<T, N>();
+        }
     } else {
         kt->fwd_xt = nullptr;
         kt->inv_tx = nullptr;
@@ -51,6 +57,7 @@ bool fill_n(int M, KTable<T>* kt) {
     kt->teams_x = kThreads / team_size<N>();
     kt->y_conv = k_lines<T, N, LM_CONV>;
     kt->y_coef = k_lines<T, N, LM_COEF>;
+    kt->y_adj = k_lines<T, N, LM_ADJ>;
     kt->smem_y = lines_smem<T, N>();
     kt->lines_y = kThreads / team_size<N>();
     switch (M) {
@@ -61,20 +68,6 @@ bool fill_n(int M, KTable<T>* kt) {
         case 32: fill_fused<T, N, 32>(kt); fill_theta<T, 32>(kt); return true;
         case 64: fill_fused<T, N, 64>(kt); fill_theta<T, 64>(kt); return true;
         case 128: fill_fused<T, N, 128>(kt); fill_theta<T, 128>(kt); return true;
-        default: return false;
-    }
-}
-
-template <typename T>
-bool get_kernels_impl(int N, int M, KTable<T>* kt) {
-    switch (N) {
-        case 8: return fill_n<T, 8>(M, kt);
-        case 16: return fill_n<T, 16>(M, kt);
-        case 32: return fill_n<T, 32>(M, kt);
-        case 64: return fill_n<T, 64>(M, kt);
-        case 128: return fill_n<T, 128>(M, kt);
-        case 256: return fill_n<T, 256>(M, kt);
-        case 512: return fill_n<T, 512>(M, kt);
         default: return false;
     }
 }

@@ -18,18 +18,36 @@ struct KTable {
     size_t smem_xt = 0;
     XK fwd_x = nullptr, inv_x = nullptr;     // split path, x only
     size_t smem_x = 0;
-    LK y_conv = nullptr, y_coef = nullptr;   // lines of length N along y
+    LK y_conv = nullptr, y_coef = nullptr, y_adj = nullptr;   // lines of length N along y
     size_t smem_y = 0;
     int lines_y = 0;                          // lines per block
     LK t_fwd = nullptr, t_inv = nullptr;     // lines of length M along theta
     size_t smem_t = 0;
     int lines_t = 0;
     int teams_x = 0;                          // row pairs per block (split fwd_x/inv_x)
+    using PK = void (*)(PArgs<T>);
+    PK persist = nullptr;                     // persistent convolution (null: three kernels)
+    size_t smem_persist = 0;
 };
 
-// Fills the kernel table for (N, M); false if the size is unsupported.
+// Fills the kernel table for (N, M); false if M is unsupported.  Defined in
+// se2_inst.cuh and instantiated per (T, N) by se2_inst.cu.
+template <typename T, int N>
+bool fill_n(int M, KTable<T>* kt);
+
 template <typename T>
-bool get_kernels(int N, int M, KTable<T>* kt);
+bool get_kernels(int N, int M, KTable<T>* kt) {
+    switch (N) {
+        case 8: return fill_n<T, 8>(M, kt);
+        case 16: return fill_n<T, 16>(M, kt);
+        case 32: return fill_n<T, 32>(M, kt);
+        case 64: return fill_n<T, 64>(M, kt);
+        case 128: return fill_n<T, 128>(M, kt);
+        case 256: return fill_n<T, 256>(M, kt);
+        case 512: return fill_n<T, 512>(M, kt);
+        default: return false;
+    }
+}
 
 // FP64 twiddle generation (sincospi), rounded to T.
 template <typename T>
@@ -37,7 +55,7 @@ cudaError_t make_twiddles(c2<T>* tw, int L, cudaStream_t st);
 
 template <typename T, int N, int M>
 constexpr size_t fused_smem() {
-    return ((size_t)M * slab_pitch<N>() + (size_t)(kThreads / team_size<N>()) * xbuf_elems<N>()) * sizeof(c2<T>);
+    return ((size_t)slab_elems<M, slab_pitch<N>()>() + (size_t)(kThreads / team_size<N>()) * xbuf_elems<N>()) * sizeof(c2<T>);
 }
 template <typename T, int N>
 constexpr size_t xsplit_smem() {

@@ -1,15 +1,19 @@
 // CUDA kernels of the SE(2) convolution path (arXiv 2504.05149, Algorithms
 // 3, 4 and 6 at output grid N = L).  All grids are [theta][y][x], x fastest.
 //
-// Pass structure for one problem (|L| = N*N*M points):
-//   fwd_xt  (per y row):   real FFT along x of the M rows (two rows packed
-//                          as one complex line), then the angular DFT of the
-//                          N/2+1 columns in shared memory  -> scratch S
-//   lines<CONV> (per (theta-bin, x-bin) line): FFT along y, multiply by
-//                          W^k . C_1 ... C_k / |L| (Eq. MatSqKfgG), inverse
-//                          FFT along y, in place in S
-//   inv_tx  (per y row):   inverse angular DFT, then complex-to-real inverse
-//                          FFT along x of row pairs -> out
+// Work units for one problem (|L| = N*N*M points):
+//   A  fwd_xt  (one y row):  real FFT along x of the M rows (two rows packed
+//                            as one complex line), then the angular DFT of the
+//                            N/2+1 columns in shared memory  -> scratch S
+//   B  lines<CONV> (a group of (theta-bin, x-bin) lines): FFT along y,
+//                            multiply by W^k . C_1 ... C_k / |L| (Eq. MatSqKfgG),
+//                            inverse FFT along y, in place in S
+//   C  inv_tx  (one y row):  inverse angular DFT, then complex-to-real inverse
+//                            FFT along x of row pairs -> out
+// They run either as three kernels (one unit per block), or inside one
+// persistent kernel that takes units from a work list and waits (bounded) on
+// per-problem counters, so that problems pipeline through a small ring of
+// scratch slots that stays resident in L2.
 // When the [M][N/2+1] slab of one y row does not fit in shared memory the
 // x and theta steps run as separate passes (fwd_x, lines<FWD> along theta,
 // ..., lines<INV> along theta, inv_x).
@@ -20,14 +24,112 @@ namespace se2 {
 
 constexpr int kThreads = 256;
 constexpr int kMaxChain = 32;
+constexpr int kMaxParams = 4;
 
-enum LineMode { LM_FWD = 0, LM_INV = 1, LM_CONV = 2, LM_COEF = 3 };
+enum LineMode { LM_FWD = 0, LM_INV = 1, LM_CONV = 2, LM_COEF = 3, LM_ADJ = 4 };
 
 // Slab pitch (complex elements) for the [M][N/2+1] slab: = 2 mod 16 so that
 // the 8-lane angular teams of one warp hit distinct bank pairs.
 template <int N> __host__ __device__ constexpr int slab_pitch() {
     constexpr int H = N / 2 + 1;
     return H + ((2 - H % 16) + 16) % 16;
+}
+
+// ---------------------------------------------------------------------------
+// Global-memory access with L2 eviction hints: the scratch spectrum is kept
+// (evict_last), streamed inputs/outputs are let go first (evict_first).
+// Scratch is read through L2 only (.cg): another SM may have written it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t pol_keep() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t pol_stream() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float2 ld_s(const float2* a, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_s(const double2* a, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_s(float2* a, float2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" :: "l"(a), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_s(double2* a, double2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" :: "l"(a), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
+}
+// read-only streamed inputs (never written during a launch)
+__device__ __forceinline__ float ld_in(const float* a, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_in(const double* a, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float2 ld_in(const float2* a, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_in(const double2* a, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_out(float* a, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" :: "l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_out(double* a, double v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" :: "l"(a), "d"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ float4 ld_s4(const float4* a, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_s4(float4* a, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 :: "l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+}
+
+// Copy one slab row of H complex elements between shared memory and the
+// scratch (both 16-byte aligned) with 16-byte accesses, lanes 0..31 of a warp.
+template <typename T, int H>
+__device__ __forceinline__ void row_to_global(c2<T>* g, const c2<T>* sm, int lane, uint64_t pol) {
+    if constexpr (sizeof(c2<T>) == 8) {
+        constexpr int NV = (H - 1) / 2;
+        const float4* sv = reinterpret_cast<const float4*>(sm);
+        float4* gv = reinterpret_cast<float4*>(g);
+        for (int i = lane; i < NV; i += 32) st_s4(gv + i, sv[i], pol);
+        if (lane == 0) st_s(g + (H - 1), sm[H - 1], pol);
+    } else {
+        for (int i = lane; i < H; i += 32) st_s(g + i, sm[i], pol);
+    }
+}
+template <typename T, int H>
+__device__ __forceinline__ void row_from_global(c2<T>* sm, const c2<T>* g, int lane, uint64_t pol) {
+    if constexpr (sizeof(c2<T>) == 8) {
+        constexpr int NV = (H - 1) / 2;
+        float4* sv = reinterpret_cast<float4*>(sm);
+        const float4* gv = reinterpret_cast<const float4*>(g);
+        for (int i = lane; i < NV; i += 32) sv[i] = ld_s4(gv + i, pol);
+        if (lane == 0) sm[H - 1] = ld_s(g + (H - 1), pol);
+    } else {
+        for (int i = lane; i < H; i += 32) sm[i] = ld_s(g + i, pol);
+    }
 }
 
 template <typename T>
@@ -68,27 +170,35 @@ struct LArgs {
     const double* abs_sum;     // [problems] sum |P| or nullptr
     double* log_scale;         // [problems] out or nullptr
     int problem0;              // index of the first problem of this launch (for log_scale)
+    // LM_ADJ: second spectrum (the forward input f), parameter derivatives
+    c2<T>* s2;                 // scratch base of the f spectra (same problem stride)
+    int want_grad;             // write the grad_f spectrum back in place of G
+    int n_params;
+    const c2<T>* dC[kMaxParams];
+    double* grad_params;       // [n_params], accumulated
 };
 
 // ---------------------------------------------------------------------------
-// Forward x (real, packed row pairs) and theta, one y row per block.
+// Unit A: forward x (real, packed row pairs) and theta of y row j.
+// fprob / sprob: this problem's real grid and scratch spectrum.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int M>
-__global__ void __launch_bounds__(kThreads) k_fwd_xt(XArgs<T> a) {
+__device__ __forceinline__ void unit_fwd_xt(const XArgs<T>& a, const T* fprob, c2<T>* sprob, int j,
+                                            double* abs_out, unsigned char* smem_raw, double* red) {
     constexpr int H = N / 2 + 1, SP = slab_pitch<N>();
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
     constexpr int TEAMS = kThreads / TS, XS = xbuf_elems<N>();
     using TO = TeamOut<R1, R2>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     c2<T>* S = reinterpret_cast<c2<T>*>(smem_raw);
-    c2<T>* XB = S + M * SP;
-    __shared__ double red[kThreads / 32];
-
-    const int j = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
-    const T* fb = a.f + b * a.g_pstride + (size_t)j * N;
+    c2<T>* XB = S + slab_elems<M, SP>();
+    const int tid = threadIdx.x;
+    const T* fb = fprob + (size_t)j * N;
     const int team = tid / TS, lane = tid % TS;
     c2<T>* xb = XB + team * XS;
+    const uint64_t pin = pol_stream(), pk = pol_keep();
     T abs_acc = 0;
+    T wr[R1], wi[R1];
+    load_twiddles<N, -1, T>(a.twN, lane, wr, wi);
 
     constexpr int NP = M / 2;
     for (int p0 = 0; p0 < NP; p0 += TEAMS) {
@@ -102,19 +212,24 @@ __global__ void __launch_bounds__(kThreads) k_fwd_xt(XArgs<T> a) {
             const T* r1 = r0 + (size_t)N * N;
 #pragma unroll
             for (int q = 0; q < R1; ++q) {
-                re[q] = __ldg(r0 + lane + R2 * q);
-                im[q] = __ldg(r1 + lane + R2 * q);
-                abs_acc += fabs(re[q]) + fabs(im[q]);
+                re[q] = ld_in(r0 + lane + R2 * q, pin);
+                im[q] = ld_in(r1 + lane + R2 * q, pin);
+            }
+            if (abs_out != nullptr) {
+#pragma unroll
+                for (int q = 0; q < R1; ++q) abs_acc += fabs(re[q]) + fabs(im[q]);
             }
         }
-        team_fft<R1, R2, -1, T>(re, im, lane, xb, a.twN, SyncWarp());
-        // lane s < R1 holds Z[s + R1 k]; publish Z linearly to split the pair
+        team_fft_r<R1, R2, -1, T>(re, im, lane, xb, wr, wi, SyncWarp());
+        // lane holds Z at TO::idx; publish Z linearly to split the pair
         if (lane < TO::lanes) {
 #pragma unroll
             for (int k = 0; k < TO::regs; ++k) xb[TO::idx(lane, k)] = mk<T>(re[k], im[k]);
         }
         __syncwarp();
         if (act && lane < TO::lanes) {
+            c2<T>* s0 = S + rowoff<M, SP>(2 * p);
+            c2<T>* s1 = S + rowoff<M, SP>(2 * p + 1);
 #pragma unroll
             for (int k2 = 0; k2 < TO::regs; ++k2) {
                 const int kk = TO::idx(lane, k2);
@@ -122,75 +237,82 @@ __global__ void __launch_bounds__(kThreads) k_fwd_xt(XArgs<T> a) {
                     const c2<T> zm = xb[(N - kk) & (N - 1)];
                     const T zr = re[k2], zi = im[k2];
                     // X0 = (Z[k] + conj Z[N-k]) / 2, X1 = (Z[k] - conj Z[N-k]) / (2i)
-                    S[(2 * p) * SP + kk] = mk<T>((zr + zm.x) * (T)0.5, (zi - zm.y) * (T)0.5);
-                    S[(2 * p + 1) * SP + kk] = mk<T>((zi + zm.y) * (T)0.5, (zm.x - zr) * (T)0.5);
+                    s0[kk] = mk<T>((zr + zm.x) * (T)0.5, (zi - zm.y) * (T)0.5);
+                    s1[kk] = mk<T>((zi + zm.y) * (T)0.5, (zm.x - zr) * (T)0.5);
                 }
             }
         }
         __syncwarp();
     }
-    if (a.abs_sum != nullptr) {
+    if (abs_out != nullptr) {
         double v = (double)abs_acc;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((tid & 31) == 0) red[tid >> 5] = v;
     }
     __syncthreads();
-    if (a.abs_sum != nullptr && tid == 0) {
+    if (abs_out != nullptr && tid == 0) {
         double v = 0;
         for (int w = 0; w < kThreads / 32; ++w) v += red[w];
-        atomicAdd(a.abs_sum + b, v);
+        atomicAdd(abs_out, v);
     }
-    // angular DFT of the H columns
     {
         constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
         const int tm = tid / TSM, lm = tid % TSM;
+        T vr[Fac<M>::R1], vi[Fac<M>::R1];
+        load_twiddles<M, -1, T>(a.twM, lm, vr, vi);
         for (int c0 = 0; c0 < H; c0 += TEAMSM) {
             const int c = c0 + tm;
             const bool act = c < H;
-            column_fft<M, -1, T>(S + (act ? c : 0), SP, lm, act, a.twM, SyncWarp());
+            column_fft_r<M, SP, -1, T>(S, act ? c : 0, lm, act, vr, vi, SyncWarp());
         }
     }
     __syncthreads();
-    c2<T>* sb = a.s + b * a.s_pstride + (size_t)j * a.tp;
-    for (int e = tid; e < M * H; e += kThreads) {
-        const int r = e / H, k = e - r * H;
-        sb[(size_t)r * N * a.tp + k] = S[r * SP + k];
+    {
+        const int w = tid >> 5, l32 = tid & 31;
+        c2<T>* sb = sprob + (size_t)j * a.tp;
+        for (int r = w; r < M; r += kThreads / 32)
+            row_to_global<T, H>(sb + (size_t)r * N * a.tp, S + rowoff<M, SP>(r), l32, pk);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Inverse theta then complex-to-real x, one y row per block.
+// Unit C: inverse theta then complex-to-real x of y row j.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int M>
-__global__ void __launch_bounds__(kThreads) k_inv_tx(XArgs<T> a) {
+__device__ __forceinline__ void unit_inv_tx(const XArgs<T>& a, const c2<T>* sprob, T* oprob, int j,
+                                            unsigned char* smem_raw) {
     constexpr int H = N / 2 + 1, SP = slab_pitch<N>();
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
     constexpr int TEAMS = kThreads / TS, XS = xbuf_elems<N>();
     using TO = TeamOut<R1, R2>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     c2<T>* S = reinterpret_cast<c2<T>*>(smem_raw);
-    c2<T>* XB = S + M * SP;
-
-    const int j = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
-    const c2<T>* sb = a.s + b * a.s_pstride + (size_t)j * a.tp;
-    for (int e = tid; e < M * H; e += kThreads) {
-        const int r = e / H, k = e - r * H;
-        S[r * SP + k] = sb[(size_t)r * N * a.tp + k];
+    c2<T>* XB = S + slab_elems<M, SP>();
+    const int tid = threadIdx.x;
+    const uint64_t pk = pol_keep(), po = pol_stream();
+    {
+        const int w = tid >> 5, l32 = tid & 31;
+        const c2<T>* sb = sprob + (size_t)j * a.tp;
+        for (int r = w; r < M; r += kThreads / 32)
+            row_from_global<T, H>(S + rowoff<M, SP>(r), sb + (size_t)r * N * a.tp, l32, pk);
     }
     __syncthreads();
     {
         constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
         const int tm = tid / TSM, lm = tid % TSM;
+        T vr[Fac<M>::R1], vi[Fac<M>::R1];
+        load_twiddles<M, +1, T>(a.twM, lm, vr, vi);
         for (int c0 = 0; c0 < H; c0 += TEAMSM) {
             const int c = c0 + tm;
             const bool act = c < H;
-            column_fft<M, +1, T>(S + (act ? c : 0), SP, lm, act, a.twM, SyncWarp());
+            column_fft_r<M, SP, +1, T>(S, act ? c : 0, lm, act, vr, vi, SyncWarp());
         }
     }
     __syncthreads();
     const int team = tid / TS, lane = tid % TS;
     c2<T>* xb = XB + team * XS;
-    T* ob = a.out + b * a.g_pstride + (size_t)j * N;
+    T* ob = oprob + (size_t)j * N;
+    T wr[R1], wi[R1];
+    load_twiddles<N, +1, T>(a.twN, lane, wr, wi);
     constexpr int NP = M / 2;
     for (int p0 = 0; p0 < NP; p0 += TEAMS) {
         const int p = p0 + team;
@@ -199,8 +321,8 @@ __global__ void __launch_bounds__(kThreads) k_inv_tx(XArgs<T> a) {
 #pragma unroll
         for (int i = 0; i < RM; ++i) { re[i] = 0; im[i] = 0; }
         if (act && lane < R2) {
-            const c2<T>* s0 = S + (2 * p) * SP;
-            const c2<T>* s1 = s0 + SP;
+            const c2<T>* s0 = S + rowoff<M, SP>(2 * p);
+            const c2<T>* s1 = S + rowoff<M, SP>(2 * p + 1);
 #pragma unroll
             for (int q = 0; q < R1; ++q) {
                 const int kk = lane + R2 * q;
@@ -219,16 +341,299 @@ __global__ void __launch_bounds__(kThreads) k_inv_tx(XArgs<T> a) {
                 im[q] = A.y + B.x;
             }
         }
-        team_fft<R1, R2, +1, T>(re, im, lane, xb, a.twN, SyncWarp());
+        team_fft_r<R1, R2, +1, T>(re, im, lane, xb, wr, wi, SyncWarp());
         if (act && lane < TO::lanes) {
             T* o0 = ob + (size_t)(2 * p) * N * N;
             T* o1 = o0 + (size_t)N * N;
 #pragma unroll
             for (int k = 0; k < TO::regs; ++k) {
-                o0[TO::idx(lane, k)] = re[k];
-                o1[TO::idx(lane, k)] = im[k];
+                st_out(o0 + TO::idx(lane, k), re[k], po);
+                st_out(o1 + TO::idx(lane, k), im[k], po);
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Unit B (and the split-path theta passes): FFTs of length L along one axis
+// of the scratch spectrum for LINES consecutive lines (outer index o, x bin
+// kx; kx fastest for coalescing) starting at line g * LINES.
+//   LM_FWD / LM_INV: forward / unscaled inverse FFT in place
+//   LM_CONV (y axis): forward, multiply by W^k C_1..C_k exp(sum ls) / |L|,
+//                     inverse, in place
+//   LM_COEF (y axis): forward, scale by 1 / (|L| s_b), write the external
+//                     coefficient layout
+// b is the problem index used for C / log_scale / coefficient output.
+// ---------------------------------------------------------------------------
+template <typename T, int L, int MODE>
+__device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int b, long long g,
+                                           unsigned char* smem_raw, double* sh_scale,
+                                           c2<T>* sprob2 = nullptr, double* red = nullptr) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2, TS = team_size<L>(), RM = reg_count<L>();
+    constexpr int LINES = kThreads / TS;
+    constexpr int XS = (Fac<L>::R1 * (Fac<L>::R2 + 1)) | 1;   // odd stride: lines in distinct banks
+    using TO = TeamOut<R1, R2>;
+    c2<T>* XB = reinterpret_cast<c2<T>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int c = tid % LINES, t = tid / LINES;
+    const long long NR = (long long)a.n_outer * a.nk;
+    const long long total = NR + a.n_outer;
+    const long long line = g * LINES + c;
+    const bool act = line < total;
+    int o, kx;
+    if (line < NR) { o = (int)(line / a.nk); kx = (int)(line - (long long)o * a.nk); }
+    else { o = act ? (int)(line - NR) : 0; kx = a.nk; }
+    c2<T>* base = sprob + o * a.outer_stride + kx;
+    c2<T>* xb = XB + c * XS;
+    const uint64_t pk = pol_keep();
+
+    if constexpr (MODE == LM_CONV || MODE == LM_COEF || MODE == LM_ADJ) {
+        if (tid == 0) {
+            double sc = a.inv_L;
+            if constexpr (MODE == LM_CONV || MODE == LM_ADJ) {
+                double lsum = 0;
+                for (int i = 0; i < a.k; ++i)
+                    if (a.ls[i] != nullptr) lsum += a.ls[i][b * a.ls_pstride];
+                sc *= exp(lsum);
+            } else {
+                if (a.abs_sum != nullptr) {
+                    const double s = a.abs_sum[b] * a.inv_L;   // mean |P|
+                    double lg = 0;
+                    if (s > 0) { sc /= s; lg = log(s); }
+                    if (g == 0 && a.log_scale != nullptr) a.log_scale[a.problem0 + b] = lg;
+                }
+            }
+            *sh_scale = sc;
+        }
+        __syncthreads();
+    }
+
+    T re[RM], im[RM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i) { re[i] = 0; im[i] = 0; }
+    if (act && t < R2) {
+#pragma unroll
+        for (int q = 0; q < R1; ++q) {
+            const c2<T> v = ld_s(base + (long long)(t + R2 * q) * a.elem_stride, pk);
+            re[q] = v.x;
+            im[q] = v.y;
+        }
+    }
+    if constexpr (MODE == LM_INV) {
+        team_fft<R1, R2, +1, T>(re, im, t, xb, a.tw, SyncBlock());
+    } else {
+        team_fft<R1, R2, -1, T>(re, im, t, xb, a.tw, SyncBlock());
+    }
+    // lane t < TO::lanes now holds X[TO::idx(t, k)], k < TO::regs
+    if constexpr (MODE == LM_FWD || MODE == LM_INV) {
+        if (act && t < TO::lanes) {
+#pragma unroll
+            for (int k = 0; k < TO::regs; ++k) st_s(base + (long long)TO::idx(t, k) * a.elem_stride, mk<T>(re[k], im[k]), pk);
+        }
+    } else if constexpr (MODE == LM_COEF) {
+        if (act && t < TO::lanes) {
+            const T sc = (T)*sh_scale;
+            c2<T>* cb = a.cout + b * a.cout_pstride + (long long)o * a.N * a.cp + kx;
+#pragma unroll
+            for (int k = 0; k < TO::regs; ++k) cb[(long long)TO::idx(t, k) * a.cp] = mk<T>(re[k] * sc, im[k] * sc);
+        }
+    } else if constexpr (MODE == LM_ADJ) {
+        // transpose of the convolution (grad_f spectrum W conj(C) G^ e^{ls} / |L|)
+        // and kernel-parameter partials (1/|L|) sum_k m_k Re(W dC_i conj(G^) F^)
+        const uint64_t pin = pol_stream();
+        T fr[RM], fi[RM];
+        if (a.n_params > 0) {
+#pragma unroll
+            for (int i = 0; i < RM; ++i) { fr[i] = 0; fi[i] = 0; }
+            c2<T>* base2 = sprob2 + o * a.outer_stride + kx;
+            if (act && t < R2) {
+#pragma unroll
+                for (int q = 0; q < R1; ++q) {
+                    const c2<T> v = ld_s(base2 + (long long)(t + R2 * q) * a.elem_stride, pk);
+                    fr[q] = v.x;
+                    fi[q] = v.y;
+                }
+            }
+            team_fft<R1, R2, -1, T>(fr, fi, t, xb, a.tw, SyncBlock());
+        }
+        T acc[kMaxParams];
+#pragma unroll
+        for (int i = 0; i < kMaxParams; ++i) acc[i] = 0;
+        if (act && t < TO::lanes) {
+            const T sc = (T)*sh_scale;
+            const long long coff = (long long)o * a.N * a.cp + kx;
+            const T mk_ = (kx == 0 || kx == a.nk) ? (T)1 : (T)2;
+#pragma unroll
+            for (int k = 0; k < TO::regs; ++k) {
+                const int ky = TO::idx(t, k);
+                const T w = ((kx + ky) & 1) ? (T)-1 : (T)1;
+                const long long ci = coff + (long long)ky * a.cp;
+                if (a.n_params > 0) {
+                    // conj(G^) F^
+                    const T pr = re[k] * fr[k] + im[k] * fi[k];
+                    const T pi = re[k] * fi[k] - im[k] * fr[k];
+#pragma unroll
+                    for (int i = 0; i < kMaxParams; ++i) {
+                        if (i < a.n_params) {
+                            const c2<T> d = ld_in(a.dC[i] + b * a.c_pstride + ci, pin);
+                            acc[i] += mk_ * w * (d.x * pr - d.y * pi);
+                        }
+                    }
+                }
+                if (a.want_grad) {
+                    const c2<T> cv = ld_in(a.C[0] + b * a.c_pstride + ci, pin);
+                    // W conj(C) G^ * scale
+                    const T xr = (cv.x * re[k] + cv.y * im[k]) * sc * w;
+                    const T xi = (cv.x * im[k] - cv.y * re[k]) * sc * w;
+                    re[k] = xr;
+                    im[k] = xi;
+                }
+            }
+        }
+        if (a.n_params > 0) {
+            // block reduction of the partial sums (FP64), one atomic per parameter
+            for (int i = 0; i < a.n_params; ++i) {
+                double v = (double)acc[i];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if ((tid & 31) == 0) red[tid >> 5] = v;
+                __syncthreads();
+                if (tid == 0) {
+                    double tsum = 0;
+                    for (int w_ = 0; w_ < kThreads / 32; ++w_) tsum += red[w_];
+                    atomicAdd(a.grad_params + i, tsum * a.inv_L);
+                }
+                __syncthreads();
+            }
+        }
+        if (a.want_grad) {
+            if constexpr (R2 == 1) {
+                fft_reg<R1, +1>(re, im);
+                if (act) {
+#pragma unroll
+                    for (int q = 0; q < R1; ++q) st_s(base + (long long)q * a.elem_stride, mk<T>(re[q], im[q]), pk);
+                }
+            } else {
+                team_fft<R2, R1, +1, T>(re, im, t, xb, a.tw, SyncBlock());
+                if (act && t < R2) {
+#pragma unroll
+                    for (int q = 0; q < R1; ++q) st_s(base + (long long)(t + R2 * q) * a.elem_stride, mk<T>(re[q], im[q]), pk);
+                }
+            }
+        }
+    } else {  // LM_CONV
+        const uint64_t pin = pol_stream();
+        if (act && t < TO::lanes) {
+            const T sc = (T)*sh_scale;
+            const long long coff = (long long)o * a.N * a.cp + kx;
+#pragma unroll
+            for (int k = 0; k < TO::regs; ++k) {
+                const int ky = TO::idx(t, k);
+                T xr = re[k] * sc, xi = im[k] * sc;
+                for (int i = 0; i < a.k; ++i) {
+                    const c2<T> cv = ld_in(a.C[i] + b * a.c_pstride + coff + (long long)ky * a.cp, pin);
+                    const T r = xr * cv.x - xi * cv.y;
+                    xi = xr * cv.y + xi * cv.x;
+                    xr = r;
+                }
+                if ((a.k & 1) && ((kx + ky) & 1)) { xr = -xr; xi = -xi; }   // W^k
+                re[k] = xr;
+                im[k] = xi;
+            }
+        }
+        if constexpr (R2 == 1) {
+            fft_reg<R1, +1>(re, im);       // one lane holds the whole line
+            if (act) {
+#pragma unroll
+                for (int q = 0; q < R1; ++q) st_s(base + (long long)q * a.elem_stride, mk<T>(re[q], im[q]), pk);
+            }
+        } else {
+            // the transposed factorisation maps lane t back to x[t + R2 n]
+            team_fft<R2, R1, +1, T>(re, im, t, xb, a.tw, SyncBlock());
+            if (act && t < R2) {
+#pragma unroll
+                for (int q = 0; q < R1; ++q) st_s(base + (long long)(t + R2 * q) * a.elem_stride, mk<T>(re[q], im[q]), pk);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One-unit-per-block kernels
+// ---------------------------------------------------------------------------
+template <typename T, int N, int M>
+__global__ void __launch_bounds__(kThreads) k_fwd_xt(XArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kThreads / 32];
+    const int b = blockIdx.y;
+    unit_fwd_xt<T, N, M>(a, a.f + b * a.g_pstride, a.s + b * a.s_pstride, blockIdx.x,
+                         a.abs_sum ? a.abs_sum + b : nullptr, smem_raw, red);
+}
+
+template <typename T, int N, int M>
+__global__ void __launch_bounds__(kThreads) k_inv_tx(XArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = blockIdx.y;
+    unit_inv_tx<T, N, M>(a, a.s + b * a.s_pstride, a.out + b * a.g_pstride, blockIdx.x, smem_raw);
+}
+
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(kThreads) k_lines(LArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sh_scale;
+    __shared__ double red[kThreads / 32];
+    const int b = blockIdx.y;
+    unit_lines<T, L, MODE>(a, a.s + b * a.s_pstride, b, blockIdx.x, smem_raw, &sh_scale,
+                           a.s2 ? a.s2 + b * a.s_pstride : nullptr, red);
+}
+
+// ---------------------------------------------------------------------------
+// Radial kernel family for differentiation: Gaussian of width sigma in x, y
+// (normalised over R^2, periodised over the lattice, images |n| <= 2) times
+// 2 pi times a wrapped normal of width sigma_t centred at nu (|m| <= 4), on
+// Omega_L; plus the derivatives in sigma and sigma_t.  The 1-D factors are
+// computed in FP64 (tables: gx, dgx [N], gt, dgt [M]), then multiplied out.
+// ---------------------------------------------------------------------------
+static __global__ void k_gauss_tables(double* tab, int N, int M, double sigma, double sigma_t, double nu) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double PI = 3.14159265358979323846;
+    if (i < N) {
+        const double d = -0.5 + (double)i / N;              // x_i, already in [-1/2, 1/2)
+        double g = 0, dg = 0;
+        for (int n = -2; n <= 2; ++n) {
+            const double u2 = (d + n) * (d + n);
+            const double e = exp(-u2 / (2 * sigma * sigma));
+            g += e;
+            dg += e * (-1.0 / (sigma * sigma) + u2 / (sigma * sigma * sigma * sigma));
+        }
+        tab[i] = g / (sqrt(2 * PI) * sigma);
+        tab[N + i] = dg / sqrt(2 * PI);
+    } else if (i < N + M) {
+        const int l = i - N;
+        double v = 2 * PI * l / M - nu + PI;
+        v = v - 2 * PI * floor(v / (2 * PI)) - PI;          // [-pi, pi)
+        double t = 0, dt = 0;
+        for (int m = -4; m <= 4; ++m) {
+            const double v2 = (v + 2 * PI * m) * (v + 2 * PI * m);
+            const double e = exp(-v2 / (2 * sigma_t * sigma_t));
+            t += e;
+            dt += e * (-1.0 / (sigma_t * sigma_t) + v2 / (sigma_t * sigma_t * sigma_t * sigma_t));
+        }
+        tab[2 * N + l] = t * sqrt(2 * PI) / sigma_t;
+        tab[2 * N + M + l] = dt * sqrt(2 * PI);
+    }
+}
+
+template <typename T>
+__global__ void k_gauss_fill(const double* tab, int N, int M, T* P, T* dPs, T* dPt) {
+    const long long total = (long long)M * N * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % N), j = (int)((e / N) % N), l = (int)(e / ((long long)N * N));
+        const double gx = tab[i], gy = tab[j], dgx = tab[N + i], dgy = tab[N + j];
+        const double gt = tab[2 * N + l], dgt = tab[2 * N + M + l];
+        if (P) P[e] = (T)(gt * gy * gx);
+        if (dPs) dPs[e] = (T)(gt * (dgy * gx + gy * dgx));
+        if (dPt) dPt[e] = (T)(dgt * gy * gx);
     }
 }
 
@@ -250,6 +655,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_x(XArgs<T> a) {
     const bool act = p < a.M / 2;
     c2<T>* xb = XB + team * XS;
     const T* fb = a.f + b * a.g_pstride + (size_t)j * N;
+    const uint64_t pin = pol_stream(), pk = pol_keep();
     T re[RM], im[RM];
     T abs_acc = 0;
 #pragma unroll
@@ -259,8 +665,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_x(XArgs<T> a) {
         const T* r1 = r0 + (size_t)N * N;
 #pragma unroll
         for (int q = 0; q < R1; ++q) {
-            re[q] = __ldg(r0 + lane + R2 * q);
-            im[q] = __ldg(r1 + lane + R2 * q);
+            re[q] = ld_in(r0 + lane + R2 * q, pin);
+            im[q] = ld_in(r1 + lane + R2 * q, pin);
             abs_acc += fabs(re[q]) + fabs(im[q]);
         }
     }
@@ -279,8 +685,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_x(XArgs<T> a) {
             if (kk <= N / 2) {
                 const c2<T> zm = xb[(N - kk) & (N - 1)];
                 const T zr = re[k2], zi = im[k2];
-                s0[kk] = mk<T>((zr + zm.x) * (T)0.5, (zi - zm.y) * (T)0.5);
-                s1[kk] = mk<T>((zi + zm.y) * (T)0.5, (zm.x - zr) * (T)0.5);
+                st_s(s0 + kk, mk<T>((zr + zm.x) * (T)0.5, (zi - zm.y) * (T)0.5), pk);
+                st_s(s1 + kk, mk<T>((zi + zm.y) * (T)0.5, (zm.x - zr) * (T)0.5), pk);
             }
         }
     }
@@ -309,6 +715,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_x(XArgs<T> a) {
     const int p = blockIdx.y * TEAMS + team;
     const bool act = p < a.M / 2;
     c2<T>* xb = XB + team * XS;
+    const uint64_t pk = pol_keep(), po = pol_stream();
     T re[RM], im[RM];
 #pragma unroll
     for (int i = 0; i < RM; ++i) { re[i] = 0; im[i] = 0; }
@@ -320,12 +727,12 @@ __global__ void __launch_bounds__(kThreads) k_inv_x(XArgs<T> a) {
             const int kk = lane + R2 * q;
             c2<T> A, B;
             if (kk <= N / 2) {
-                A = s0[kk];
-                B = s1[kk];
+                A = ld_s(s0 + kk, pk);
+                B = ld_s(s1 + kk, pk);
                 if (kk == 0 || kk == N / 2) { A.y = 0; B.y = 0; }
             } else {
-                A = s0[N - kk];
-                B = s1[N - kk];
+                A = ld_s(s0 + N - kk, pk);
+                B = ld_s(s1 + N - kk, pk);
                 A.y = -A.y;
                 B.y = -B.y;
             }
@@ -339,126 +746,161 @@ __global__ void __launch_bounds__(kThreads) k_inv_x(XArgs<T> a) {
         T* o1 = o0 + (size_t)N * N;
 #pragma unroll
         for (int k = 0; k < TO::regs; ++k) {
-            o0[TO::idx(lane, k)] = re[k];
-            o1[TO::idx(lane, k)] = im[k];
+            st_out(o0 + TO::idx(lane, k), re[k], po);
+            st_out(o1 + TO::idx(lane, k), im[k], po);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Line pass: FFTs of length L along one axis of the scratch spectrum, for
-// all lines (outer index o, x bin kx), kx fastest for coalescing.
-//   LM_FWD / LM_INV: forward / unscaled inverse FFT in place
-//   LM_CONV (y axis): forward, multiply by W^k C_1..C_k exp(sum ls) / |L|,
-//                     inverse, in place
-//   LM_COEF (y axis): forward, scale by 1 / (|L| s_b), write the external
-//                     coefficient layout
-// grid = (ceil(lines / LINES), problems)
+// Persistent convolution kernel: all units of all B problems of one call.
+// Work list in rounds r = 0 .. B+2: round r holds A(r), then C(r-3), then
+// B(r-1) (for the problems that exist), so a unit's inputs were produced
+// about a round earlier.  Problem p uses scratch slot p % D (D = 4).
+// Dependencies (waited on by the unit's thread 0, bounded):
+//   B(p) needs all nA units A(p); C(p) needs all nB units B(p);
+//   A(p), p >= D, needs all nC units C(p - D) (its slot is then free).
+// Units are taken in list order from an atomic counter and every unit only
+// waits on units earlier in the list, which were taken by running blocks, so
+// the waits end.  A wait longer than `spin_limit` polls sets err = 1; then
+// every block stops taking units and the kernel returns.
+// Thread 0 fetches the next list index and that unit's dependency counter
+// one unit ahead, so their latency overlaps the current unit's work.
 // ---------------------------------------------------------------------------
-template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(kThreads) k_lines(LArgs<T> a) {
-    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2, TS = team_size<L>(), RM = reg_count<L>();
-    constexpr int LINES = kThreads / TS;
-    constexpr int XS = (Fac<L>::R1 * (Fac<L>::R2 + 1)) | 1;   // odd stride: lines in distinct banks
+template <typename T>
+struct PArgs {
+    XArgs<T> x;
+    LArgs<T> l;
+    int B;                     // problems in this launch
+    int D;                     // scratch slots
+    int nA, nB, nC;            // units per stage per problem
+    unsigned* work;            // [1] next unit
+    unsigned* cnt;             // [3 * B] completed units per (stage, problem)
+    int* err;                  // device error word (0 = ok), sticky until read by the host
+    long long spin_limit;      // polls before a wait gives up
+    unsigned dep_extra;        // added to the A->B wait target; nonzero only to test the timeout path
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Map a work-list index to (stage 0=A,1=B,2=C, problem, unit); false if past the end.
+__device__ __forceinline__ bool decode_unit(unsigned g, int B, int nA, int nB, int nC,
+                                            int& stage, int& p, int& u) {
+    long long rem = g;
+    const long long full = (long long)nA + nB + nC;
+    for (int r = 0; r < B + 3; ++r) {
+        if (r >= 3 && r <= B - 1) {            // full rounds r .. B-1: skip whole ones
+            const long long nfull = (long long)B - r;
+            long long skip = rem / full;
+            if (skip > nfull - 1) skip = nfull - 1;
+            r += (int)skip;
+            rem -= skip * full;
+        }
+        const bool ha = r < B, hc = r >= 3 && r <= B + 2, hb = r >= 1 && r <= B;
+        if (ha) { if (rem < nA) { stage = 0; p = r; u = (int)rem; return true; } rem -= nA; }
+        if (hc) { if (rem < nC) { stage = 2; p = r - 3; u = (int)rem; return true; } rem -= nC; }
+        if (hb) { if (rem < nB) { stage = 1; p = r - 1; u = (int)rem; return true; } rem -= nB; }
+    }
+    return false;
+}
+
+// Dependency of a unit: counter and target (dep = nullptr: none).
+template <typename T>
+__device__ __forceinline__ const unsigned* unit_dep(const PArgs<T>& a, int stage, int p, unsigned& target) {
+    if (stage == 1) { target = (unsigned)a.nA + a.dep_extra; return a.cnt + p; }
+    if (stage == 2) { target = (unsigned)a.nB; return a.cnt + a.B + p; }
+    if (p >= a.D) { target = (unsigned)a.nC; return a.cnt + 2 * a.B + (p - a.D); }
+    return nullptr;
+}
+
+template <typename T, int N, int M>
+__global__ void __launch_bounds__(kThreads) k_conv_persist(PArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    c2<T>* XB = reinterpret_cast<c2<T>*>(smem_raw);
+    __shared__ double red[kThreads / 32];
     __shared__ double sh_scale;
-
-    const int b = blockIdx.y, tid = threadIdx.x;
-    const int c = tid % LINES, t = tid / LINES;
-    const long long NR = (long long)a.n_outer * a.nk;
-    const long long total = NR + a.n_outer;
-    const long long line = (long long)blockIdx.x * LINES + c;
-    const bool act = line < total;
-    int o, kx;
-    if (line < NR) { o = (int)(line / a.nk); kx = (int)(line - (long long)o * a.nk); }
-    else { o = act ? (int)(line - NR) : 0; kx = a.nk; }
-    c2<T>* base = a.s + b * a.s_pstride + o * a.outer_stride + kx;
-    c2<T>* xb = XB + c * XS;
-
-    if constexpr (MODE == LM_CONV || MODE == LM_COEF) {
+    __shared__ int sh_unit[3];
+    const int tid = threadIdx.x;
+    // thread-0 pipeline state: the current unit, its early dependency read,
+    // and the list index of the next unit (atomic in flight)
+    int cs = -1, cp = 0, cu = 0;
+    unsigned cv = 0, g_next = 0;
+    if (tid == 0) {
+        const unsigned g0 = atomicAdd(a.work, 1u);
+        g_next = atomicAdd(a.work, 1u);
+        if (decode_unit(g0, a.B, a.nA, a.nB, a.nC, cs, cp, cu)) {
+            unsigned tg;
+            const unsigned* d = unit_dep(a, cs, cp, tg);
+            cv = d ? ld_relaxed(d) : 0u;
+        } else {
+            cs = -1;
+        }
+    }
+    for (;;) {
+        int ns = -1, np = 0, nu = 0;
+        unsigned nv = 0;
         if (tid == 0) {
-            double sc = a.inv_L;
-            if constexpr (MODE == LM_CONV) {
-                double lsum = 0;
-                for (int i = 0; i < a.k; ++i)
-                    if (a.ls[i] != nullptr) lsum += a.ls[i][b * a.ls_pstride];
-                sc *= exp(lsum);
-            } else {
-                if (a.abs_sum != nullptr) {
-                    const double s = a.abs_sum[b] * a.inv_L;   // mean |P|
-                    double lg = 0;
-                    if (s > 0) { sc /= s; lg = log(s); }
-                    if (blockIdx.x == 0 && a.log_scale != nullptr) a.log_scale[a.problem0 + b] = lg;
+            int stage = cs;
+            if (stage >= 0 && *(volatile int*)a.err != 0) stage = -1;
+            if (stage >= 0) {
+                unsigned target = 0;
+                const unsigned* dep = unit_dep(a, cs, cp, target);
+                if (dep != nullptr) {
+                    if (cv >= target) {
+                        __threadfence();        // the early relaxed read, upgraded to acquire
+                    } else {
+                        long long it = 0;
+                        while (ld_acquire(dep) < target) {
+                            if (++it > a.spin_limit || *(volatile int*)a.err != 0) {
+                                atomicCAS(a.err, 0, 1);
+                                stage = -1;
+                                break;
+                            }
+                            __nanosleep(64);
+                        }
+                    }
                 }
             }
-            sh_scale = sc;
+            sh_unit[0] = stage;
+            sh_unit[1] = cp;
+            sh_unit[2] = cu;
+            if (stage >= 0) {
+                // look one unit ahead
+                if (decode_unit(g_next, a.B, a.nA, a.nB, a.nC, ns, np, nu)) {
+                    g_next = atomicAdd(a.work, 1u);
+                    unsigned tg;
+                    const unsigned* d = unit_dep(a, ns, np, tg);
+                    nv = d ? ld_relaxed(d) : 0u;
+                } else {
+                    ns = -1;
+                }
+            }
         }
         __syncthreads();
-    }
-
-    T re[RM], im[RM];
-#pragma unroll
-    for (int i = 0; i < RM; ++i) { re[i] = 0; im[i] = 0; }
-    if (act && t < R2) {
-#pragma unroll
-        for (int q = 0; q < R1; ++q) {
-            const c2<T> v = base[(long long)(t + R2 * q) * a.elem_stride];
-            re[q] = v.x;
-            im[q] = v.y;
-        }
-    }
-    if constexpr (MODE == LM_INV) {
-        team_fft<R1, R2, +1, T>(re, im, t, xb, a.tw, SyncBlock());
-    } else {
-        team_fft<R1, R2, -1, T>(re, im, t, xb, a.tw, SyncBlock());
-    }
-    // lane t < TO::lanes now holds X[TO::idx(t, k)], k < TO::regs
-    using TO = TeamOut<R1, R2>;
-    if constexpr (MODE == LM_FWD || MODE == LM_INV) {
-        if (act && t < TO::lanes) {
-#pragma unroll
-            for (int k = 0; k < TO::regs; ++k) base[(long long)TO::idx(t, k) * a.elem_stride] = mk<T>(re[k], im[k]);
-        }
-    } else if constexpr (MODE == LM_COEF) {
-        if (act && t < TO::lanes) {
-            const T sc = (T)sh_scale;
-            c2<T>* cb = a.cout + b * a.cout_pstride + (long long)o * a.N * a.cp + kx;
-#pragma unroll
-            for (int k = 0; k < TO::regs; ++k) cb[(long long)TO::idx(t, k) * a.cp] = mk<T>(re[k] * sc, im[k] * sc);
-        }
-    } else {  // LM_CONV
-        if (act && t < TO::lanes) {
-            const T sc = (T)sh_scale;
-            const long long coff = (long long)o * a.N * a.cp + kx;
-#pragma unroll
-            for (int k = 0; k < TO::regs; ++k) {
-                const int ky = TO::idx(t, k);
-                T xr = re[k] * sc, xi = im[k] * sc;
-                for (int i = 0; i < a.k; ++i) {
-                    const c2<T> cv = a.C[i][b * a.c_pstride + coff + (long long)ky * a.cp];
-                    const T r = xr * cv.x - xi * cv.y;
-                    xi = xr * cv.y + xi * cv.x;
-                    xr = r;
-                }
-                if ((a.k & 1) && ((kx + ky) & 1)) { xr = -xr; xi = -xi; }   // W^k
-                re[k] = xr;
-                im[k] = xi;
-            }
-        }
-        if constexpr (R2 == 1) {
-            fft_reg<R1, +1>(re, im);       // one lane holds the whole line
-            if (act) {
-#pragma unroll
-                for (int q = 0; q < R1; ++q) base[(long long)q * a.elem_stride] = mk<T>(re[q], im[q]);
-            }
+        const int stage = sh_unit[0], p = sh_unit[1], u = sh_unit[2];
+        __syncthreads();     // everyone has read sh_unit before it is rewritten
+        if (stage < 0) break;
+        c2<T>* sprob = a.x.s + (size_t)(p % a.D) * a.x.s_pstride;
+        if (stage == 0) {
+            unit_fwd_xt<T, N, M>(a.x, a.x.f + p * a.x.g_pstride, sprob, u, nullptr, smem_raw, red);
+        } else if (stage == 1) {
+            unit_lines<T, N, LM_CONV>(a.l, sprob, p, u, smem_raw, &sh_scale);
         } else {
-            // the transposed factorisation maps lane t back to x[t + R2 n]
-            team_fft<R2, R1, +1, T>(re, im, t, xb, a.tw, SyncBlock());
-            if (act && t < R2) {
-#pragma unroll
-                for (int q = 0; q < R1; ++q) base[(long long)(t + R2 * q) * a.elem_stride] = mk<T>(re[q], im[q]);
-            }
+            unit_inv_tx<T, N, M>(a.x, sprob, a.x.out + p * a.x.g_pstride, u, smem_raw);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(a.cnt + stage * a.B + p, 1u);
+            cs = ns; cp = np; cu = nu; cv = nv;
         }
     }
 }

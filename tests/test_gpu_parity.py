@@ -231,3 +231,38 @@ def test_invalid_arguments_on_gpu_plan(se2):
     assert st == 1
     with pytest.raises(ValueError):
         se2.convolve(plan, f[:1].double(), C[:1])
+
+
+def test_persistent_and_three_kernel_paths_agree(se2):
+    """The persistent dataflow kernel (default for FP32 fused sizes) and the
+    three-kernel sequence give the oracle's result on B = 7 problems (more
+    than the 3 scratch slots, so slots are reused)."""
+    code = _RAGGED.replace("N, M, B = 64, 16, 5", "N, M, B = 256, 64, 7")
+    _sub({}, code)
+    _sub({"SE2_NO_PERSIST": "1"}, code)
+
+
+def test_bounded_wait_times_out_and_plan_recovers(se2):
+    """A dependency nothing satisfies: the kernel's wait gives up, the host
+    reads SE2_ERR_TIMEOUT, and the plan then computes correctly again."""
+    N, M = 64, 16
+    rng = np.random.default_rng(5)
+    F = rng.standard_normal((1, M, N, N)).astype(np.float32)
+    P = rng.random((1, M, N, N)).astype(np.float32)
+    plan = se2.Plan(N, M, batch=2)
+    f = torch.from_numpy(F).cuda()
+    C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
+    out = torch.empty_like(f)
+    import ctypes
+    lib = se2.load_library()
+    st = lib.se2_debug_wait_timeout(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    with pytest.raises(se2.SE2Error) as ei:
+        plan.status()
+    assert ei.value.status == 5
+    plan.status()   # cleared
+    out = se2.convolve(plan, f, C)
+    plan.status()
+    want = O.convolve(F[0].astype(np.float64), P[0].astype(np.float64))
+    assert _rel(out[0].double().cpu().numpy(), want) < 1e-5
