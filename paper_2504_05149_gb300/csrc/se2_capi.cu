@@ -115,8 +115,10 @@ se2_status plan_init(se2_plan_s* p) {
     p->fused = kt.fwd_xt != nullptr && !(split && split[0] == '1');
     se2_status st = set_smem<T>(kt);
     if (st != SE2_OK) return st;
-    const char* nop = getenv("SE2_NO_PERSIST");
-    p->persist = p->fused && kt.persist != nullptr && !(nop && nop[0] == '1');
+    // The persistent dataflow kernel is opt-in (SE2_PERSIST=1): on 256^2 x 64
+    // it measured slower than the three-kernel sequence.
+    const char* per = getenv("SE2_PERSIST");
+    p->persist = p->fused && kt.persist != nullptr && (per && per[0] == '1');
     if (p->persist) {
         cudaError_t r = cudaFuncSetAttribute((const void*)kt.persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kt.smem_persist);

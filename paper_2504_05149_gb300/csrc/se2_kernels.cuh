@@ -132,6 +132,56 @@ __device__ __forceinline__ void row_from_global(c2<T>* sm, const c2<T>* g, int l
     }
 }
 
+// Load the [M][N/2+1] slab of one y row (rows `rstride` apart in the scratch)
+// into shared memory: every thread issues all of its loads before its first
+// shared-memory store, so the loads are in flight together.
+template <typename T, int N, int M>
+__device__ __forceinline__ void slab_from_global(c2<T>* S, const c2<T>* g, size_t rstride, uint64_t pol) {
+    constexpr int H = N / 2 + 1, SP = slab_pitch<N>();
+    const int tid = threadIdx.x;
+    if constexpr (sizeof(c2<T>) == 8) {
+        constexpr int NV = (H - 1) / 2;                  // float4 per row
+        constexpr int TOT = M * NV;
+        constexpr int PER = (TOT + kThreads - 1) / kThreads;
+        float4 v[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * kThreads;
+            if (e < TOT) {
+                const int r = e / NV, c = e - r * NV;
+                v[q] = ld_s4(reinterpret_cast<const float4*>(g + r * rstride) + c, pol);
+            }
+        }
+        c2<T> last = mk<T>(0, 0);
+        if (tid < M) last = ld_s(g + tid * rstride + (H - 1), pol);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * kThreads;
+            if (e < TOT) {
+                const int r = e / NV, c = e - r * NV;
+                reinterpret_cast<float4*>(S + rowoff<M, SP>(r))[c] = v[q];
+            }
+        }
+        if (tid < M) S[rowoff<M, SP>(tid) + H - 1] = last;
+    } else {
+        constexpr int TOT = M * H;
+        constexpr int PER = (TOT + kThreads - 1) / kThreads;
+        for (int q0 = 0; q0 < PER; q0 += 8) {
+            c2<T> v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = tid + (q0 + q) * kThreads;
+                if (q0 + q < PER && e < TOT) { const int r = e / H, c = e - r * H; v[q] = ld_s(g + r * rstride + c, pol); }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = tid + (q0 + q) * kThreads;
+                if (q0 + q < PER && e < TOT) { const int r = e / H, c = e - r * H; S[rowoff<M, SP>(r) + c] = v[q]; }
+            }
+        }
+    }
+}
+
 template <typename T>
 struct XArgs {                 // fwd_xt / fwd_x / inv_tx / inv_x
     const T* f;                // real grids (fwd) or nullptr
@@ -289,12 +339,7 @@ __device__ __forceinline__ void unit_inv_tx(const XArgs<T>& a, const c2<T>* spro
     c2<T>* XB = S + slab_elems<M, SP>();
     const int tid = threadIdx.x;
     const uint64_t pk = pol_keep(), po = pol_stream();
-    {
-        const int w = tid >> 5, l32 = tid & 31;
-        const c2<T>* sb = sprob + (size_t)j * a.tp;
-        for (int r = w; r < M; r += kThreads / 32)
-            row_from_global<T, H>(S + rowoff<M, SP>(r), sb + (size_t)r * N * a.tp, l32, pk);
-    }
+    slab_from_global<T, N, M>(S, sprob + (size_t)j * a.tp, (size_t)N * a.tp, pk);
     __syncthreads();
     {
         constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
@@ -463,28 +508,35 @@ __device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int 
             const T sc = (T)*sh_scale;
             const long long coff = (long long)o * a.N * a.cp + kx;
             const T mk_ = (kx == 0 || kx == a.nk) ? (T)1 : (T)2;
+            for (int i = 0; i < a.n_params; ++i) {
+                const c2<T>* Db = a.dC[i] + b * a.c_pstride + coff;
+                c2<T> d[TO::regs];
 #pragma unroll
-            for (int k = 0; k < TO::regs; ++k) {
-                const int ky = TO::idx(t, k);
-                const T w = ((kx + ky) & 1) ? (T)-1 : (T)1;
-                const long long ci = coff + (long long)ky * a.cp;
-                if (a.n_params > 0) {
-                    // conj(G^) F^
+                for (int k = 0; k < TO::regs; ++k) d[k] = ld_in(Db + (long long)TO::idx(t, k) * a.cp, pin);
+#pragma unroll
+                for (int k = 0; k < TO::regs; ++k) {
+                    const int ky = TO::idx(t, k);
+                    const T w = ((kx + ky) & 1) ? (T)-1 : (T)1;
+                    // Re(W dC conj(G^) F^)
                     const T pr = re[k] * fr[k] + im[k] * fi[k];
                     const T pi = re[k] * fi[k] - im[k] * fr[k];
+                    const T v = mk_ * w * (d[k].x * pr - d[k].y * pi);
 #pragma unroll
-                    for (int i = 0; i < kMaxParams; ++i) {
-                        if (i < a.n_params) {
-                            const c2<T> d = ld_in(a.dC[i] + b * a.c_pstride + ci, pin);
-                            acc[i] += mk_ * w * (d.x * pr - d.y * pi);
-                        }
-                    }
+                    for (int q = 0; q < kMaxParams; ++q) if (q == i) acc[q] += v;
                 }
-                if (a.want_grad) {
-                    const c2<T> cv = ld_in(a.C[0] + b * a.c_pstride + ci, pin);
+            }
+            if (a.want_grad) {
+                const c2<T>* Cb = a.C[0] + b * a.c_pstride + coff;
+                c2<T> cv[TO::regs];
+#pragma unroll
+                for (int k = 0; k < TO::regs; ++k) cv[k] = ld_in(Cb + (long long)TO::idx(t, k) * a.cp, pin);
+#pragma unroll
+                for (int k = 0; k < TO::regs; ++k) {
+                    const int ky = TO::idx(t, k);
+                    const T w = ((kx + ky) & 1) ? (T)-1 : (T)1;
                     // W conj(C) G^ * scale
-                    const T xr = (cv.x * re[k] + cv.y * im[k]) * sc * w;
-                    const T xi = (cv.x * im[k] - cv.y * re[k]) * sc * w;
+                    const T xr = (cv[k].x * re[k] + cv[k].y * im[k]) * sc * w;
+                    const T xi = (cv[k].x * im[k] - cv[k].y * re[k]) * sc * w;
                     re[k] = xr;
                     im[k] = xi;
                 }
@@ -525,19 +577,25 @@ __device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int 
         if (act && t < TO::lanes) {
             const T sc = (T)*sh_scale;
             const long long coff = (long long)o * a.N * a.cp + kx;
+            // all loads of one coefficient array first, then the products
+            for (int i = 0; i < a.k; ++i) {
+                const c2<T>* Cb = a.C[i] + b * a.c_pstride + coff;
+                c2<T> cv[TO::regs];
+#pragma unroll
+                for (int k = 0; k < TO::regs; ++k) cv[k] = ld_in(Cb + (long long)TO::idx(t, k) * a.cp, pin);
+#pragma unroll
+                for (int k = 0; k < TO::regs; ++k) {
+                    const T r = re[k] * cv[k].x - im[k] * cv[k].y;
+                    im[k] = re[k] * cv[k].y + im[k] * cv[k].x;
+                    re[k] = r;
+                }
+            }
 #pragma unroll
             for (int k = 0; k < TO::regs; ++k) {
                 const int ky = TO::idx(t, k);
-                T xr = re[k] * sc, xi = im[k] * sc;
-                for (int i = 0; i < a.k; ++i) {
-                    const c2<T> cv = ld_in(a.C[i] + b * a.c_pstride + coff + (long long)ky * a.cp, pin);
-                    const T r = xr * cv.x - xi * cv.y;
-                    xi = xr * cv.y + xi * cv.x;
-                    xr = r;
-                }
-                if ((a.k & 1) && ((kx + ky) & 1)) { xr = -xr; xi = -xi; }   // W^k
-                re[k] = xr;
-                im[k] = xi;
+                const bool neg = (a.k & 1) && ((kx + ky) & 1);           // W^k
+                re[k] = neg ? -re[k] * sc : re[k] * sc;
+                im[k] = neg ? -im[k] * sc : im[k] * sc;
             }
         }
         if constexpr (R2 == 1) {
@@ -822,12 +880,41 @@ __device__ __forceinline__ const unsigned* unit_dep(const PArgs<T>& a, int stage
     return nullptr;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
+}
+
+// Pull the HBM-resident inputs of a unit towards L2 ahead of its turn: the
+// f rows of a unit A, the first coefficient tile of a unit B (units C read
+// scratch, which is already in L2).
+template <typename T, int N, int M>
+__device__ __forceinline__ void prefetch_unit(const PArgs<T>& a, int stage, int p, int u) {
+    const int tid = threadIdx.x;
+    if (stage == 0) {
+        const char* fb = reinterpret_cast<const char*>(a.x.f + p * a.x.g_pstride + (size_t)u * N);
+        constexpr int LPR = (N * (int)sizeof(T) + 127) / 128;       // 128-byte lines per row
+        for (int e = tid; e < M * LPR; e += kThreads) {
+            const int r = e / LPR, c = e - r * LPR;
+            prefetch_l2(fb + (size_t)r * N * N * sizeof(T) + c * 128);
+        }
+    } else if (stage == 1) {
+        constexpr int LINES = kThreads / team_size<N>();
+        const long long line = (long long)u * LINES;
+        const long long NR = (long long)a.l.n_outer * a.l.nk;
+        if (line < NR) {
+            const int o = (int)(line / a.l.nk), kx = (int)(line - (long long)o * a.l.nk);
+            const char* cb = reinterpret_cast<const char*>(a.l.C[0] + p * a.l.c_pstride + (long long)o * a.l.N * a.l.cp + kx);
+            for (int ky = tid; ky < N; ky += kThreads) prefetch_l2(cb + (size_t)ky * a.l.cp * sizeof(c2<T>));
+        }
+    }
+}
+
 template <typename T, int N, int M>
 __global__ void __launch_bounds__(kThreads) k_conv_persist(PArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kThreads / 32];
     __shared__ double sh_scale;
-    __shared__ int sh_unit[3];
+    __shared__ int sh_unit[6];
     const int tid = threadIdx.x;
     // thread-0 pipeline state: the current unit, its early dependency read,
     // and the list index of the next unit (atomic in flight)
@@ -883,11 +970,16 @@ __global__ void __launch_bounds__(kThreads) k_conv_persist(PArgs<T> a) {
                     ns = -1;
                 }
             }
+            sh_unit[3] = ns;
+            sh_unit[4] = np;
+            sh_unit[5] = nu;
         }
         __syncthreads();
         const int stage = sh_unit[0], p = sh_unit[1], u = sh_unit[2];
+        const int pst = sh_unit[3], pp = sh_unit[4], pu = sh_unit[5];
         __syncthreads();     // everyone has read sh_unit before it is rewritten
         if (stage < 0) break;
+        if (pst >= 0) prefetch_unit<T, N, M>(a, pst, pp, pu);
         c2<T>* sprob = a.x.s + (size_t)(p % a.D) * a.x.s_pstride;
         if (stage == 0) {
             unit_fwd_xt<T, N, M>(a.x, a.x.f + p * a.x.g_pstride, sprob, u, nullptr, smem_raw, red);

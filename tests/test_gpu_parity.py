@@ -238,18 +238,22 @@ def test_persistent_and_three_kernel_paths_agree(se2):
     three-kernel sequence give the oracle's result on B = 7 problems (more
     than the 3 scratch slots, so slots are reused)."""
     code = _RAGGED.replace("N, M, B = 64, 16, 5", "N, M, B = 256, 64, 7")
+    _sub({"SE2_PERSIST": "1"}, code)
     _sub({}, code)
-    _sub({"SE2_NO_PERSIST": "1"}, code)
 
 
 def test_bounded_wait_times_out_and_plan_recovers(se2):
     """A dependency nothing satisfies: the kernel's wait gives up, the host
     reads SE2_ERR_TIMEOUT, and the plan then computes correctly again."""
+    os.environ["SE2_PERSIST"] = "1"    # read at plan creation
     N, M = 64, 16
     rng = np.random.default_rng(5)
     F = rng.standard_normal((1, M, N, N)).astype(np.float32)
     P = rng.random((1, M, N, N)).astype(np.float32)
-    plan = se2.Plan(N, M, batch=2)
+    try:
+        plan = se2.Plan(N, M, batch=2)
+    finally:
+        del os.environ["SE2_PERSIST"]
     f = torch.from_numpy(F).cuda()
     C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
     out = torch.empty_like(f)
