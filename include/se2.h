@@ -182,6 +182,31 @@ se2_status se2_plan_status(se2_plan_t plan, void* stream);
 se2_status se2_debug_wait_timeout(se2_plan_t plan, const void* f, const void* coeffs, void* out,
                                   void* stream);
 
+/*
+ * se2_convolve_noalloc -- the same result as se2_convolve (FP32, one kernel
+ * spectrum per problem, no log scale) for callers that cannot create a plan
+ * because creating one allocates device memory: for instance code running
+ * inside a host framework's execution step where device allocation is not
+ * allowed, or code that must not risk the implicit synchronisation that
+ * cudaMalloc / cudaFree may cause.  The paper has no counterpart; this is a
+ * deployment variant of Algorithm 3 at N = L.
+ *   f, coeffs, out  as in se2_convolve (float / complex float, caller-owned)
+ *   N, M, B         sizes; the batch is processed in chunks that fit
+ * Memory: the call uses a fixed 64 MiB device array defined in the library
+ * (twiddle tables + scratch), present on every GPU that loads the library
+ * until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  A problem whose scratch exceeds the array (e.g.
+ * N = 512 with M = 128) is rejected with SE2_ERR_UNSUPPORTED.
+ * The first call on a device sets the device up (looks up the array's
+ * device address, writes the twiddle tables, synchronises the device once);
+ * make that first call before any stream capture.  All calls share the one
+ * array, so calls that may overlap on the GPU (different streams, or other
+ * threads) race and must be serialised by the caller.  Nothing in the array
+ * needs to start at zero.  Errors: as the other calls (se2_last_error()).
+ */
+se2_status se2_convolve_noalloc(const void* f, const void* coeffs, void* out, int N, int M, int B,
+                                void* stream);
+
 /* Thread-local text of the last error (never NULL). */
 const char* se2_last_error(void);
 

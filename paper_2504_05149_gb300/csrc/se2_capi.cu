@@ -52,6 +52,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void se2::set_last_error(const char* msg) { g_err = msg; }
+
 struct se2_plan_s {
     int N = 0, M = 0, batch = 0, dev = 0;
     se2_precision prec = SE2_F32;

@@ -49,6 +49,9 @@ bool get_kernels(int N, int M, KTable<T>* kt) {
     }
 }
 
+// Sets the thread-local text returned by se2_last_error().
+void set_last_error(const char* msg);
+
 // FP64 twiddle generation (sincospi), rounded to T.
 template <typename T>
 cudaError_t make_twiddles(c2<T>* tw, int L, cudaStream_t st);
