@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--N", type=int, default=N_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="c2", choices=["c2", "c2chain", "c4", "c5"],
+                    help="c2: single convolutions at 256^2x64 (the headline); c2chain: 8-fold chains; "
+                         "c4: 4096 uneven problems with separable chains (CUDA graph); c5: forward+adjoint")
+    ap.add_argument("--problems", type=int, default=4096, help="c4 batch size")
     return ap.parse_args()
 
 
@@ -173,6 +177,10 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.config != "c2":
+        from functools import partial
+        {"c2chain": run_chain8, "c4": run_batch, "c5": run_adjoint}[args.config](args)
+        return
     import torch
     import torch.distributed as dist
     import paper_2504_05149_gb300 as se2
@@ -302,6 +310,139 @@ def plan_chunk(plan, N, M, B):
     if env and 1 <= int(env) < c:
         c = int(env)
     return min(c, B)
+
+
+def _clock_and_time(fn, steps, warmup, dev, settle=0.6):
+    """Warm up, settle ~0.6 s under load (clock sampling), then time `steps`
+    calls of fn with CUDA events on the current stream."""
+    import torch
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(vis.split(",")[dev.index or 0].strip() if vis else (dev.index or 0))
+    sampler.start()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    t0 = time.time()
+    while time.time() - t0 < settle:
+        fn()
+        torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t1 = time.time()
+    sampler.stop()
+    return e0.elapsed_time(e1), sampler.summary(t0, t1)
+
+
+def _line(metric, value, unit, args, ms, cfg, extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+         "dtype": "f32", "data": "synthetic", "config": cfg}
+    d.update(extra)
+    print(json.dumps(d), flush=True)
+
+
+def run_chain8(args):
+    """8-fold chains f * rho_1 * ... * rho_8 at 256^2 x 64 (the chain's second
+    config), one chain of distinct kernels per problem."""
+    import torch
+    import paper_2504_05149_gb300 as se2
+    import synth
+    N, M, B, k = args.N, args.M, args.batch, 8
+    dev = torch.device("cuda", 0)
+    plan = se2.Plan(N, M, batch=B)
+    Fs, Cs = [], [[] for _ in range(k)]
+    for b in range(B):
+        prob = synth.make_problem(2, 500 + b, N, M, n_bumps=16, n_kernels=k)
+        Fs.append(torch.from_numpy(synth.sample_bumps(N, M, prob.bumps).astype(np.float32)))
+        for i, kp in enumerate(prob.kernels):
+            Cs[i].append(torch.from_numpy(synth.sample_kernel(N, M, kp).astype(np.float32)))
+    f = torch.stack(Fs).to(dev)
+    C = [se2.coeffs(plan, torch.stack(c).to(dev))[0] for c in Cs]
+    out = torch.empty_like(f)
+    ms, clocks = _clock_and_time(lambda: se2.convolve_chain(plan, f, C, out=out), args.steps, args.warmup, dev)
+    L = N * N * M
+    alg = B * (8 * L + k * 8 * M * N * (N // 2 + 1))
+    hbm, src = peaks()
+    ach = alg / (ms / args.steps / 1e3) / 1e9
+    _line("8-fold SE(2) convolution chains/s at N=256, M=64 (FP32)", B * args.steps / (ms / 1e3), "chain/s", args, ms,
+          {"workload": f"se2_convolve_chain k=8 distinct kernels, batch {B}", "grid": [M, N, N]},
+          {"roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "traffic": None, "peak_source": src, "alg_bytes_per_chain": alg / B},
+           "gpu_launches": 3 * args.steps, "clocks": clocks})
+
+
+def run_batch(args):
+    """4096 independent problems of uneven size (N in {32,64,128,256}, M in
+    {16,32,64}), each with a chain of k ~ U{1..16} separable radial kernels,
+    as one CUDA graph of per-class launches."""
+    import torch
+    import synth
+    from paper_2504_05149_gb300.batch import BatchRunner
+    dev = torch.device("cuda", 0)
+    rng = synth.SplitMix64(synth.config_seed(4, 0))
+    shapes, chains, bumps = [], [], []
+    for i in range(args.problems):
+        N = [32, 64, 128, 256][rng.randint(0, 3)]
+        M = [16, 32, 64][rng.randint(0, 2)]
+        k = rng.randint(1, 16)
+        nb = rng.randint(3, 16)
+        shapes.append((N, M))
+        bumps.append(synth.draw_bumps(rng, nb))
+        chains.append([synth.draw_kernel(rng) for _ in range(k)])
+    runner = BatchRunner(shapes, device=0)
+    for i in range(args.problems):
+        N, M = shapes[i]
+        runner.f_of(i).copy_(synth.sample_bumps_torch(N, M, bumps[i], dev, torch.float32))
+        runner.set_chain(i, [(kp.sigma, kp.sigma_theta, kp.nu) for kp in chains[i]])
+    runner.build_tables()
+    runner.tune()
+    runner.capture()
+    ms, clocks = _clock_and_time(runner.replay, args.steps, args.warmup, dev)
+    pts = runner.points()
+    hbm, src = peaks()
+    alg = 8 * pts                                     # read f, write out (factored coefficients)
+    ach = alg / (ms / args.steps / 1e3) / 1e9
+    _line("SE(2) convolutions/s, 4096 uneven problems with separable kernel chains (FP32)",
+          args.problems * args.steps / (ms / 1e3), "conv/s", args, ms,
+          {"workload": "4096 problems, N~U{32,64,128,256}, M~U{16,32,64}, chains k~U{1..16}, 3..16 bumps; "
+                       "per-size-class plans on forked streams in one CUDA graph", "points_per_step": pts,
+           "classes": {f"{N}x{M}": [len(v), runner.config[(N, M)][0], runner.config[(N, M)][1]]
+                       for (N, M), v in runner.classes.items()}},
+          {"points_per_s": pts * args.steps / (ms / 1e3),
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "traffic": None, "peak_source": src, "alg_bytes_per_step": alg},
+           "gpu_launches": runner.launches_per_run() * args.steps, "clocks": clocks})
+
+
+def run_adjoint(args):
+    """Differentiation config: forward + adjoint (grad f, grad sigma, grad
+    sigma_theta) at 256^2 x 64, batch 64, shared kernel, FP32."""
+    import torch
+    import paper_2504_05149_gb300 as se2
+    import synth
+    N, M, B = args.N, args.M, 64
+    dev = torch.device("cuda", 0)
+    plan = se2.Plan(N, M, batch=B, flags=se2.SHARED_KERNEL)
+    f = torch.stack([synth.sample_bumps_torch(N, M, synth.make_problem(5, b, N, M, n_bumps=16).bumps, dev, torch.float32)
+                     for b in range(B)]).contiguous().requires_grad_(True)
+    target = torch.randn_like(f)
+    params = torch.tensor([0.025, 0.25], dtype=torch.float64, device=dev, requires_grad=True)
+
+    def step():
+        out = se2.SE2Conv.apply(f, params, plan)
+        loss = 0.5 * ((out - target) ** 2).sum()
+        loss.backward()
+    ms, clocks = _clock_and_time(step, args.steps, args.warmup, dev)
+    _line("SE(2) forward+adjoint convolutions/s at N=256, M=64, batch 64 (FP32)", B * args.steps / (ms / 1e3),
+          "conv/s", args, ms, {"workload": "loss = 1/2||f * rho(sigma, sigma_theta) - target||^2, grads wrt f and "
+                               "(sigma, sigma_theta); includes kernel sampling, 3 coefficient transforms, forward, adjoint",
+                               "grid": [M, N, N], "global_batch": B},
+          {"clocks": clocks})
 
 
 if __name__ == "__main__":

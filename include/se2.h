@@ -63,6 +63,7 @@ typedef enum {
 
 /* Plan flags */
 #define SE2_SHARED_KERNEL 0x1u  /* one coefficient array serves the whole batch */
+#define SE2_PERSISTENT    0x2u  /* FP32: run se2_convolve(_chain) as one persistent dataflow kernel */
 
 /*
  * se2_plan_create -- validate sizes, build FP64-accurate twiddle tables and
@@ -160,6 +161,30 @@ se2_status se2_backward(se2_plan_t plan, const void* grad_out, const void* f, in
  */
 se2_status se2_sample_radial_gaussian(se2_plan_t plan, double sigma, double sigma_theta, double nu,
                                       void* P, void* dP_dsigma, void* dP_dsigma_theta, void* stream);
+
+/*
+ * se2_separable_tables -- coefficients of a chain of separable radial kernels
+ * in factored form.  The kernel family of se2_sample_radial_gaussian is a
+ * product of 1-D factors, so its C = DFT(P)/|L| is tt (x) ty (x) tx, and the
+ * product over a chain (Eq. MatSqKfgG) stays factored.  For problem b with
+ * k[b] kernels whose (sigma, sigma_theta, nu) are params[b][j][0..2] (j <
+ * k[b], array [B][kmax][3]), writes tables[b] = [tx (N/2+1) | ty (N) | tt (M)]
+ * complex (FP64 sampling and DFTs, rounded to the plan's type), with the
+ * extra W^(k-1) folded into tx and ty so that se2_convolve_separable applies
+ * W once.  params, k, tables: device memory.
+ */
+se2_status se2_separable_tables(se2_plan_t plan, const double* params, const int* k, int kmax, int B,
+                                void* tables, void* stream);
+
+/*
+ * se2_convolve_separable -- se2_convolve with the coefficient array given by
+ * factored tables (se2_separable_tables): the multiply step reads N/2+1+N+M
+ * complex numbers per problem instead of M*N*(N/2+1), so a convolution moves
+ * 8 bytes per grid point (read f, write out) in FP32.
+ *   tables  device, [B][N/2+1+N+M] complex ([1][...] with SE2_SHARED_KERNEL)
+ */
+se2_status se2_convolve_separable(se2_plan_t plan, const void* f, int B, const void* tables, void* out,
+                                  void* stream);
 
 /*
  * se2_plan_status -- synchronise `stream`, then report and clear the plan's

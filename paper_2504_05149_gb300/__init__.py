@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libse2.so")
 F64 = 0
 F32 = 1
 SHARED_KERNEL = 0x1
+PERSISTENT = 0x2
 
 _STATUS = {0: "SE2_OK", 1: "SE2_ERR_INVALID_ARG", 2: "SE2_ERR_UNSUPPORTED", 3: "SE2_ERR_OOM",
            4: "SE2_ERR_CUDA", 5: "SE2_ERR_TIMEOUT", 6: "SE2_ERR_NUMERIC"}
@@ -54,13 +55,16 @@ def load_library(path: str = LIB_PATH):
     lib.se2_convolve.argtypes = [vp, vp, ip, vp, vp, vp, vp]
     lib.se2_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp, vp]
     lib.se2_plan_status.argtypes = [vp, vp]
+    lib.se2_separable_tables.argtypes = [vp, vp, vp, ip, ip, vp, vp]
+    lib.se2_convolve_separable.argtypes = [vp, vp, ip, vp, vp, vp]
     lib.se2_backward.argtypes = [vp, vp, vp, ip, vp, vp, ip, ctypes.POINTER(vp), vp, vp, vp]
     lib.se2_sample_radial_gaussian.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
     lib.se2_last_error.restype = ctypes.c_char_p
     lib.se2_version.restype = ctypes.c_char_p
     for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_chain",
-                 "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian"):
+                 "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
+                 "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -221,6 +225,40 @@ def sample_radial_gaussian(plan: Plan, sigma: float, sigma_theta: float, nu: flo
     return (P, dPs, dPt) if derivs else P
 
 
+def table_len(plan: Plan) -> int:
+    return plan.N // 2 + 1 + plan.N + plan.M
+
+
+def separable_tables(plan: Plan, params: torch.Tensor, k: torch.Tensor) -> torch.Tensor:
+    """Factored chain coefficients (se2_separable_tables).  params: float64
+    [B, kmax, 3] (sigma, sigma_theta, nu) on the plan's device; k: int32 [B]
+    chain lengths.  Returns [B, N/2+1+N+M] complex."""
+    if params.dim() != 3 or params.shape[2] != 3 or params.dtype != torch.float64 or not params.is_contiguous():
+        raise ValueError("params: contiguous float64 [B, kmax, 3]")
+    B, kmax = params.shape[0], params.shape[1]
+    if k.dtype != torch.int32 or k.shape != (B,) or not k.is_contiguous():
+        raise ValueError("k: contiguous int32 [B]")
+    tab = torch.empty((B, table_len(plan)), dtype=plan.cdtype, device=params.device)
+    _check(load_library().se2_separable_tables(plan.handle, _ptr(params), _ptr(k), kmax, B, _ptr(tab),
+                                               _stream(params.device)))
+    return tab
+
+
+def convolve_separable(plan: Plan, f: torch.Tensor, tables: torch.Tensor, out: Optional[torch.Tensor] = None):
+    """se2_convolve with factored coefficient tables."""
+    B = plan._check_grid(f, "f")
+    if out is None:
+        out = torch.empty_like(f)
+    else:
+        plan._check_grid(out, "out")
+    nt = 1 if plan.flags & SHARED_KERNEL else B
+    if tables.shape != (nt, table_len(plan)) or tables.dtype != plan.cdtype or not tables.is_contiguous():
+        raise ValueError(f"tables: expected contiguous {plan.cdtype} [{nt}, {table_len(plan)}]")
+    _check(load_library().se2_convolve_separable(plan.handle, _ptr(f), B, _ptr(tables), _ptr(out),
+                                                 _stream(f.device)))
+    return out
+
+
 class SE2Conv(torch.autograd.Function):
     """out = f * rho(sigma, sigma_theta) for a batch f [B, M, N, N] and the
     radial Gaussian x wrapped-normal kernel shared by the batch, differentiable
@@ -252,4 +290,5 @@ class SE2Conv(torch.autograd.Function):
 
 
 __all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_chain", "backward", "sample_radial_gaussian",
-           "SE2Conv", "load_library", "LIB_PATH", "SHARED_KERNEL"]
+           "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
+           "SHARED_KERNEL", "PERSISTENT"]

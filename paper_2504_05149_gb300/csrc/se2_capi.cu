@@ -95,7 +95,7 @@ se2_status set_smem(const KTable<T>& kt) {
         {(const void*)kt.fwd_xt, kt.smem_xt}, {(const void*)kt.inv_tx, kt.smem_xt},
         {(const void*)kt.fwd_x, kt.smem_x},   {(const void*)kt.inv_x, kt.smem_x},
         {(const void*)kt.y_conv, kt.smem_y},  {(const void*)kt.y_coef, kt.smem_y},
-        {(const void*)kt.y_adj, kt.smem_y},
+        {(const void*)kt.y_adj, kt.smem_y},   {(const void*)kt.y_sep, kt.smem_y},
         {(const void*)kt.t_fwd, kt.smem_t},   {(const void*)kt.t_inv, kt.smem_t},
     };
     for (auto& e : list) {
@@ -120,10 +120,14 @@ se2_status plan_init(se2_plan_s* p) {
     // The persistent dataflow kernel is opt-in (SE2_PERSIST=1): on 256^2 x 64
     // it measured slower than the three-kernel sequence.
     const char* per = getenv("SE2_PERSIST");
-    p->persist = p->fused && kt.persist != nullptr && (per && per[0] == '1');
+    p->persist = p->fused && kt.persist != nullptr &&
+                 ((p->flags & SE2_PERSISTENT) || (per && per[0] == '1'));
     if (p->persist) {
         cudaError_t r = cudaFuncSetAttribute((const void*)kt.persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kt.smem_persist);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute((const void*)kt.persist_sep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kt.smem_persist);
         if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
         int per_sm = 0, nsm = 0;
         r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kt.persist, kThreads, kt.smem_persist);
@@ -255,7 +259,7 @@ unsigned y_blocks(se2_plan_s* p) {
 template <typename T>
 se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* coeffs,
                        const double* const* log_scales, int k, void* out, cudaStream_t st,
-                       unsigned dep_extra, long long spin_limit) {
+                       unsigned dep_extra, long long spin_limit, const void* sep_tables = nullptr) {
     KTable<T>& kt = table<T>(p);
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
     const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
@@ -267,9 +271,13 @@ se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* c
     a.l.k = k;
     a.l.c_pstride = cps;
     a.l.ls_pstride = lps;
-    for (int i = 0; i < k; ++i) {
+    for (int i = 0; i < k && coeffs; ++i) {
         a.l.C[i] = (const c2<T>*)coeffs[i];
         a.l.ls[i] = (log_scales && log_scales[i]) ? log_scales[i] : nullptr;
+    }
+    if (sep_tables) {
+        a.l.sep = (const c2<T>*)sep_tables;
+        a.l.sep_pstride = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)(p->N / 2 + 1 + p->N + p->M);
     }
     a.B = B;
     a.D = p->slots;
@@ -285,7 +293,8 @@ se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* c
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     const long long units = (long long)B * (a.nA + a.nB + a.nC);
     const int grid = (int)(units < p->persist_grid ? units : p->persist_grid);
-    kt.persist<<<grid, kThreads, kt.smem_persist, st>>>(a);
+    if (sep_tables) kt.persist_sep<<<grid, kThreads, kt.smem_persist, st>>>(a);
+    else kt.persist<<<grid, kThreads, kt.smem_persist, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SE2_OK;
@@ -376,6 +385,27 @@ se2_status run_backward(se2_plan_s* p, const void* g, const void* f, int B, cons
     return SE2_OK;
 }
 
+template <typename T>
+se2_status run_sep(se2_plan_s* p, const void* f, int B, const void* tables, void* out, cudaStream_t st) {
+    KTable<T>& kt = table<T>(p);
+    if (p->persist) return run_persist<T>(p, f, B, nullptr, nullptr, 1, out, st, 0, kSpinLimit, tables);
+    const size_t g = (size_t)p->N * p->N * p->M;
+    const long long tps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)(p->N / 2 + 1 + p->N + p->M);
+    for (int c0 = 0; c0 < B; c0 += p->chunk) {
+        const int nb = (B - c0 < p->chunk) ? (B - c0) : p->chunk;
+        launch_forward<T>(p, (const T*)f + c0 * g, nb, nullptr, st);
+        LArgs<T> l = yargs<T>(p);
+        l.k = 1;
+        l.sep = (const c2<T>*)tables + c0 * tps;
+        l.sep_pstride = tps;
+        kt.y_sep<<<dim3(y_blocks<T>(p), nb), kThreads, kt.smem_y, st>>>(l);
+        launch_inverse<T>(p, (T*)out + c0 * g, nb, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
+}
+
 se2_status check_plan(se2_plan_t p) {
     if (p == nullptr) return fail(SE2_ERR_INVALID_ARG, "plan is NULL");
     return SE2_OK;
@@ -397,7 +427,7 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (!is_pow2(M) || M < 2 || M > 128) return fail(SE2_ERR_UNSUPPORTED, "M=%d: need a power of two in [2, 128]", M);
     if (batch < 1) return fail(SE2_ERR_INVALID_ARG, "batch=%d must be >= 1", batch);
     if (precision != SE2_F32 && precision != SE2_F64) return fail(SE2_ERR_UNSUPPORTED, "precision %d not supported", (int)precision);
-    if (flags & ~SE2_SHARED_KERNEL) return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT)) return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -547,6 +577,39 @@ se2_status se2_sample_radial_gaussian(se2_plan_t p, double sigma, double sigma_t
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SE2_OK;
+}
+
+se2_status se2_separable_tables(se2_plan_t p, const double* params, const int* k, int kmax, int B, void* tables,
+                                void* stream) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    if (params == nullptr || k == nullptr || tables == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (kmax < 1 || B < 1) return fail(SE2_ERR_INVALID_ARG, "kmax=%d and B=%d must be >= 1", kmax, B);
+    if (!aligned(params, 8) || !aligned(k, 4) || !aligned(tables, p->elem)) return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    DeviceGuard guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long tps = (long long)(p->N / 2 + 1 + p->N + p->M);
+    const size_t sm = sizeof(double) * 3 * ((size_t)p->N + p->M);
+    if (p->prec == SE2_F32)
+        k_sep_tables<float><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (float2*)tables, tps);
+    else
+        k_sep_tables<double><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (double2*)tables, tps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
+}
+
+se2_status se2_convolve_separable(se2_plan_t p, const void* f, int B, const void* tables, void* out, void* stream) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    if (f == nullptr || tables == nullptr || out == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (B < 1 || B > p->batch) return fail(SE2_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, p->batch);
+    const size_t re = p->elem / 2;
+    if (!aligned(f, re) || !aligned(out, re) || !aligned(tables, p->elem)) return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    if (f == out) return fail(SE2_ERR_INVALID_ARG, "out aliases f");
+    DeviceGuard guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == SE2_F32 ? run_sep<float>(p, f, B, tables, out, s) : run_sep<double>(p, f, B, tables, out, s);
 }
 
 se2_status se2_plan_status(se2_plan_t p, void* stream) {

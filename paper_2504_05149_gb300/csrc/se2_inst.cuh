@@ -25,13 +25,15 @@ template <typename T, int N, int M>
 void fill_fused(KTable<T>* kt) {
     constexpr size_t sm = fused_smem<T, N, M>();
     kt->persist = nullptr;
+    kt->persist_sep = nullptr;
     kt->smem_persist = 0;
     if constexpr (N >= 32 && M >= 8 && sm <= kMaxDynSmem) {
         kt->fwd_xt = k_fwd_xt<T, N, M>;
         kt->inv_tx = k_inv_tx<T, N, M>;
         kt->smem_xt = sm;
         if constexpr (sizeof(T) == 4) {
-            kt->persist = k_conv_persist<T, N, M>;
+            kt->persist = k_conv_persist<T, N, M, LM_CONV>;
+            kt->persist_sep = k_conv_persist<T, N, M, LM_SEP>;
             kt->smem_persist = sm > lines_smem<T, N>() ? sm : lines_smem<T, N>();
         }
     } else {
@@ -58,6 +60,7 @@ bool fill_n(int M, KTable<T>* kt) {
     kt->y_conv = k_lines<T, N, LM_CONV>;
     kt->y_coef = k_lines<T, N, LM_COEF>;
     kt->y_adj = k_lines<T, N, LM_ADJ>;
+    kt->y_sep = k_lines<T, N, LM_SEP>;
     kt->smem_y = lines_smem<T, N>();
     kt->lines_y = kThreads / team_size<N>();
     switch (M) {

@@ -18,7 +18,7 @@ struct KTable {
     size_t smem_xt = 0;
     XK fwd_x = nullptr, inv_x = nullptr;     // split path, x only
     size_t smem_x = 0;
-    LK y_conv = nullptr, y_coef = nullptr, y_adj = nullptr;   // lines of length N along y
+    LK y_conv = nullptr, y_coef = nullptr, y_adj = nullptr, y_sep = nullptr;   // lines of length N along y
     size_t smem_y = 0;
     int lines_y = 0;                          // lines per block
     LK t_fwd = nullptr, t_inv = nullptr;     // lines of length M along theta
@@ -27,6 +27,7 @@ struct KTable {
     int teams_x = 0;                          // row pairs per block (split fwd_x/inv_x)
     using PK = void (*)(PArgs<T>);
     PK persist = nullptr;                     // persistent convolution (null: three kernels)
+    PK persist_sep = nullptr;                 // same with separable coefficient tables
     size_t smem_persist = 0;
 };
 

@@ -26,7 +26,7 @@ constexpr int kThreads = 256;
 constexpr int kMaxChain = 32;
 constexpr int kMaxParams = 4;
 
-enum LineMode { LM_FWD = 0, LM_INV = 1, LM_CONV = 2, LM_COEF = 3, LM_ADJ = 4 };
+enum LineMode { LM_FWD = 0, LM_INV = 1, LM_CONV = 2, LM_COEF = 3, LM_ADJ = 4, LM_SEP = 5 };
 
 // Slab pitch (complex elements) for the [M][N/2+1] slab: = 2 mod 16 so that
 // the 8-lane angular teams of one warp hit distinct bank pairs.
@@ -226,6 +226,10 @@ struct LArgs {
     int n_params;
     const c2<T>* dC[kMaxParams];
     double* grad_params;       // [n_params], accumulated
+    // LM_SEP: separable coefficients C = tt[ktheta] ty[ky] tx[kx] per problem,
+    // tables [problem][(N/2+1) + N + M] complex (tx, ty, tt), W^(k-1) folded in
+    const c2<T>* sep;
+    long long sep_pstride;
 };
 
 // ---------------------------------------------------------------------------
@@ -432,7 +436,7 @@ __device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int 
     c2<T>* xb = XB + c * XS;
     const uint64_t pk = pol_keep();
 
-    if constexpr (MODE == LM_CONV || MODE == LM_COEF || MODE == LM_ADJ) {
+    if constexpr (MODE == LM_CONV || MODE == LM_COEF || MODE == LM_ADJ || MODE == LM_SEP) {
         if (tid == 0) {
             double sc = a.inv_L;
             if constexpr (MODE == LM_CONV || MODE == LM_ADJ) {
@@ -481,6 +485,42 @@ __device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int 
             c2<T>* cb = a.cout + b * a.cout_pstride + (long long)o * a.N * a.cp + kx;
 #pragma unroll
             for (int k = 0; k < TO::regs; ++k) cb[(long long)TO::idx(t, k) * a.cp] = mk<T>(re[k] * sc, im[k] * sc);
+        }
+    } else if constexpr (MODE == LM_SEP) {
+        // C from three 1-D tables (a chain of separable kernels), then W
+        if (act && t < TO::lanes) {
+            const T sc = (T)*sh_scale;
+            const c2<T>* tb = a.sep + b * a.sep_pstride;
+            const c2<T> cx = tb[kx];
+            const c2<T> ct = tb[a.nk + 1 + a.N + o];
+            // cx * ct, then * ty per ky
+            const T xr = cx.x * ct.x - cx.y * ct.y, xi = cx.x * ct.y + cx.y * ct.x;
+            c2<T> cy[TO::regs];
+#pragma unroll
+            for (int k = 0; k < TO::regs; ++k) cy[k] = tb[a.nk + 1 + TO::idx(t, k)];
+#pragma unroll
+            for (int k = 0; k < TO::regs; ++k) {
+                const int ky = TO::idx(t, k);
+                const T cr = xr * cy[k].x - xi * cy[k].y, ci = xr * cy[k].y + xi * cy[k].x;
+                const T r = re[k] * cr - im[k] * ci;
+                const T i2 = re[k] * ci + im[k] * cr;
+                const bool neg = (kx + ky) & 1;                           // W
+                re[k] = neg ? -r * sc : r * sc;
+                im[k] = neg ? -i2 * sc : i2 * sc;
+            }
+        }
+        if constexpr (R2 == 1) {
+            fft_reg<R1, +1>(re, im);
+            if (act) {
+#pragma unroll
+                for (int q = 0; q < R1; ++q) st_s(base + (long long)q * a.elem_stride, mk<T>(re[q], im[q]), pk);
+            }
+        } else {
+            team_fft<R2, R1, +1, T>(re, im, t, xb, a.tw, SyncBlock());
+            if (act && t < R2) {
+#pragma unroll
+                for (int q = 0; q < R1; ++q) st_s(base + (long long)(t + R2 * q) * a.elem_stride, mk<T>(re[q], im[q]), pk);
+            }
         }
     } else if constexpr (MODE == LM_ADJ) {
         // transpose of the convolution (grad_f spectrum W conj(C) G^ e^{ls} / |L|)
@@ -634,8 +674,9 @@ __global__ void __launch_bounds__(kThreads) k_inv_tx(XArgs<T> a) {
     unit_inv_tx<T, N, M>(a, a.s + b * a.s_pstride, a.out + b * a.g_pstride, blockIdx.x, smem_raw);
 }
 
+// FP32 line kernels are held to 85 registers so that three blocks share an SM.
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(kThreads) k_lines(LArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_lines(LArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sh_scale;
     __shared__ double red[kThreads / 32];
@@ -678,6 +719,91 @@ static __global__ void k_gauss_tables(double* tab, int N, int M, double sigma, d
         }
         tab[2 * N + l] = t * sqrt(2 * PI) / sigma_t;
         tab[2 * N + M + l] = dt * sqrt(2 * PI);
+    }
+}
+
+// Separable chain tables: for problem b with k_b kernels (sigma, sigma_t, nu)
+// from params[b][j][3], the 1-D factor spectra of each kernel (FP64 samples,
+// FP64 direct DFT divided by the length) multiplied over the chain:
+//   tx[kx] (kx <= N/2), ty[ky] (ky < N), tt[kt] (kt < M),
+// with W^(k_b - 1) = (-1)^((kx + ky)(k_b - 1)) folded into tx and ty, so that
+// the convolution applies W once.  One block per problem.
+template <typename T>
+__global__ void k_sep_tables(const double* params, const int* kcount, int kmax, int N, int M,
+                             c2<T>* tab, long long tab_pstride) {
+    const int b = blockIdx.x;
+    const int k = kcount[b];
+    const double PI = 3.14159265358979323846;
+    extern __shared__ double sh[];                 // g[N], gt[M], e^{-2 pi i n/N} [N], e^{-2 pi i n/M} [M]
+    double* g = sh;
+    double* gt = sh + N;
+    double2* twN = reinterpret_cast<double2*>(sh + N + M);
+    double2* twM = twN + N;
+    for (int i = threadIdx.x; i < N + M; i += blockDim.x) {
+        double sn, cn;
+        if (i < N) { sincospi(2.0 * i / N, &sn, &cn); twN[i] = make_double2(cn, -sn); }
+        else { sincospi(2.0 * (i - N) / M, &sn, &cn); twM[i - N] = make_double2(cn, -sn); }
+    }
+    c2<T>* tb = tab + b * tab_pstride;
+    const int H = N / 2 + 1;
+    const int tot = H + N + M;
+    // accumulate in registers: each thread owns entries e = tid, tid + blockDim, ...
+    double ar[8], ai[8];
+    for (int q = 0; q < 8; ++q) { ar[q] = 1.0; ai[q] = 0.0; }
+    for (int j = 0; j < k; ++j) {
+        const double sigma = params[((size_t)b * kmax + j) * 3 + 0];
+        const double sigma_t = params[((size_t)b * kmax + j) * 3 + 1];
+        const double nu = params[((size_t)b * kmax + j) * 3 + 2];
+        __syncthreads();
+        for (int i = threadIdx.x; i < N + M; i += blockDim.x) {
+            if (i < N) {
+                const double d = -0.5 + (double)i / N;
+                double acc = 0;
+                for (int n = -2; n <= 2; ++n) acc += exp(-(d + n) * (d + n) / (2 * sigma * sigma));
+                g[i] = acc / (sqrt(2 * PI) * sigma);
+            } else {
+                const int l = i - N;
+                double v = 2 * PI * l / M - nu + PI;
+                v = v - 2 * PI * floor(v / (2 * PI)) - PI;
+                double acc = 0;
+                for (int m = -4; m <= 4; ++m) acc += exp(-(v + 2 * PI * m) * (v + 2 * PI * m) / (2 * sigma_t * sigma_t));
+                gt[l] = acc * sqrt(2 * PI) / sigma_t;
+            }
+        }
+        __syncthreads();
+        for (int q = 0; q < 8; ++q) {
+            const int e = threadIdx.x + q * blockDim.x;
+            if (e >= tot) break;
+            const double* src;
+            const double2* tw;
+            int L, kk;
+            if (e < H) { src = g; L = N; kk = e; tw = twN; }
+            else if (e < H + N) { src = g; L = N; kk = e - H; tw = twN; }
+            else { src = gt; L = M; kk = e - H - N; tw = twM; }
+            double sr = 0, si = 0;
+            int idx = 0;                                   // (kk * n) mod L
+            for (int n = 0; n < L; ++n) {
+                sr += src[n] * tw[idx].x;
+                si += src[n] * tw[idx].y;
+                idx += kk;
+                if (idx >= L) idx -= L;
+            }
+            sr /= L;
+            si /= L;
+            const double r = ar[q] * sr - ai[q] * si;
+            ai[q] = ar[q] * si + ai[q] * sr;
+            ar[q] = r;
+        }
+    }
+    for (int q = 0; q < 8; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e >= tot) break;
+        double sgn = 1.0;
+        if (e < H + N && ((k - 1) & 1)) {
+            const int kk = e < H ? e : e - H;
+            if (kk & 1) sgn = -1.0;
+        }
+        tb[e] = mk<T>((T)(ar[q] * sgn), (T)(ai[q] * sgn));
     }
 }
 
@@ -897,7 +1023,7 @@ __device__ __forceinline__ void prefetch_unit(const PArgs<T>& a, int stage, int 
             const int r = e / LPR, c = e - r * LPR;
             prefetch_l2(fb + (size_t)r * N * N * sizeof(T) + c * 128);
         }
-    } else if (stage == 1) {
+    } else if (stage == 1 && a.l.C[0] != nullptr) {
         constexpr int LINES = kThreads / team_size<N>();
         const long long line = (long long)u * LINES;
         const long long NR = (long long)a.l.n_outer * a.l.nk;
@@ -909,7 +1035,7 @@ __device__ __forceinline__ void prefetch_unit(const PArgs<T>& a, int stage, int 
     }
 }
 
-template <typename T, int N, int M>
+template <typename T, int N, int M, int BMODE>
 __global__ void __launch_bounds__(kThreads) k_conv_persist(PArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kThreads / 32];
@@ -984,7 +1110,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_persist(PArgs<T> a) {
         if (stage == 0) {
             unit_fwd_xt<T, N, M>(a.x, a.x.f + p * a.x.g_pstride, sprob, u, nullptr, smem_raw, red);
         } else if (stage == 1) {
-            unit_lines<T, N, LM_CONV>(a.l, sprob, p, u, smem_raw, &sh_scale);
+            unit_lines<T, N, BMODE>(a.l, sprob, p, u, smem_raw, &sh_scale);
         } else {
             unit_inv_tx<T, N, M>(a.x, sprob, a.x.out + p * a.x.g_pstride, u, smem_raw);
         }

@@ -177,3 +177,31 @@ def make_problem(config: int, index: int, N: int, M: int, n_bumps: int,
     else:
         kernels = [draw_kernel(rng) for _ in range(n_kernels)]
     return Problem(N, M, bumps, kernels)
+
+
+def sample_bumps_torch(N: int, M: int, bumps: Sequence[Bump], device, dtype=None):
+    """sample_bumps evaluated with torch on `device` (same formulas), for
+    batches too large to generate on the host.  Returns [M][N][N]."""
+    import torch
+    dtype = dtype or torch.float64
+    x = torch.arange(N, dtype=torch.float64, device=device) / N - 0.5
+    th = 2.0 * math.pi * torch.arange(M, dtype=torch.float64, device=device) / M
+    cx = torch.tensor([b.cx for b in bumps], dtype=torch.float64, device=device)[:, None]
+    cy = torch.tensor([b.cy for b in bumps], dtype=torch.float64, device=device)[:, None]
+    sx = torch.tensor([b.sx for b in bumps], dtype=torch.float64, device=device)[:, None]
+    sy = torch.tensor([b.sy for b in bumps], dtype=torch.float64, device=device)[:, None]
+    ka = torch.tensor([b.kappa for b in bumps], dtype=torch.float64, device=device)[:, None]
+    mu = torch.tensor([b.mu for b in bumps], dtype=torch.float64, device=device)[:, None]
+    amp = torch.tensor([b.amp for b in bumps], dtype=torch.float64, device=device)[:, None]
+
+    def per(c, s):
+        d = torch.remainder(x[None, :] - c + 0.5, 1.0) - 0.5
+        acc = torch.zeros_like(d)
+        for n in range(-2, 3):
+            acc = acc + torch.exp(-((d + n) ** 2) / (2.0 * s * s))
+        return acc
+
+    X = per(cx, sx)
+    Y = per(cy, sy)
+    T = amp * torch.exp(ka * (torch.cos(th[None, :] - mu) - 1.0))
+    return torch.einsum("bl,bj,bi->lji", T, Y, X).to(dtype)

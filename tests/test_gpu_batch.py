@@ -1,0 +1,95 @@
+"""Separable chain tables, the separable convolution and the batched runner
+(uneven sizes, chains of 1..16 kernels, CUDA graph) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth  # noqa: E402
+from oracle import se2_oracle as O  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def se2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_05149_gb300 import build as b
+    b.build()
+    import paper_2504_05149_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _oracle_chain_coeffs(N, M, kernels):
+    C = np.ones((M, N, N), dtype=np.complex128)
+    for kp in kernels:
+        gx, gy, gt = synth.kernel_factors(N, M, kp)
+        C = C * O.coeffs_separable(gx, gy, gt)
+    return C
+
+
+@pytest.mark.parametrize("prec,N,M,k", [("f64", 32, 16, 1), ("f64", 32, 16, 4), ("f32", 64, 32, 7), ("f32", 256, 64, 16)])
+def test_separable_tables_and_convolution(se2, prec, N, M, k):
+    rng = synth.SplitMix64(777 + k)
+    kernels = [synth.draw_kernel(rng) for _ in range(k)]
+    kernels = [synth.KernelParams(kp.sigma, kp.sigma_theta, rng.uniform(0, 6.28)) for kp in kernels]
+    plan = se2.Plan(N, M, batch=2, precision=prec)
+    params = torch.zeros((2, 16, 3), dtype=torch.float64)
+    for j, kp in enumerate(kernels):
+        params[:, j] = torch.tensor([kp.sigma, kp.sigma_theta, kp.nu], dtype=torch.float64)
+    kk = torch.tensor([k, k], dtype=torch.int32)
+    tab = se2.separable_tables(plan, params.cuda(), kk.cuda())
+    t = tab[0].cpu().numpy().astype(np.complex128)
+    H = N // 2 + 1
+    tx, ty, tt = t[:H], t[H:H + N], t[H + N:]
+    C = tt[:, None, None] * ty[None, :, None] * tx[None, None, :]
+    want = _oracle_chain_coeffs(N, M, kernels)[..., :H]
+    if (k - 1) % 2:        # W^(k-1) folded in
+        want = O.weight_W(N, M)[..., :H] * want
+    tol = 1e-12 if prec == "f64" else 2e-6
+    assert _rel(C, want) < tol
+    npd = np.float64 if prec == "f64" else np.float32
+    F = np.stack([synth.sample_bumps(N, M, synth.make_problem(4, b, N, M, n_bumps=5).bumps) for b in range(2)]).astype(npd)
+    out = se2.convolve_separable(plan, torch.from_numpy(F).cuda(), tab).double().cpu().numpy()
+    Ps = [synth.sample_kernel(N, M, kp) for kp in kernels]
+    for b in range(2):
+        assert _rel(out[b], O.convolve_chain(F[b].astype(np.float64), Ps)) < (1e-10 if prec == "f64" else 1e-5)
+
+
+def test_batch_runner_uneven_sizes_graph(se2, tmp_path):
+    """A small batch shaped like the batching config (sizes N in {32,64,128},
+    M in {16,32}, chains of 1..16 kernels, 3..16 bumps), autotuned, captured
+    in a CUDA graph and replayed twice; every problem against the oracle."""
+    from paper_2504_05149_gb300.batch import BatchRunner
+    rng = synth.SplitMix64(4000)
+    shapes, probs = [], []
+    for i in range(14):
+        N = [32, 64, 128][rng.randint(0, 2)]
+        M = [16, 32][rng.randint(0, 1)]
+        k = rng.randint(1, 16)
+        prob = synth.make_problem(4, i, N, M, n_bumps=rng.randint(3, 16), n_kernels=k)
+        shapes.append((N, M))
+        probs.append(prob)
+    runner = BatchRunner(shapes, cache_path=str(tmp_path / "tune.json"))
+    for i, prob in enumerate(probs):
+        runner.f_of(i).copy_(torch.from_numpy(synth.sample_bumps(prob.N, prob.M, prob.bumps).astype(np.float32)))
+        runner.set_chain(i, [(kp.sigma, kp.sigma_theta, kp.nu) for kp in prob.kernels])
+    runner.build_tables()
+    runner.tune(reps=1)
+    runner.capture()
+    for rep in range(2):
+        for c in runner.order:
+            runner.out[c].zero_()
+        runner.replay()
+        torch.cuda.synchronize()
+        for i, prob in enumerate(probs):
+            F = synth.sample_bumps(prob.N, prob.M, prob.bumps).astype(np.float32).astype(np.float64)
+            Ps = [synth.sample_kernel(prob.N, prob.M, kp) for kp in prob.kernels]
+            want = O.convolve_chain(F, Ps)
+            assert _rel(runner.out_of(i).double().cpu().numpy(), want) < 1e-5, (i, prob.N, prob.M, len(prob.kernels))
+    assert runner.launches_per_run() > 0
+    assert (tmp_path / "tune.json").exists()
