@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--N", type=int, default=N_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c2chain", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c2chain", "c3", "c4", "c5"],
                     help="c2: single convolutions at 256^2x64 (the headline); c2chain: 8-fold chains; "
                          "c4: 4096 uneven problems with separable chains (CUDA graph); c5: forward+adjoint")
     ap.add_argument("--problems", type=int, default=4096, help="c4 batch size")
@@ -179,7 +179,7 @@ def main():
         return
     if args.config != "c2":
         from functools import partial
-        {"c2chain": run_chain8, "c4": run_batch, "c5": run_adjoint}[args.config](args)
+        {"c2chain": run_chain8, "c3": run_precision, "c4": run_batch, "c5": run_adjoint}[args.config](args)
         return
     import torch
     import torch.distributed as dist
@@ -417,6 +417,50 @@ def run_batch(args):
            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "traffic": None, "peak_source": src, "alg_bytes_per_step": alg},
            "gpu_launches": runner.launches_per_run() * args.steps, "clocks": clocks})
+
+
+def run_precision(args):
+    """Precision config: N=512, M=128, batch 8, 32-bump f1 with amplitudes
+    log-uniform in [1e-6, 1], a 32-fold separable kernel chain per problem;
+    split-bf16 tensor-core angular DFT vs the plain FP32 path, both timed,
+    max-rel error of each against the FP64 oracle on problem 0."""
+    import torch
+    import paper_2504_05149_gb300 as se2
+    import synth
+    from oracle import se2_oracle as O
+    N, M, B, K = 512, 128, 8, 32
+    dev = torch.device("cuda", 0)
+    probs = [synth.make_problem(3, b, N, M, n_bumps=32, n_kernels=K, log_amp=True) for b in range(B)]
+    f = torch.stack([synth.sample_bumps_torch(N, M, p.bumps, dev, torch.float32) for p in probs]).contiguous()
+    params = torch.zeros((B, K, 3), dtype=torch.float64)
+    for b, p in enumerate(probs):
+        for j, kp in enumerate(p.kernels):
+            params[b, j] = torch.tensor([kp.sigma, kp.sigma_theta, kp.nu])
+    params = params.to(dev)
+    kk = torch.full((B,), K, dtype=torch.int32, device=dev)
+    res = {}
+    for prec in ("split_bf16", "f32"):
+        plan = se2.Plan(N, M, batch=B, precision=prec)
+        tab = se2.separable_tables(plan, params, kk)
+        out = torch.empty_like(f)
+        ms, clocks = _clock_and_time(lambda: se2.convolve_separable(plan, f, tab, out), args.steps, args.warmup, dev)
+        plan.status()
+        res[prec] = (B * args.steps / (ms / 1e3), ms, out[0].double().cpu().numpy(), clocks)
+        plan.close()
+    F0 = f[0].double().cpu().numpy()
+    coeffs = []
+    for kp in probs[0].kernels:
+        gx, gy, gt = synth.kernel_factors(N, M, kp)
+        coeffs.append(O.coeffs_separable(gx, gy, gt))
+    want = O.convolve_chain(F0, None, coeffs=coeffs)
+    err = {p: float(np.max(np.abs(res[p][2] - want)) / np.max(np.abs(want))) for p in res}
+    v, ms, _, clocks = res["split_bf16"]
+    _line("SE(2) convolutions/s at N=512, M=128, 32-fold chain: split-bf16 tensor-core angular DFT",
+          v, "conv/s", args, ms,
+          {"workload": "batch 8, 32-bump f1 with amplitudes log-uniform in [1e-6, 1], 32-fold separable chain",
+           "grid": [M, N, N]},
+          {"fp32_value": res["f32"][0], "max_rel_err_vs_fp64_oracle": err, "clocks": clocks,
+           "gpu_launches": 5 * args.steps})
 
 
 def run_adjoint(args):

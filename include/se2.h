@@ -58,7 +58,11 @@ typedef enum {
 
 typedef enum {
     SE2_F64 = 0,              /* double storage and arithmetic                */
-    SE2_F32 = 1               /* float storage and arithmetic, FP64 tables    */
+    SE2_F32 = 1,              /* float storage and arithmetic, FP64 tables    */
+    SE2_SPLIT_BF16 = 2,       /* float storage; the angular DFT (M = 64, 128)
+                                 runs on the tensor cores with bf16 hi + lo
+                                 operands (3 products), FP32 accumulation      */
+    SE2_BF16 = 3              /* as SE2_SPLIT_BF16 with one bf16 product      */
 } se2_precision;
 
 /* Plan flags */

@@ -23,6 +23,9 @@ LIB_PATH = os.path.join(_HERE, "lib", "libse2.so")
 
 F64 = 0
 F32 = 1
+SPLIT_BF16 = 2
+BF16 = 3
+_PRECISIONS = {"f64": F64, "f32": F32, "split_bf16": SPLIT_BF16, "bf16": BF16}
 SHARED_KERNEL = 0x1
 PERSISTENT = 0x2
 
@@ -89,16 +92,15 @@ class Plan:
     def __init__(self, N: int, M: int, batch: int = 1, precision: str = "f32", flags: int = 0,
                  device: Optional[int] = None):
         lib = load_library()
-        if precision not in ("f32", "f64"):
-            raise ValueError("precision must be 'f32' or 'f64'")
+        if precision not in _PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
         self.N, self.M, self.batch, self.flags = N, M, batch, flags
         self.precision = precision
         self.device = torch.cuda.current_device() if device is None else int(device)
-        self.dtype = torch.float32 if precision == "f32" else torch.float64
-        self.cdtype = torch.complex64 if precision == "f32" else torch.complex128
+        self.dtype = torch.float64 if precision == "f64" else torch.float32
+        self.cdtype = torch.complex128 if precision == "f64" else torch.complex64
         h = ctypes.c_void_p()
-        _check(lib.se2_plan_create(ctypes.byref(h), N, M, batch, F32 if precision == "f32" else F64,
-                                   flags, self.device))
+        _check(lib.se2_plan_create(ctypes.byref(h), N, M, batch, _PRECISIONS[precision], flags, self.device))
         self._h = h
 
     @property

@@ -15,6 +15,7 @@
 
 #include "../../include/se2.h"
 #include "se2_internal.h"
+#include "se2_tc.cuh"
 
 using namespace se2;
 
@@ -74,6 +75,12 @@ struct se2_plan_s {
     unsigned* ctr = nullptr;    // [1 + 3 * batch] work counter + unit counters
     int* err = nullptr;         // sticky device error word
     int nslots = 0;             // problem slots in the scratch (>= 2)
+    // mixed precision: angular DFT on the tensor cores (0 = off, 1 or 3 products)
+    int tc = 0;
+    void* tcB = nullptr;        // B images: [dir -1: hi, lo][dir +1: hi, lo]
+    TcKernel tc_fwd = nullptr, tc_inv = nullptr;
+    size_t tc_smem = 0;
+    int nsm = 0;
     double* tab = nullptr;      // [2N + 2M] FP64 tables of the Gaussian kernel family
     KTable<float> kf;
     KTable<double> kd;
@@ -138,6 +145,28 @@ se2_status plan_init(se2_plan_s* p) {
         p->persist_grid = per_sm * nsm;
     }
     p->elem = sizeof(c2<T>);
+    if (p->prec == SE2_SPLIT_BF16 || p->prec == SE2_BF16) {
+        p->tc = p->prec == SE2_SPLIT_BF16 ? 3 : 1;
+        p->fused = false;                    // x and theta as separate passes
+        p->persist = false;
+        if (!tc_kernel(p->M, -1, p->tc, &p->tc_fwd, &p->tc_smem) || !tc_kernel(p->M, +1, p->tc, &p->tc_inv, &p->tc_smem))
+            return fail(SE2_ERR_UNSUPPORTED, "tensor-core angular DFT needs M = 64 or 128 (M=%d)", p->M);
+        cudaError_t r = cudaFuncSetAttribute((const void*)p->tc_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->tc_smem);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute((const void*)p->tc_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->tc_smem);
+        if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
+        std::vector<unsigned char> img, all;
+        tc_dft_matrix(-1, img);
+        all.insert(all.end(), img.begin(), img.end());
+        tc_dft_matrix(+1, img);
+        all.insert(all.end(), img.begin(), img.end());
+        r = cudaMalloc(&p->tcB, all.size());
+        if (r != cudaSuccess) return fail(SE2_ERR_OOM, "tensor-core DFT matrix: %s", cudaGetErrorString(r));
+        r = cudaMemcpy(p->tcB, all.data(), all.size(), cudaMemcpyHostToDevice);
+        if (r != cudaSuccess) return cuda_fail(r, "cudaMemcpy");
+        r = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev);
+        if (r != cudaSuccess) return cuda_fail(r, "device attribute");
+    }
     cudaError_t e;
     if ((e = cudaMalloc(&p->twN, sizeof(c2<T>) * p->N)) != cudaSuccess) return fail(SE2_ERR_OOM, "twiddles: %s", cudaGetErrorString(e));
     if ((e = cudaMalloc(&p->twM, sizeof(c2<T>) * p->M)) != cudaSuccess) return fail(SE2_ERR_OOM, "twiddles: %s", cudaGetErrorString(e));
@@ -150,6 +179,8 @@ void plan_free(se2_plan_s* p) {
     if (p->ctr) cudaFree(p->ctr);
     if (p->err) cudaFree(p->err);
     if (p->tab) cudaFree(p->tab);
+    if (p->tcB) cudaFree(p->tcB);
+    p->tcB = nullptr;
     p->ctr = nullptr;
     p->err = nullptr;
     p->tab = nullptr;
@@ -162,6 +193,9 @@ void plan_free(se2_plan_s* p) {
 }
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+// FP64 plans use double kernels; every other precision keeps float storage.
+bool is_f64(const se2_plan_s* p) { return p->prec == SE2_F64; }
 
 // Polls before a device-side wait gives up (each poll sleeps ~64 ns plus an
 // L2 round trip, so this is of the order of a second).
@@ -181,6 +215,27 @@ XArgs<T> xargs(se2_plan_s* p, int slot0 = 0) {
     a.twN = (const c2<T>*)p->twN;
     a.twM = (const c2<T>*)p->twM;
     return a;
+}
+
+// Angular DFT of nb scratch spectra on the tensor cores (mixed precision).
+template <typename T>
+void launch_tc(se2_plan_s* p, c2<T>* s, int nb, int dir, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        TcArgs t{};
+        t.s = s;
+        t.s_pstride = p->s_pstride;
+        t.N = p->N;
+        t.tp = p->tp;
+        t.bmat = reinterpret_cast<const uint4*>((const unsigned char*)p->tcB + (dir < 0 ? 0 : 2 * kTcOpBytes));
+        t.tw = (const float2*)p->twM;
+        t.err = p->err;
+        const long long lines = (long long)p->N * (p->N / 2 + 1);
+        const int tiles = (int)((lines + kTcLines - 1) / kTcLines);
+        int gx = (p->nsm + nb - 1) / nb;
+        if (gx > tiles) gx = tiles;
+        if (gx < 1) gx = 1;
+        (dir < 0 ? p->tc_fwd : p->tc_inv)<<<dim3(gx, nb), kTcLines, p->tc_smem, st>>>(t);
+    }
 }
 
 // Forward x and theta transforms of nb real grids into the scratch.
@@ -205,7 +260,8 @@ void launch_forward(se2_plan_s* p, const T* f, int nb, double* abs_sum, cudaStre
         l.N = p->N;
         l.tw = (const c2<T>*)p->twM;
         const long long lines = (long long)p->N * (p->N / 2 + 1);
-        kt.t_fwd<<<dim3((unsigned)((lines + kt.lines_t - 1) / kt.lines_t), nb), kThreads, kt.smem_t, st>>>(l);
+        if (p->tc) launch_tc<T>(p, a.s, nb, -1, st);
+        else kt.t_fwd<<<dim3((unsigned)((lines + kt.lines_t - 1) / kt.lines_t), nb), kThreads, kt.smem_t, st>>>(l);
     }
 }
 
@@ -227,7 +283,8 @@ void launch_inverse(se2_plan_s* p, T* out, int nb, cudaStream_t st, int slot0 = 
         l.N = p->N;
         l.tw = (const c2<T>*)p->twM;
         const long long lines = (long long)p->N * (p->N / 2 + 1);
-        kt.t_inv<<<dim3((unsigned)((lines + kt.lines_t - 1) / kt.lines_t), nb), kThreads, kt.smem_t, st>>>(l);
+        if (p->tc) launch_tc<T>(p, a.s, nb, +1, st);
+        else kt.t_inv<<<dim3((unsigned)((lines + kt.lines_t - 1) / kt.lines_t), nb), kThreads, kt.smem_t, st>>>(l);
         const int pairs = p->M / 2;
         kt.inv_x<<<dim3(p->N, (pairs + kt.teams_x - 1) / kt.teams_x, nb), kThreads, kt.smem_x, st>>>(a);
     }
@@ -426,7 +483,8 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (!is_pow2(N) || N < 8 || N > 512) return fail(SE2_ERR_UNSUPPORTED, "N=%d: need a power of two in [8, 512]", N);
     if (!is_pow2(M) || M < 2 || M > 128) return fail(SE2_ERR_UNSUPPORTED, "M=%d: need a power of two in [2, 128]", M);
     if (batch < 1) return fail(SE2_ERR_INVALID_ARG, "batch=%d must be >= 1", batch);
-    if (precision != SE2_F32 && precision != SE2_F64) return fail(SE2_ERR_UNSUPPORTED, "precision %d not supported", (int)precision);
+    if (precision != SE2_F32 && precision != SE2_F64 && precision != SE2_SPLIT_BF16 && precision != SE2_BF16)
+        return fail(SE2_ERR_UNSUPPORTED, "precision %d not supported", (int)precision);
     if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT)) return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -444,7 +502,7 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     p->flags = flags;
     p->tp = ((N / 2 + 1) + 15) / 16 * 16;           // 128-byte aligned scratch rows (FP32)
     p->s_pstride = (size_t)M * N * p->tp;
-    se2_status st = (precision == SE2_F32) ? plan_init<float>(p) : plan_init<double>(p);
+    se2_status st = (precision != SE2_F64) ? plan_init<float>(p) : plan_init<double>(p);
     if (st != SE2_OK) { plan_free(p); delete p; return st; }
     // scratch for `chunk` problems at a time (whole batch up to 1 GiB);
     // SE2_MAX_CHUNK (environment) caps it, e.g. to exercise ragged chunks.
@@ -506,7 +564,7 @@ se2_status se2_coeffs(se2_plan_t p, const void* samples, int n, void* coeffs, do
         return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
-    return p->prec == SE2_F32 ? run_coeffs<float>(p, samples, n, coeffs, log_scale, s)
+    return !is_f64(p) ? run_coeffs<float>(p, samples, n, coeffs, log_scale, s)
                               : run_coeffs<double>(p, samples, n, coeffs, log_scale, s);
 }
 
@@ -527,7 +585,7 @@ se2_status se2_convolve_chain(se2_plan_t p, const void* f, int B, const void* co
     if (f == out) return fail(SE2_ERR_INVALID_ARG, "out aliases f");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
-    return p->prec == SE2_F32 ? run_chain<float>(p, f, B, coeffs, log_scales, k, out, s)
+    return !is_f64(p) ? run_chain<float>(p, f, B, coeffs, log_scales, k, out, s)
                               : run_chain<double>(p, f, B, coeffs, log_scales, k, out, s);
 }
 
@@ -551,7 +609,7 @@ se2_status se2_backward(se2_plan_t p, const void* grad_out, const void* f, int B
     if (grad_f != nullptr && (grad_f == grad_out || grad_f == f)) return fail(SE2_ERR_INVALID_ARG, "grad_f aliases an input");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
-    return p->prec == SE2_F32
+    return !is_f64(p)
                ? run_backward<float>(p, grad_out, f, B, coeffs, log_scale, n_params, dcoeffs, grad_params, grad_f, s)
                : run_backward<double>(p, grad_out, f, B, coeffs, log_scale, n_params, dcoeffs, grad_params, grad_f, s);
 }
@@ -570,7 +628,7 @@ se2_status se2_sample_radial_gaussian(se2_plan_t p, double sigma, double sigma_t
     k_gauss_tables<<<(p->N + p->M + 127) / 128, 128, 0, s>>>(p->tab, p->N, p->M, sigma, sigma_theta, nu);
     const long long total = (long long)p->N * p->N * p->M;
     const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-    if (p->prec == SE2_F32)
+    if (!is_f64(p))
         k_gauss_fill<float><<<blocks, 256, 0, s>>>(p->tab, p->N, p->M, (float*)P, (float*)dP_dsigma, (float*)dP_dsigma_theta);
     else
         k_gauss_fill<double><<<blocks, 256, 0, s>>>(p->tab, p->N, p->M, (double*)P, (double*)dP_dsigma, (double*)dP_dsigma_theta);
@@ -590,7 +648,7 @@ se2_status se2_separable_tables(se2_plan_t p, const double* params, const int* k
     cudaStream_t s = (cudaStream_t)stream;
     const long long tps = (long long)(p->N / 2 + 1 + p->N + p->M);
     const size_t sm = sizeof(double) * 3 * ((size_t)p->N + p->M);
-    if (p->prec == SE2_F32)
+    if (!is_f64(p))
         k_sep_tables<float><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (float2*)tables, tps);
     else
         k_sep_tables<double><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (double2*)tables, tps);
@@ -609,7 +667,7 @@ se2_status se2_convolve_separable(se2_plan_t p, const void* f, int B, const void
     if (f == out) return fail(SE2_ERR_INVALID_ARG, "out aliases f");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
-    return p->prec == SE2_F32 ? run_sep<float>(p, f, B, tables, out, s) : run_sep<double>(p, f, B, tables, out, s);
+    return !is_f64(p) ? run_sep<float>(p, f, B, tables, out, s) : run_sep<double>(p, f, B, tables, out, s);
 }
 
 se2_status se2_plan_status(se2_plan_t p, void* stream) {

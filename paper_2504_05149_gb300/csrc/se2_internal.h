@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "se2_kernels.cuh"
 
 namespace se2 {
@@ -49,6 +51,12 @@ bool get_kernels(int N, int M, KTable<T>* kt) {
         default: return false;
     }
 }
+
+// Tensor-core angular DFT (se2_tc.cu).
+struct TcArgs;
+using TcKernel = void (*)(TcArgs);
+bool tc_kernel(int M, int dir, int split, TcKernel* out, size_t* smem);
+void tc_dft_matrix(int dir, std::vector<unsigned char>& img);
 
 // Sets the thread-local text returned by se2_last_error().
 void set_last_error(const char* msg);

@@ -1,0 +1,73 @@
+"""Mixed precision: the angular DFT on the tensor cores (tcgen05, bf16 hi+lo
+split or one bf16 product, FP32 accumulation) against the FP64 oracle, beside
+the plain FP32 path.  Bars: 1e-3 relative for the split-bf16 mode (its error
+is reported, and in practice near 1e-5), 1e-2 for one bf16 product."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth  # noqa: E402
+from oracle import se2_oracle as O  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def se2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_05149_gb300 import build as b
+    b.build()
+    import paper_2504_05149_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("N,M,B", [(64, 64, 3), (128, 64, 2), (32, 128, 3), (256, 128, 1)])
+def test_split_bf16_and_bf16_vs_oracle(se2, N, M, B):
+    rng = np.random.default_rng(N + M)
+    F = rng.standard_normal((B, M, N, N)).astype(np.float32)
+    P = rng.random((B, M, N, N)).astype(np.float32)
+    errs = {}
+    for prec in ("f32", "split_bf16", "bf16"):
+        plan = se2.Plan(N, M, batch=B, precision=prec)
+        C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
+        out = se2.convolve(plan, torch.from_numpy(F).cuda(), C).double().cpu().numpy()
+        plan.status()
+        errs[prec] = max(_rel(out[b], O.convolve(F[b].astype(np.float64), P[b].astype(np.float64))) for b in range(B))
+    assert errs["f32"] < 3e-6
+    assert errs["split_bf16"] < 1e-3
+    assert errs["bf16"] < 2e-2
+    assert errs["split_bf16"] < errs["bf16"]
+    print("max-rel errors", errs)
+
+
+def test_precision_config_chain_log_amplitudes(se2):
+    """Precision-config shape at reduced size: 32-bump f1 with amplitudes
+    log-uniform in [1e-6, 1] and a 32-fold separable kernel chain."""
+    N, M = 128, 128
+    prob = synth.make_problem(3, 0, N, M, n_bumps=32, n_kernels=32, log_amp=True)
+    F = synth.sample_bumps(N, M, prob.bumps).astype(np.float32)
+    params = torch.zeros((1, 32, 3), dtype=torch.float64)
+    for j, kp in enumerate(prob.kernels):
+        params[0, j] = torch.tensor([kp.sigma, kp.sigma_theta, kp.nu])
+    coeffs = []
+    for kp in prob.kernels:
+        gx, gy, gt = synth.kernel_factors(N, M, kp)
+        coeffs.append(O.coeffs_separable(gx, gy, gt))
+    want = O.convolve_chain(F.astype(np.float64), None, coeffs=coeffs)
+    for prec, tol in (("f32", 1e-5), ("split_bf16", 1e-3)):
+        plan = se2.Plan(N, M, batch=1, precision=prec)
+        tab = se2.separable_tables(plan, params.cuda(), torch.tensor([32], dtype=torch.int32).cuda())
+        out = se2.convolve_separable(plan, torch.from_numpy(F[None]).cuda(), tab)[0].double().cpu().numpy()
+        plan.status()
+        assert _rel(out, want) < tol, prec
+
+
+def test_tc_unsupported_angular_size(se2):
+    with pytest.raises(se2.SE2Error) as ei:
+        se2.Plan(64, 32, batch=1, precision="split_bf16")
+    assert ei.value.status == 2
