@@ -47,6 +47,8 @@ def parse():
                     help="c2: single convolutions at 256^2x64 (the headline); c2chain: 8-fold chains; "
                          "c4: 4096 uneven problems with separable chains (CUDA graph); c5: forward+adjoint")
     ap.add_argument("--problems", type=int, default=4096, help="c4 batch size")
+    ap.add_argument("--precision", default="f32", choices=["f32", "split_bf16", "bf16"],
+                    help="c2: arithmetic of the angular DFT (tensor cores for split_bf16 / bf16)")
     return ap.parse_args()
 
 
@@ -196,7 +198,7 @@ def main():
     L = N * N * M
 
     F, P = workload_inputs(N, M, B, rank)
-    plan = se2.Plan(N, M, batch=B, precision="f32", device=local)
+    plan = se2.Plan(N, M, batch=B, precision=args.precision, device=local)
     f = torch.from_numpy(F).to(dev)
     C, _ = se2.coeffs(plan, torch.from_numpy(P).to(dev))
     out = torch.empty_like(f)
@@ -279,7 +281,8 @@ def main():
             "metric": "SE(2) convolutions/s at N=256, M=64 (FP32) and fraction of HBM roofline",
             "value": value, "unit": "conv/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": "f32" if args.precision == "f32" else f"f32 storage, {args.precision} tensor-core angular DFT",
+            "data": "synthetic",
             "config": {"workload": f"se2_convolve, batch of {B} independent problems per GPU, N={N}, M={M}, "
                                    f"one radial kernel per problem (precomputed spectra), 16-bump f1",
                        "global_batch": B * world, "grid": [M, N, N], "parallelism": f"replicas x{world}",

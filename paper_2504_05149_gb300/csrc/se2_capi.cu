@@ -234,7 +234,7 @@ void launch_tc(se2_plan_s* p, c2<T>* s, int nb, int dir, cudaStream_t st) {
         int gx = (p->nsm + nb - 1) / nb;
         if (gx > tiles) gx = tiles;
         if (gx < 1) gx = 1;
-        (dir < 0 ? p->tc_fwd : p->tc_inv)<<<dim3(gx, nb), kTcLines, p->tc_smem, st>>>(t);
+        (dir < 0 ? p->tc_fwd : p->tc_inv)<<<dim3(gx, nb), kTcThreads, p->tc_smem, st>>>(t);
     }
 }
 

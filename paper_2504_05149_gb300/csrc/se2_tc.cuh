@@ -24,6 +24,7 @@
 namespace se2 {
 
 constexpr int kTcLines = 128;            // lines per tile (tensor-memory lanes)
+constexpr int kTcThreads = 256;          // two threads per line
 constexpr int kTcK = 128;                // K of one contraction (64 complex samples)
 constexpr int kTcOpBytes = kTcLines * kTcK * 2;   // one bf16 operand: 32 KB
 
@@ -88,7 +89,7 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 }
 
 template <int M, int DIR, int SPLIT>
-__global__ void __launch_bounds__(kTcLines, 1) k_theta_tc(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
     static_assert(M == 64 || M == 128, "tensor-core angular DFT: M = 64 or 128");
     constexpr int NPART = (M == 128) ? 2 : 1;              // even / odd contractions
     constexpr int NLO = (SPLIT == 3) ? 1 : 0;
@@ -97,7 +98,8 @@ __global__ void __launch_bounds__(kTcLines, 1) k_theta_tc(TcArgs a) {
     unsigned char* sA = smem + (1 + NLO) * kTcOpBytes;     // per part: A_hi [, A_lo]
     __shared__ uint32_t tmem_base;
     __shared__ __align__(8) uint64_t mbar;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid % kTcLines, half = tid / kTcLines;   // line of the tile, which half of it
     const int b = blockIdx.y;
     const int H = a.N / 2 + 1;
     const long long nlines = (long long)a.N * H;
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(kTcLines, 1) k_theta_tc(TcArgs a) {
     {
         const uint4* src = a.bmat;
         uint4* dst = reinterpret_cast<uint4*>(sB);
-        for (int i = tid; i < (1 + NLO) * kTcOpBytes / 16; i += kTcLines) dst[i] = src[i];
+        for (int i = tid; i < (1 + NLO) * kTcOpBytes / 16; i += kTcThreads) dst[i] = src[i];
     }
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
     if (warp == 0) {
@@ -123,38 +125,46 @@ __global__ void __launch_bounds__(kTcLines, 1) k_theta_tc(TcArgs a) {
     uint32_t phase = 0;
 
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const long long line = (long long)tile * kTcLines + tid;
+        const long long line = (long long)tile * kTcLines + row;
         const bool act = line < nlines;
         const int y = act ? (int)(line / H) : 0;
         const int kx = act ? (int)(line - (long long)y * H) : 0;
         float2* base = sp + (size_t)y * a.tp + kx;          // sample l at base + l * N * tp
         const size_t ls = (size_t)a.N * a.tp;
-        // 1. this thread's line -> A rows (8 bf16 = 4 samples per 16-byte store)
-#pragma unroll 1
-        for (int part = 0; part < NPART; ++part) {
+        // 1. this thread's half of its line -> A rows (8 bf16 = 4 samples per
+        //    16-byte store); 16 loads in flight per batch.  M = 128: half =
+        //    even / odd samples (the two contractions); M = 64: half = samples
+        //    [0, 32) / [32, 64) of the one contraction.
+        {
+            const int part = (NPART == 2) ? half : 0;
+            const int lbeg = (NPART == 2) ? 0 : 32 * half;
             unsigned char* Ahi = sA + part * (1 + NLO) * kTcOpBytes;
             unsigned char* Alo = Ahi + kTcOpBytes;
+            constexpr int lcount = (NPART == 2) ? 64 : 32;   // samples of this thread
 #pragma unroll 1
-            for (int l0 = 0; l0 < 64; l0 += 4) {
-                float2 v[4];
+            for (int l0 = lbeg; l0 < lbeg + lcount; l0 += 16) {
+                float2 v[16];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int l = (l0 + q) * NPART + part;      // sample index (even/odd for M = 128)
+                for (int q = 0; q < 16; ++q) {
+                    const int l = (l0 + q) * NPART + part;      // sample index
                     v[q] = act ? __ldcg(base + (size_t)l * ls) : make_float2(0.f, 0.f);
                 }
-                uint32_t h[4], o[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    __nv_bfloat16 hr, lr, hi_, li;
-                    split_bf16(v[q].x, hr, lr);
-                    split_bf16(v[q].y, hi_, li);
-                    // (re, im) -> one 32-bit word, re in the low half (lower address)
-                    h[q] = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi_) << 16);
-                    o[q] = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t h[4], o[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        __nv_bfloat16 hr, lr, hi_, li;
+                        split_bf16(v[4 * g + q].x, hr, lr);
+                        split_bf16(v[4 * g + q].y, hi_, li);
+                        // (re, im) -> one 32-bit word, re in the low half (lower address)
+                        h[q] = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi_) << 16);
+                        o[q] = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
+                    }
+                    const int off = tc_off(row, 2 * (l0 + 4 * g));
+                    *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    if (NLO) *reinterpret_cast<uint4*>(Alo + off) = make_uint4(o[0], o[1], o[2], o[3]);
                 }
-                const int off = tc_off(tid, 2 * l0);
-                *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                if (NLO) *reinterpret_cast<uint4*>(Alo + off) = make_uint4(o[0], o[1], o[2], o[3]);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -190,12 +200,15 @@ __global__ void __launch_bounds__(kTcLines, 1) k_theta_tc(TcArgs a) {
         ok = __syncthreads_and((int)done) != 0;      // one decision for the whole block
         if (!ok && tid == 0) atomicExch(a.err, 2);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // 4. read this warp's lines back and write them in place
+        // 4. read the lines back and write them in place: warps w and w + 4
+        //    share the lanes 32 (w % 4) .. +31 and take columns [0, 64) and
+        //    [64, 128) (output bins [0, 32) and [32, 64) of each contraction)
         if (ok) {
-            const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+            const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+            const int cbeg = 64 * half;
             if constexpr (M == 64) {
 #pragma unroll 1
-                for (int c0 = 0; c0 < 128; c0 += 32) {
+                for (int c0 = cbeg; c0 < cbeg + 64; c0 += 32) {
                     float v[32];
                     tc_ld32(lane_base + c0, v);
                     if (act) {
@@ -206,7 +219,7 @@ __global__ void __launch_bounds__(kTcLines, 1) k_theta_tc(TcArgs a) {
                 }
             } else {
 #pragma unroll 1
-                for (int c0 = 0; c0 < 128; c0 += 32) {
+                for (int c0 = cbeg; c0 < cbeg + 64; c0 += 32) {
                     float e[32], o[32];
                     tc_ld32(lane_base + c0, e);
                     tc_ld32(lane_base + 128 + c0, o);
