@@ -32,6 +32,7 @@ def _nvcc() -> str:
 
 
 SIZES = (8, 16, 32, 64, 128, 256, 512)
+FAST_SIZES = (32, 64, 128, 256)
 
 
 def units():
@@ -45,6 +46,9 @@ def units():
             for t in ("float", "double"):
                 for n in SIZES:
                     out.append((src, f"se2_inst_{t}_{n}.o", [f"-DSE2_T={t}", f"-DSE2_N={n}"]))
+        elif f == "se2_fast.cu":
+            for n in FAST_SIZES:
+                out.append((src, f"se2_fast_{n}.o", [f"-DSE2_FN={n}"]))
         else:
             out.append((src, f + ".o", []))
     return out

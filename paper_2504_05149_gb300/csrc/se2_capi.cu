@@ -85,7 +85,20 @@ struct se2_plan_s {
     KTable<float> kf;
     KTable<double> kd;
     bool fused = false;
+    // FP32 paired-FFT kernels for the convolution and chain (null: generic ones)
+    bool fast = false;
+    FastTable ft;
 };
+
+bool se2::get_fast(int N, int M, FastTable* t) {
+    switch (N) {
+        case 32: return get_fast_n<32>(M, t);
+        case 64: return get_fast_n<64>(M, t);
+        case 128: return get_fast_n<128>(M, t);
+        case 256: return get_fast_n<256>(M, t);
+        default: return false;
+    }
+}
 
 namespace {
 
@@ -166,6 +179,20 @@ se2_status plan_init(se2_plan_s* p) {
         if (r != cudaSuccess) return cuda_fail(r, "cudaMemcpy");
         r = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev);
         if (r != cudaSuccess) return cuda_fail(r, "device attribute");
+    }
+    // FP32 convolutions run on the paired-FFT kernels where they exist;
+    // SE2_FAST=0 (environment) keeps the generic ones (used to test both).
+    if constexpr (sizeof(T) == 4) {
+        const char* fe = getenv("SE2_FAST");
+        if (p->prec == SE2_F32 && p->fused && !p->persist && !(fe && fe[0] == '0') && get_fast(p->N, p->M, &p->ft)) {
+            cudaError_t r = cudaFuncSetAttribute((const void*)p->ft.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_xt);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute((const void*)p->ft.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_xt);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute((const void*)p->ft.lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
+            if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
+            p->fast = true;
+        }
     }
     cudaError_t e;
     if ((e = cudaMalloc(&p->twN, sizeof(c2<T>) * p->N)) != cudaSuccess) return fail(SE2_ERR_OOM, "twiddles: %s", cudaGetErrorString(e));
@@ -357,11 +384,50 @@ se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* c
     return SE2_OK;
 }
 
+// Convolution / chain on the FP32 paired-FFT kernels (paired scratch layout).
+se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* const* coeffs,
+                          const double* const* log_scales, int k, float* out, cudaStream_t st) {
+    const FastTable& ft = p->ft;
+    const size_t g = (size_t)p->N * p->N * p->M;
+    const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
+    const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
+    const long long pairs = (long long)p->M * (p->N / 4 + 1);
+    const unsigned yb = (unsigned)((pairs + ft.lines_per_block - 1) / ft.lines_per_block);
+    for (int c0 = 0; c0 < B; c0 += p->chunk) {
+        const int nb = (B - c0 < p->chunk) ? (B - c0) : p->chunk;
+        FArgs a{};
+        a.f = f + c0 * g;
+        a.out = out + c0 * g;
+        a.s = (float4*)p->scratch;
+        a.s_pstride = (long long)(p->s_pstride / 2);
+        a.tp4 = p->tp / 2;
+        a.twN = (const float2*)p->twN;
+        a.twM = (const float2*)p->twM;
+        a.k = k;
+        a.c_pstride = cps;
+        a.ls_pstride = lps;
+        a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
+        for (int i = 0; i < k; ++i) {
+            a.C[i] = (const float2*)coeffs[i] + c0 * cps;
+            a.ls[i] = (log_scales && log_scales[i]) ? log_scales[i] + c0 * lps : nullptr;
+        }
+        ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+        ft.lines<<<dim3(yb, nb), kThreads, ft.smem_y, st>>>(a);
+        ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
+}
+
 template <typename T>
 se2_status run_chain(se2_plan_s* p, const void* f, int B, const void* const* coeffs,
                      const double* const* log_scales, int k, void* out, cudaStream_t st) {
     KTable<T>& kt = table<T>(p);
     if (p->persist) return run_persist<T>(p, f, B, coeffs, log_scales, k, out, st, 0, kSpinLimit);
+    if constexpr (sizeof(T) == 4) {
+        if (p->fast) return run_chain_fast(p, (const float*)f, B, coeffs, log_scales, k, (float*)out, st);
+    }
     const size_t g = (size_t)p->N * p->N * p->M;
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
     const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;

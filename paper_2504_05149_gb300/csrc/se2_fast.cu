@@ -1,0 +1,41 @@
+// Instantiation of the FP32 paired-FFT convolution kernels for one N
+// (compiled once per N with -DSE2_FN=<N>, in parallel).
+#include "se2_internal.h"
+
+#if !defined(SE2_FN)
+#error "compile with -DSE2_FN=<N>"
+#endif
+
+namespace se2 {
+
+namespace {
+template <int N, int M>
+bool fill_fast_nm(FastTable* t) {
+    constexpr size_t sx = fast_xt_smem<N, M>(), sy = fast_lines_smem<N>();
+    if constexpr (sx <= kMaxDynSmem && sy <= kMaxDynSmem) {
+        t->fwd = kf_fwd_xt<N, M>;
+        t->lines = kf_lines<N, M>;
+        t->inv = kf_inv_tx<N, M>;
+        t->smem_xt = sx;
+        t->smem_y = sy;
+        t->lines_per_block = fast_lines<N>();
+        return true;
+    }
+    return false;
+}
+}  // namespace
+
+template <int N>
+bool get_fast_n(int M, FastTable* t) {
+    switch (M) {
+        case 8: return fill_fast_nm<N, 8>(t);
+        case 16: return fill_fast_nm<N, 16>(t);
+        case 32: return fill_fast_nm<N, 32>(t);
+        case 64: return fill_fast_nm<N, 64>(t);
+        case 128: return fill_fast_nm<N, 128>(t);
+        default: return false;
+    }
+}
+template bool get_fast_n<SE2_FN>(int M, FastTable* t);
+
+}  // namespace se2

@@ -1,0 +1,566 @@
+// FP32 fast path of the three-kernel convolution (units A, B, C of the
+// convolution of Algorithm 3 / the chain of Eq. MatSqKfgG at output grid
+// N = L).  Every FFT here runs on two independent lines at once, one in each
+// half of a float2 register ("paired"), so that each butterfly, twiddle and
+// coefficient product is one sm_100+ f32x2 instruction (add/mul/fma.f32x2)
+// acting on both lines.
+//
+// Scratch layout of this path ("paired spectrum"), Q = N/4, per (theta bin
+// m, y or ky) row of Q + 1 float4 entries:
+//   entry u < Q : (Re X[u], Re X[u+Q], Im X[u], Im X[u+Q])
+//   entry Q     : (Re X[N/2], 0, Im X[N/2], 0)
+// where X[kx] is the spectrum at x frequency kx.  The x-frequency pairs
+// (u, u+Q) are the two lines that the y pass transforms together.  Spectra in
+// this scratch are twice the true ones (the factor 1/2 of the real-FFT split
+// is folded into the product's scale).
+//
+// Shared-memory slab (units A and C): M rows of pitch P = Q + 1 entries, row r
+// at r * P + (r >> 3); with P = 1 (mod 8) the strided row accesses of the
+// angular teams fall in distinct 16-byte bank groups.  The x FFTs exchange
+// through their own four slab rows (no separate buffer).
+#pragma once
+#include "se2_kernels.cuh"
+
+namespace se2 {
+
+// ---------------------------------------------------------------------------
+// Paired FP32 arithmetic
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 pf(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __fadd2_rn(a, pneg(b)); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Two in-register DFTs of R <= 32 points (radix-2 decimation in frequency,
+// natural order in and out), one per half of re/im.  A rotation by +-i is a
+// swap of the real and imaginary registers with a sign that the following
+// butterfly absorbs: in decimation in frequency that rotated element is always
+// the second operand of the next butterfly, so nr/ni never outlive one stage.
+template <int R, int DIR>
+__device__ __forceinline__ void fft2_reg(float2* re, float2* im) {
+    if constexpr (R > 1) {
+        bool nr[R], ni[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) { nr[i] = false; ni[i] = false; }
+#pragma unroll
+        for (int half = R / 2; half >= 1; half >>= 1) {
+#pragma unroll
+            for (int base = 0; base < R; base += 2 * half) {
+#pragma unroll
+                for (int j = 0; j < half; ++j) {
+                    const int a = base + j, b = a + half;
+                    const float2 ar = re[a], ai = im[a], br = re[b], bi = im[b];
+                    float2 sr, si, dr, di;
+                    if (!nr[b]) { sr = padd(ar, br); dr = psub(ar, br); } else { sr = psub(ar, br); dr = padd(ar, br); }
+                    if (!ni[b]) { si = padd(ai, bi); di = psub(ai, bi); } else { si = psub(ai, bi); di = padd(ai, bi); }
+                    re[a] = sr;
+                    im[a] = si;
+                    nr[b] = false;
+                    ni[b] = false;
+                    const int q = j * (16 / half);          // rotation e^{DIR i pi q / 16}
+                    if (q == 0) {
+                        re[b] = dr;
+                        im[b] = di;
+                    } else if (q == 8) {                    // (r, i) * DIR i = (-DIR i, DIR r)
+                        re[b] = di;
+                        nr[b] = (DIR == 1);
+                        im[b] = dr;
+                        ni[b] = (DIR == -1);
+                    } else {
+                        const float c = (float)cpi16(q), s = (float)(DIR * spi16(q));
+                        re[b] = pfma(dr, bc2(c), pmul(di, bc2(-s)));
+                        im[b] = pfma(dr, bc2(s), pmul(di, bc2(c)));
+                    }
+                }
+            }
+        }
+        float2 tr[R], ti[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) { tr[i] = re[i]; ti[i] = im[i]; }
+#pragma unroll
+        for (int i = 0; i < R; ++i) { re[i] = tr[bitrev<R>(i)]; im[i] = ti[bitrev<R>(i)]; }
+    }
+}
+
+// (re + i im) *= w for DIR = -1 and *= conj(w) for DIR = +1, w = (wr, wi) the
+// forward twiddle e^{-2 pi i n / L} broadcast to both halves.
+template <int DIR>
+__device__ __forceinline__ void ptw(float2& re, float2& im, float2 wr, float2 wi) {
+    if constexpr (DIR < 0) {
+        const float2 r = pfma(re, wr, pneg(pmul(im, wi)));
+        im = pfma(re, wi, pmul(im, wr));
+        re = r;
+    } else {
+        const float2 r = pfma(re, wr, pmul(im, wi));
+        im = pfma(im, wr, pneg(pmul(re, wi)));
+        re = r;
+    }
+}
+
+// Exchange slot of step-A output k1 of lane t: row k1 of R2 slots, XOR
+// swizzled so that both the row writes and the column reads are conflict-free.
+template <int R1, int R2>
+__device__ __forceinline__ int xslot(int k1, int t) { return k1 * R2 + (t ^ (k1 & (R2 - 1))); }
+
+// Paired team FFT of length L = R1 * R2 (two lines, one per register half).
+//  in : lane t < R2 holds x[t + R2 j], j < R1
+//  out: lane s < R1 holds X[s + R1 k], k < R2
+// xb: the team's R1 * R2 float4 exchange slots; tw4: forward length-L
+// twiddles as (wr, wr, wi, wi).  Lanes with act = false only synchronise.
+template <int R1, int R2, int DIR, typename Sync>
+__device__ __forceinline__ void team_fft2(float2* re, float2* im, int lane, bool act, float4* xb,
+                                          const float4* tw4, Sync sync) {
+    if constexpr (R2 == 1) {
+        fft2_reg<R1, DIR>(re, im);
+    } else {
+        if (lane < R2) {
+            fft2_reg<R1, DIR>(re, im);
+#pragma unroll
+            for (int k1 = 1; k1 < R1; ++k1) {
+                const float4 w = tw4[lane * k1];
+                ptw<DIR>(re[k1], im[k1], pf(w.x, w.y), pf(w.z, w.w));
+            }
+            if (act) {
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1)
+                    xb[xslot<R1, R2>(k1, lane)] = make_float4(re[k1].x, re[k1].y, im[k1].x, im[k1].y);
+            }
+        }
+        sync();
+        if (lane < R1) {
+            if (act) {
+#pragma unroll
+                for (int t = 0; t < R2; ++t) {
+                    const float4 v = xb[xslot<R1, R2>(lane, t)];
+                    re[t] = pf(v.x, v.y);
+                    im[t] = pf(v.z, v.w);
+                }
+            }
+            fft2_reg<R2, DIR>(re, im);
+        }
+        sync();
+    }
+}
+
+__device__ __forceinline__ constexpr int frow(int r, int P) { return r * P + (r >> 3); }
+template <int N, int M> __host__ __device__ constexpr int fslab4() { return M * (N / 4 + 1) + (M >> 3) + 1; }
+
+// Paired in-place FFT of slab column pair u (rows r at frow(r, P) + u) by a
+// team of team_size<L>() lanes; (wr, wi): this lane's step-A twiddles
+// e^{-2 pi i lane k / L} as broadcast pairs.
+template <int L, int P, int DIR, typename Sync>
+__device__ __forceinline__ void column_fft2(float4* S, int u, int lane, bool act, const float2* wr,
+                                            const float2* wi, Sync sync) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2, RM = reg_count<L>();
+    float2 re[RM], im[RM];
+    if constexpr (R2 == 1) {
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < L; ++r) { const float4 v = S[frow(r, P) + u]; re[r] = pf(v.x, v.y); im[r] = pf(v.z, v.w); }
+            fft2_reg<L, DIR>(re, im);
+#pragma unroll
+            for (int r = 0; r < L; ++r) S[frow(r, P) + u] = make_float4(re[r].x, re[r].y, im[r].x, im[r].y);
+        }
+    } else {
+        if (act && lane < R2) {
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const float4 v = S[frow(lane + R2 * j, P) + u];
+                re[j] = pf(v.x, v.y);
+                im[j] = pf(v.z, v.w);
+            }
+            fft2_reg<R1, DIR>(re, im);
+#pragma unroll
+            for (int k1 = 1; k1 < R1; ++k1) ptw<DIR>(re[k1], im[k1], wr[k1], wi[k1]);
+        }
+        sync();     // every step-A load is done before any step-A store
+        if (act && lane < R2) {
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1)
+                S[frow(k1 + R1 * lane, P) + u] = make_float4(re[k1].x, re[k1].y, im[k1].x, im[k1].y);
+        }
+        sync();
+        if (act && lane < R1) {
+#pragma unroll
+            for (int t = 0; t < R2; ++t) {
+                const float4 v = S[frow(lane + R1 * t, P) + u];
+                re[t] = pf(v.x, v.y);
+                im[t] = pf(v.z, v.w);
+            }
+            fft2_reg<R2, DIR>(re, im);
+#pragma unroll
+            for (int k = 0; k < R2; ++k) S[frow(lane + R1 * k, P) + u] = make_float4(re[k].x, re[k].y, im[k].x, im[k].y);
+        }
+    }
+}
+
+struct FArgs {
+    const float* f;
+    float* out;
+    float4* s;                   // paired scratch of the first problem of the launch
+    long long s_pstride;         // float4 entries per problem
+    int tp4;                     // scratch row pitch (float4)
+    const float2* twN;           // forward twiddles of length N and M
+    const float2* twM;
+    int k;                       // kernels in the chain
+    const float2* C[kMaxChain];  // coefficient arrays [B][M][N][N/2+1] (or shared)
+    const double* ls[kMaxChain]; // per-problem log scales (or null)
+    long long c_pstride, ls_pstride;
+    double inv_L;
+};
+
+__device__ __forceinline__ void fill_tw4(float4* tw, const float2* src, int L) {
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        const float2 w = src[n];
+        tw[n] = make_float4(w.x, w.x, w.y, w.y);
+    }
+}
+
+// This lane's step-A twiddles of the length-M angular team FFT, broadcast.
+template <int M>
+__device__ __forceinline__ void angular_twiddles(const float2* twM, int lm, float2* wr, float2* wi) {
+    constexpr int R1 = Fac<M>::R1, R2 = Fac<M>::R2;
+    const int l = lm < R2 ? lm : 0;
+#pragma unroll
+    for (int k = 0; k < R1; ++k) {
+        const float2 w = twM[(l * k) % M];
+        wr[k] = bc2(w.x);
+        wi[k] = bc2(w.y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Unit A: forward real x FFT of the M theta rows of y row j (rows 4q, 4q+1
+// packed as one complex line, rows 4q+2, 4q+3 as the other half), the split
+// into row spectra, then the paired angular FFT of the slab columns; the DC
+// and Nyquist columns (both real along x) travel as one complex column.
+// ---------------------------------------------------------------------------
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
+    constexpr int Q = N / 4, P = Q + 1;
+    constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
+    constexpr int TEAMS = kThreads / TS, JOBS = M / 4;
+    constexpr int QK = Q / R1;            // register distance between x bins u and u + Q
+    constexpr int HK = N / (2 * R1);      // register of bin N/2 on lane 0
+    constexpr size_t NN = (size_t)N * N;
+    static_assert(Q % R1 == 0 && Q % R2 == 0, "pairing needs N/4 divisible by the radices");
+    extern __shared__ float4 fsm[];
+    float4* S = fsm;
+    float4* TW = fsm + fslab4<N, M>();
+    const int tid = threadIdx.x, j = blockIdx.x, b = blockIdx.y;
+    fill_tw4(TW, a.twN, N);
+    __syncthreads();
+    const uint64_t pin = pol_stream(), pk = pol_keep();
+    const float* fb = a.f + (size_t)b * NN * M + (size_t)j * N;
+    const int team = tid / TS, lane = tid % TS;
+    for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
+        const int q = q0 + team;
+        const bool act = q < JOBS;
+        float2 re[RM], im[RM];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
+        if (act && lane < R2) {
+            const float* r0 = fb + (size_t)(4 * q) * NN;
+#pragma unroll
+            for (int jj = 0; jj < R1; ++jj) {
+                const int x = lane + R2 * jj;
+                re[jj] = pf(ld_in(r0 + x, pin), ld_in(r0 + 2 * NN + x, pin));
+                im[jj] = pf(ld_in(r0 + NN + x, pin), ld_in(r0 + 3 * NN + x, pin));
+            }
+        }
+        float4* xb = S + frow(4 * (act ? q : 0), P);
+        team_fft2<R1, R2, -1>(re, im, lane, act, xb, TW, SyncWarp());
+        // lane s < R1 holds Z[s + R1 k], k < R2 (half a: rows 4q/4q+1, b: 4q+2/4q+3)
+        if (act && lane < R1) {
+#pragma unroll
+            for (int k = 0; k < R2; ++k) xb[lane + R1 * k] = make_float4(re[k].x, re[k].y, im[k].x, im[k].y);
+        }
+        __syncwarp();
+        float4 zm[HK + 1];
+        if (act && lane < R1) {
+#pragma unroll
+            for (int k = 0; k <= HK; ++k) {
+                const int kk = lane + R1 * k;
+                zm[k] = kk <= N / 2 ? xb[(N - kk) & (N - 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncwarp();   // every read of Z is done before the rows take the spectra
+        if (act && lane < R1) {
+            // X0 = Z + conj Z[N-k], X1 = -i (Z - conj Z[N-k]): twice the spectra of the two rows
+            float4* row0 = S + frow(4 * q, P);
+            const float2 n0 = padd(re[HK], pf(zm[HK].x, zm[HK].y));   // Re X0[N/2] (lane 0)
+            const float2 n1 = padd(im[HK], pf(zm[HK].z, zm[HK].w));   // Re X1[N/2]
+#pragma unroll
+            for (int k = 0; k < QK; ++k) {
+                const int u = lane + R1 * k, h = k + QK;
+                const float2 lr = pf(zm[k].x, zm[k].y), li = pf(zm[k].z, zm[k].w);
+                const float2 hr = pf(zm[h].x, zm[h].y), hi = pf(zm[h].z, zm[h].w);
+                const float2 a0r = padd(re[k], lr), a0i = psub(im[k], li), a1r = padd(im[k], li), a1i = psub(lr, re[k]);
+                const float2 b0r = padd(re[h], hr), b0i = psub(im[h], hi), b1r = padd(im[h], hi), b1i = psub(hr, re[h]);
+                float4 e0 = make_float4(a0r.x, b0r.x, a0i.x, b0i.x);
+                float4 e1 = make_float4(a1r.x, b1r.x, a1i.x, b1i.x);
+                float4 e2 = make_float4(a0r.y, b0r.y, a0i.y, b0i.y);
+                float4 e3 = make_float4(a1r.y, b1r.y, a1i.y, b1i.y);
+                if (k == 0 && lane == 0) {   // X[0], X[N/2] are real: one complex DC entry
+                    e0.z = n0.x;
+                    e1.z = n1.x;
+                    e2.z = n0.y;
+                    e3.z = n1.y;
+                }
+                row0[u] = e0;
+                row0[P + u] = e1;
+                row0[2 * P + u] = e2;
+                row0[3 * P + u] = e3;
+            }
+        }
+    }
+    __syncthreads();
+    {
+        constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
+        const int tm = tid / TSM, lm = tid % TSM;
+        float2 wr[Fac<M>::R1], wi[Fac<M>::R1];
+        angular_twiddles<M>(a.twM, lm, wr, wi);
+        for (int c0 = 0; c0 < Q; c0 += TEAMSM) {
+            const int u = c0 + tm;
+            const bool act = u < Q;
+            column_fft2<M, P, -1>(S, act ? u : 0, lm, act, wr, wi, SyncWarp());
+        }
+    }
+    __syncthreads();
+    // split the DC column's transform Y = F(X[.,0] + i X[.,N/2]) into the two
+    // real columns' transforms: (Y + conj Y[-m]) / 2 and (Y - conj Y[-m]) / 2i
+    float4 yv = make_float4(0.f, 0.f, 0.f, 0.f), ym = yv;
+    if (tid < M) {
+        yv = S[frow(tid, P)];
+        ym = S[frow((M - tid) & (M - 1), P)];
+    }
+    __syncthreads();
+    if (tid < M) {
+        float4 e = yv;
+        e.x = 0.5f * (yv.x + ym.x);
+        e.z = 0.5f * (yv.z - ym.z);
+        S[frow(tid, P)] = e;
+        S[frow(tid, P) + Q] = make_float4(0.5f * (yv.z + ym.z), 0.f, 0.5f * (ym.x - yv.x), 0.f);
+    }
+    __syncthreads();
+    {
+        float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * a.tp4;
+        for (int e = tid; e < M * P; e += kThreads) {
+            const int r = e / P, u = e - r * P;
+            st_s4(sb + (size_t)r * N * a.tp4 + u, S[frow(r, P) + u], pk);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Unit B: for LINES pairs of (theta bin, x bins u, u + N/4) lines: paired FFT
+// along y, multiply by W^k C_1 ... C_k exp(sum ls) / |L| (and the 1/2 of the
+// split), inverse FFT along y, in place.
+// ---------------------------------------------------------------------------
+template <int N> __host__ __device__ constexpr int fast_xs() { return N + 2; }   // = 2 (mod 8) float4
+template <int N> __host__ __device__ constexpr int fast_lines() { return kThreads / team_size<N>(); }
+
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
+    constexpr int Q = N / 4, P1 = Q + 1, CP = N / 2 + 1;
+    constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, RM = reg_count<N>();
+    constexpr int LINES = fast_lines<N>(), XS = fast_xs<N>();
+    static_assert(R1 % 2 == 0, "ky parity is the lane parity");
+    extern __shared__ float4 fsm[];
+    float4* XB = fsm;
+    float4* TW = fsm + LINES * XS;
+    __shared__ double sh_scale;
+    const int tid = threadIdx.x, b = blockIdx.y;
+    fill_tw4(TW, a.twN, N);
+    if (tid == 0) {
+        double lsum = 0;
+        for (int i = 0; i < a.k; ++i)
+            if (a.ls[i] != nullptr) lsum += a.ls[i][b * a.ls_pstride];
+        sh_scale = 0.5 * a.inv_L * exp(lsum);
+    }
+    __syncthreads();
+    const int c = tid % LINES, t = tid / LINES;
+    const int pl = blockIdx.x * LINES + c;
+    const bool act = pl < M * P1;
+    const int o = act ? pl / P1 : 0, u = act ? pl - (pl / P1) * P1 : 0;
+    float4* base = a.s + (size_t)b * a.s_pstride + (size_t)o * N * a.tp4 + u;
+    float4* xb = XB + c * XS;
+    const uint64_t pk = pol_keep(), pin = pol_stream();
+    float2 re[RM], im[RM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
+    if (act && t < R2) {
+#pragma unroll
+        for (int jj = 0; jj < R1; ++jj) {
+            const float4 v = ld_s4(base + (size_t)(t + R2 * jj) * a.tp4, pk);
+            re[jj] = pf(v.x, v.y);
+            im[jj] = pf(v.z, v.w);
+        }
+    }
+    team_fft2<R1, R2, -1>(re, im, t, act, xb, TW, SyncBlock());
+    // lane s < R1 holds ky = s + R1 k, k < R2
+    if (act && t < R1) {
+        const bool hasb = u < Q;
+        const int kxa = hasb ? u : N / 2;
+        const float sc = (float)sh_scale;
+        const bool neg = (a.k & 1) && ((u + t) & 1);        // W^k at (kx, ky), both halves alike
+        const float2 s2 = bc2(neg ? -sc : sc);
+        for (int i = 0; i < a.k; ++i) {
+            const float2* cb = a.C[i] + (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa + (size_t)t * CP;
+            float2 ca[R2], cq[R2];
+#pragma unroll
+            for (int k = 0; k < R2; ++k) {
+                ca[k] = ld_in(cb + (size_t)(R1 * k) * CP, pin);
+                cq[k] = hasb ? ld_in(cb + (size_t)(R1 * k) * CP + Q, pin) : pf(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < R2; ++k) {
+                const float2 cr = pf(ca[k].x, cq[k].x), ci = pf(ca[k].y, cq[k].y);
+                const float2 r = pfma(re[k], cr, pneg(pmul(im[k], ci)));
+                im[k] = pfma(re[k], ci, pmul(im[k], cr));
+                re[k] = r;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R2; ++k) {
+            re[k] = pmul(re[k], s2);
+            im[k] = pmul(im[k], s2);
+        }
+    }
+    team_fft2<R2, R1, +1>(re, im, t, act, xb, TW, SyncBlock());
+    if (act && t < R2) {
+#pragma unroll
+        for (int k = 0; k < R1; ++k)
+            st_s4(base + (size_t)(t + R2 * k) * a.tp4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y), pk);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Unit C: paired inverse angular FFT of the slab columns (DC and Nyquist
+// columns recombined into one complex column first), then the inverse x FFTs
+// of row pairs (4q, 4q+1) and (4q+2, 4q+3) as the two halves.
+// ---------------------------------------------------------------------------
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
+    constexpr int Q = N / 4, P = Q + 1;
+    constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
+    constexpr int TEAMS = kThreads / TS, JOBS = M / 4;
+    constexpr int QJ = Q / R2, HJ = N / (2 * R2);
+    constexpr size_t NN = (size_t)N * N;
+    constexpr int LOADS = (M * P + kThreads - 1) / kThreads;
+    extern __shared__ float4 fsm[];
+    float4* S = fsm;
+    float4* TW = fsm + fslab4<N, M>();
+    const int tid = threadIdx.x, j = blockIdx.x, b = blockIdx.y;
+    const uint64_t pk = pol_keep(), po = pol_stream();
+    fill_tw4(TW, a.twN, N);
+    {
+        const float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * a.tp4;
+        float4 v[LOADS];
+#pragma unroll
+        for (int i = 0; i < LOADS; ++i) {
+            const int e = tid + kThreads * i;
+            if (e < M * P) {
+                const int r = e / P, u = e - r * P;
+                v[i] = ld_s4(sb + (size_t)r * N * a.tp4 + u, pk);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < LOADS; ++i) {
+            const int e = tid + kThreads * i;
+            if (e < M * P) {
+                const int r = e / P, u = e - r * P;
+                S[frow(r, P) + u] = v[i];
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < M) {   // DC column + i * Nyquist column
+        float4 e = S[frow(tid, P)];
+        const float4 ny = S[frow(tid, P) + Q];
+        e.x -= ny.z;
+        e.z += ny.x;
+        S[frow(tid, P)] = e;
+    }
+    __syncthreads();
+    {
+        constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
+        const int tm = tid / TSM, lm = tid % TSM;
+        float2 wr[Fac<M>::R1], wi[Fac<M>::R1];
+        angular_twiddles<M>(a.twM, lm, wr, wi);
+        for (int c0 = 0; c0 < Q; c0 += TEAMSM) {
+            const int u = c0 + tm;
+            const bool act = u < Q;
+            column_fft2<M, P, +1>(S, act ? u : 0, lm, act, wr, wi, SyncWarp());
+        }
+    }
+    __syncthreads();
+    // entry (m, 0) now holds (X_m[0], X_m[Q].re, X_m[N/2], X_m[Q].im) with
+    // X_m[0], X_m[N/2] real
+    const int team = tid / TS, lane = tid % TS;
+    float* ob = a.out + (size_t)b * NN * M + (size_t)j * N;
+    for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
+        const int q = q0 + team;
+        const bool act = q < JOBS;
+        float2 re[RM], im[RM];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
+        const float4* row0 = S + frow(4 * (act ? q : 0), P);
+        if (act && lane < R2) {
+            // Z_a[kk] = X_{4q}[kk] + i X_{4q+1}[kk], Z_b likewise with rows 4q+2, 4q+3,
+            // kk = lane + R2 jj; bins above N/2 are conjugates of N - kk
+#pragma unroll
+            for (int jj = 0; jj < QJ; ++jj) {
+                const int e = lane + R2 * jj;
+                const float4 v0 = row0[e], v1 = row0[P + e], v2 = row0[2 * P + e], v3 = row0[3 * P + e];
+                const bool dc = (jj == 0) && lane == 0;
+                // kk = e (low half; the DC entry's imaginary slot holds X[N/2])
+                const float i0 = dc ? 0.f : v0.z, i1 = dc ? 0.f : v1.z, i2 = dc ? 0.f : v2.z, i3 = dc ? 0.f : v3.z;
+                re[jj] = pf(v0.x - i1, v2.x - i3);
+                im[jj] = pf(i0 + v1.x, i2 + v3.x);
+                // kk = e + Q (high half)
+                re[jj + QJ] = pf(v0.y - v1.w, v2.y - v3.w);
+                im[jj + QJ] = pf(v0.w + v1.y, v2.w + v3.y);
+            }
+#pragma unroll
+            for (int jj = HJ; jj < HJ + QJ; ++jj) {
+                // kk = lane + R2 jj in [N/2, N/2 + Q): X[kk] = conj X[N - kk], N - kk - Q < Q
+                const bool ny = (jj == HJ) && lane == 0;
+                const int e = ny ? 0 : N - lane - R2 * jj - Q;
+                const float4 v0 = row0[e], v1 = row0[P + e], v2 = row0[2 * P + e], v3 = row0[3 * P + e];
+                // kk: high half of entry e, conjugated; the Nyquist bin is the DC entry's z
+                const float r0 = ny ? v0.z : v0.y, r1 = ny ? v1.z : v1.y, r2 = ny ? v2.z : v2.y, r3 = ny ? v3.z : v3.y;
+                const float n0 = ny ? 0.f : -v0.w, n1 = ny ? 0.f : -v1.w, n2 = ny ? 0.f : -v2.w, n3 = ny ? 0.f : -v3.w;
+                re[jj] = pf(r0 - n1, r2 - n3);
+                im[jj] = pf(n0 + r1, n2 + r3);
+                // kk + Q: low half of entry e, conjugated (Nyquist lane: X[Q] = high half of entry 0)
+                const float s0 = ny ? v0.y : v0.x, s1 = ny ? v1.y : v1.x, s2 = ny ? v2.y : v2.x, s3 = ny ? v3.y : v3.x;
+                const float m0 = ny ? -v0.w : -v0.z, m1 = ny ? -v1.w : -v1.z, m2 = ny ? -v2.w : -v2.z, m3 = ny ? -v3.w : -v3.z;
+                re[jj + QJ] = pf(s0 - m1, s2 - m3);
+                im[jj + QJ] = pf(m0 + s1, m2 + s3);
+            }
+        }
+        __syncwarp();   // every read of the team's rows is done before the exchange reuses them
+        float4* xb = S + frow(4 * (act ? q : 0), P);
+        team_fft2<R1, R2, +1>(re, im, lane, act, xb, TW, SyncWarp());
+        if (act && lane < R1) {
+            float* o0 = ob + (size_t)(4 * q) * NN;
+#pragma unroll
+            for (int k = 0; k < R2; ++k) {
+                const int x = lane + R1 * k;
+                st_out(o0 + x, re[k].x, po);
+                st_out(o0 + NN + x, im[k].x, po);
+                st_out(o0 + 2 * NN + x, re[k].y, po);
+                st_out(o0 + 3 * NN + x, im[k].y, po);
+            }
+        }
+    }
+}
+
+template <int N, int M> constexpr size_t fast_xt_smem() { return (size_t)(fslab4<N, M>() + N) * sizeof(float4); }
+template <int N> constexpr size_t fast_lines_smem() { return (size_t)(fast_lines<N>() * fast_xs<N>() + N) * sizeof(float4); }
+
+}  // namespace se2

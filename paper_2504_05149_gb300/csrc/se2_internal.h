@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "se2_kernels.cuh"
+#include "se2_fast.cuh"
 
 namespace se2 {
 
@@ -51,6 +51,18 @@ bool get_kernels(int N, int M, KTable<T>* kt) {
         default: return false;
     }
 }
+
+// FP32 paired-FFT convolution kernels (se2_fast.cu), N in {32, 64, 128, 256},
+// M in {8, ..., 128}.
+struct FastTable {
+    using FK = void (*)(FArgs);
+    FK fwd = nullptr, lines = nullptr, inv = nullptr;
+    size_t smem_xt = 0, smem_y = 0;
+    int lines_per_block = 0;
+};
+template <int N>
+bool get_fast_n(int M, FastTable* t);
+bool get_fast(int N, int M, FastTable* t);   // se2_capi.cu
 
 // Tensor-core angular DFT (se2_tc.cu).
 struct TcArgs;

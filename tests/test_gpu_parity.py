@@ -211,6 +211,17 @@ def test_ragged_chunks_and_forced_split_path(se2):
     _sub({"SE2_MAX_CHUNK": "2", "SE2_FORCE_SPLIT": "1"}, _RAGGED)
 
 
+def test_paired_and_generic_fp32_kernels_agree(se2):
+    """The FP32 paired-FFT kernels (default where they exist) and the generic
+    kernels (SE2_FAST=0) both give the oracle's result at 256^2 x 64, and at
+    128^2 x 128 through ragged scratch chunks."""
+    code = _RAGGED.replace("N, M, B = 64, 16, 5", "N, M, B = 256, 64, 3")
+    _sub({"SE2_FAST": "0"}, code)
+    _sub({}, code)
+    code = _RAGGED.replace("N, M, B = 64, 16, 5", "N, M, B = 128, 128, 3")
+    _sub({"SE2_MAX_CHUNK": "2"}, code)
+
+
 def test_invalid_arguments_on_gpu_plan(se2):
     plan = se2.Plan(32, 16, batch=2)
     f = torch.zeros((3, 16, 32, 32), device="cuda")
