@@ -108,8 +108,10 @@ __device__ __forceinline__ int xslot(int k1, int t) { return k1 * R2 + (t ^ (k1 
 // Paired team FFT of length L = R1 * R2 (two lines, one per register half).
 //  in : lane t < R2 holds x[t + R2 j], j < R1
 //  out: lane s < R1 holds X[s + R1 k], k < R2
-// xb: the team's R1 * R2 float4 exchange slots; tw4: forward length-L
-// twiddles as (wr, wr, wi, wi).  Lanes with act = false only synchronise.
+// xb: the team's R1 * R2 float4 exchange slots; tw4: this factorisation's
+// step-A twiddles, tw4[k1 * R2 + t] = e^{-2 pi i t k1 / L} as (wr, wr, wi, wi)
+// (consecutive lanes read consecutive entries).  Lanes with act = false only
+// synchronise.
 template <int R1, int R2, int DIR, typename Sync>
 __device__ __forceinline__ void team_fft2(float2* re, float2* im, int lane, bool act, float4* xb,
                                           const float4* tw4, Sync sync) {
@@ -120,7 +122,7 @@ __device__ __forceinline__ void team_fft2(float2* re, float2* im, int lane, bool
             fft2_reg<R1, DIR>(re, im);
 #pragma unroll
             for (int k1 = 1; k1 < R1; ++k1) {
-                const float4 w = tw4[lane * k1];
+                const float4 w = tw4[k1 * R2 + lane];
                 ptw<DIR>(re[k1], im[k1], pf(w.x, w.y), pf(w.z, w.w));
             }
             if (act) {
@@ -212,11 +214,18 @@ struct FArgs {
     double inv_L;
 };
 
-__device__ __forceinline__ void fill_tw4(float4* tw, const float2* src, int L) {
-    for (int n = threadIdx.x; n < L; n += blockDim.x) {
-        const float2 w = src[n];
+// Step-A twiddle table of the team FFT of length L = R1 * R2 (layout of
+// team_fft2) from the forward table src of length L.
+template <int R1, int R2>
+__device__ __forceinline__ void fill_tw4(float4* tw, const float2* src) {
+    for (int n = threadIdx.x; n < R1 * R2; n += blockDim.x) {
+        const int k1 = n / R2, t = n - k1 * R2;
+        const float2 w = src[k1 * t];
         tw[n] = make_float4(w.x, w.x, w.y, w.y);
     }
+}
+__device__ __forceinline__ void copy_tw(float2* dst, const float2* src, int L) {
+    for (int n = threadIdx.x; n < L; n += blockDim.x) dst[n] = src[n];
 }
 
 // This lane's step-A twiddles of the length-M angular team FFT, broadcast.
@@ -250,9 +259,8 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
     extern __shared__ float4 fsm[];
     float4* S = fsm;
     float4* TW = fsm + fslab4<N, M>();
+    float2* TWM = reinterpret_cast<float2*>(TW + N);
     const int tid = threadIdx.x, j = blockIdx.x, b = blockIdx.y;
-    fill_tw4(TW, a.twN, N);
-    __syncthreads();
     const uint64_t pin = pol_stream(), pk = pol_keep();
     const float* fb = a.f + (size_t)b * NN * M + (size_t)j * N;
     const int team = tid / TS, lane = tid % TS;
@@ -270,6 +278,11 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
                 re[jj] = pf(ld_in(r0 + x, pin), ld_in(r0 + 2 * NN + x, pin));
                 im[jj] = pf(ld_in(r0 + NN + x, pin), ld_in(r0 + 3 * NN + x, pin));
             }
+        }
+        if (q0 == 0) {   // the table fills overlap the first loads
+            fill_tw4<R1, R2>(TW, a.twN);
+            copy_tw(TWM, a.twM, M);
+            __syncthreads();
         }
         float4* xb = S + frow(4 * (act ? q : 0), P);
         team_fft2<R1, R2, -1>(re, im, lane, act, xb, TW, SyncWarp());
@@ -322,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
         constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
         const int tm = tid / TSM, lm = tid % TSM;
         float2 wr[Fac<M>::R1], wi[Fac<M>::R1];
-        angular_twiddles<M>(a.twM, lm, wr, wi);
+        angular_twiddles<M>(TWM, lm, wr, wi);
         for (int c0 = 0; c0 < Q; c0 += TEAMSM) {
             const int u = c0 + tm;
             const bool act = u < Q;
@@ -360,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
 // along y, multiply by W^k C_1 ... C_k exp(sum ls) / |L| (and the 1/2 of the
 // split), inverse FFT along y, in place.
 // ---------------------------------------------------------------------------
-template <int N> __host__ __device__ constexpr int fast_xs() { return N + 2; }   // = 2 (mod 8) float4
+template <int N> __host__ __device__ constexpr int fast_xs() { return N + 1; }   // = 1 (mod 8) float4
 template <int N> __host__ __device__ constexpr int fast_lines() { return kThreads / team_size<N>(); }
 
 template <int N, int M>
@@ -371,17 +384,10 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     static_assert(R1 % 2 == 0, "ky parity is the lane parity");
     extern __shared__ float4 fsm[];
     float4* XB = fsm;
-    float4* TW = fsm + LINES * XS;
+    float4* TWF = fsm + LINES * XS;     // forward (R1 x R2) and inverse (R2 x R1) tables
+    float4* TWI = TWF + N;
     __shared__ double sh_scale;
     const int tid = threadIdx.x, b = blockIdx.y;
-    fill_tw4(TW, a.twN, N);
-    if (tid == 0) {
-        double lsum = 0;
-        for (int i = 0; i < a.k; ++i)
-            if (a.ls[i] != nullptr) lsum += a.ls[i][b * a.ls_pstride];
-        sh_scale = 0.5 * a.inv_L * exp(lsum);
-    }
-    __syncthreads();
     const int c = tid % LINES, t = tid / LINES;
     const int pl = blockIdx.x * LINES + c;
     const bool act = pl < M * P1;
@@ -400,7 +406,17 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
             im[jj] = pf(v.z, v.w);
         }
     }
-    team_fft2<R1, R2, -1>(re, im, t, act, xb, TW, SyncBlock());
+    // table fills and the scale overlap the loads
+    fill_tw4<R1, R2>(TWF, a.twN);
+    fill_tw4<R2, R1>(TWI, a.twN);
+    if (tid == 0) {
+        double lsum = 0;
+        for (int i = 0; i < a.k; ++i)
+            if (a.ls[i] != nullptr) lsum += a.ls[i][b * a.ls_pstride];
+        sh_scale = 0.5 * a.inv_L * exp(lsum);
+    }
+    __syncthreads();
+    team_fft2<R1, R2, -1>(re, im, t, act, xb, TWF, SyncBlock());
     // lane s < R1 holds ky = s + R1 k, k < R2
     if (act && t < R1) {
         const bool hasb = u < Q;
@@ -430,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
             im[k] = pmul(im[k], s2);
         }
     }
-    team_fft2<R2, R1, +1>(re, im, t, act, xb, TW, SyncBlock());
+    team_fft2<R2, R1, +1>(re, im, t, act, xb, TWI, SyncBlock());
     if (act && t < R2) {
 #pragma unroll
         for (int k = 0; k < R1; ++k)
@@ -454,26 +470,34 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
     extern __shared__ float4 fsm[];
     float4* S = fsm;
     float4* TW = fsm + fslab4<N, M>();
+    float2* TWM = reinterpret_cast<float2*>(TW + N);
     const int tid = threadIdx.x, j = blockIdx.x, b = blockIdx.y;
     const uint64_t pk = pol_keep(), po = pol_stream();
-    fill_tw4(TW, a.twN, N);
     {
+        // batches of at most ~20 loads in flight per thread (registers)
+        constexpr int CH = LOADS <= 20 ? LOADS : (LOADS + 1) / 2;
         const float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * a.tp4;
-        float4 v[LOADS];
+        for (int i0 = 0; i0 < LOADS; i0 += CH) {
+            float4 v[CH];
 #pragma unroll
-        for (int i = 0; i < LOADS; ++i) {
-            const int e = tid + kThreads * i;
-            if (e < M * P) {
-                const int r = e / P, u = e - r * P;
-                v[i] = ld_s4(sb + (size_t)r * N * a.tp4 + u, pk);
+            for (int i = 0; i < CH; ++i) {
+                const int e = tid + kThreads * (i0 + i);
+                if (i0 + i < LOADS && e < M * P) {
+                    const int r = e / P, u = e - r * P;
+                    v[i] = ld_s4(sb + (size_t)r * N * a.tp4 + u, pk);
+                }
             }
-        }
+            if (i0 == 0) {   // the table fills overlap the loads
+                fill_tw4<R1, R2>(TW, a.twN);
+                copy_tw(TWM, a.twM, M);
+            }
 #pragma unroll
-        for (int i = 0; i < LOADS; ++i) {
-            const int e = tid + kThreads * i;
-            if (e < M * P) {
-                const int r = e / P, u = e - r * P;
-                S[frow(r, P) + u] = v[i];
+            for (int i = 0; i < CH; ++i) {
+                const int e = tid + kThreads * (i0 + i);
+                if (i0 + i < LOADS && e < M * P) {
+                    const int r = e / P, u = e - r * P;
+                    S[frow(r, P) + u] = v[i];
+                }
             }
         }
     }
@@ -490,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
         constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
         const int tm = tid / TSM, lm = tid % TSM;
         float2 wr[Fac<M>::R1], wi[Fac<M>::R1];
-        angular_twiddles<M>(a.twM, lm, wr, wi);
+        angular_twiddles<M>(TWM, lm, wr, wi);
         for (int c0 = 0; c0 < Q; c0 += TEAMSM) {
             const int u = c0 + tm;
             const bool act = u < Q;
@@ -560,7 +584,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
     }
 }
 
-template <int N, int M> constexpr size_t fast_xt_smem() { return (size_t)(fslab4<N, M>() + N) * sizeof(float4); }
-template <int N> constexpr size_t fast_lines_smem() { return (size_t)(fast_lines<N>() * fast_xs<N>() + N) * sizeof(float4); }
+template <int N, int M> constexpr size_t fast_xt_smem() { return (size_t)(fslab4<N, M>() + N + M / 2) * sizeof(float4); }
+template <int N> constexpr size_t fast_lines_smem() { return (size_t)(fast_lines<N>() * fast_xs<N>() + 2 * N) * sizeof(float4); }
 
 }  // namespace se2
