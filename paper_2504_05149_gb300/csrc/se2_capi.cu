@@ -55,6 +55,9 @@ struct DeviceGuard {
 
 void se2::set_last_error(const char* msg) { g_err = msg; }
 
+constexpr int kMaxPipe = 4;
+constexpr int kPipeDepth = 2, kPipeGroup = 2;   // default pipelining of the FP32 fast path
+
 struct se2_plan_s {
     int N = 0, M = 0, batch = 0, dev = 0;
     se2_precision prec = SE2_F32;
@@ -88,6 +91,12 @@ struct se2_plan_s {
     // FP32 paired-FFT kernels for the convolution and chain (null: generic ones)
     bool fast = false;
     FastTable ft;
+    // pipelined fast path: problem groups of pipe_group on pipe_depth streams
+    // (the caller's and pipe_depth - 1 of the plan's), each group with its own
+    // scratch slots, so that kernels of different groups overlap
+    int pipe_depth = 1, pipe_group = 0;
+    cudaStream_t aux[kMaxPipe] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxPipe] = {};
 };
 
 bool se2::get_fast(int N, int M, FastTable* t) {
@@ -203,6 +212,14 @@ se2_status plan_init(se2_plan_s* p) {
 }
 
 void plan_free(se2_plan_s* p) {
+    for (int d = 0; d < kMaxPipe; ++d) {
+        if (p->aux[d]) cudaStreamDestroy(p->aux[d]);
+        if (p->ev_join[d]) cudaEventDestroy(p->ev_join[d]);
+        p->aux[d] = nullptr;
+        p->ev_join[d] = nullptr;
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    p->ev_fork = nullptr;
     if (p->ctr) cudaFree(p->ctr);
     if (p->err) cudaFree(p->err);
     if (p->tab) cudaFree(p->tab);
@@ -385,6 +402,10 @@ se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* c
 }
 
 // Convolution / chain on the FP32 paired-FFT kernels (paired scratch layout).
+// With pipe_depth > 1 the batch goes in groups of pipe_group problems,
+// round-robin over pipe_depth streams forked from (and joined back into) st,
+// each stream with its own scratch slots; a group's three kernels stay in
+// order on its stream while groups on other streams overlap them.
 se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* const* coeffs,
                           const double* const* log_scales, int k, float* out, cudaStream_t st) {
     const FastTable& ft = p->ft;
@@ -393,30 +414,48 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
     const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
     const long long pairs = (long long)p->M * (p->N / 4 + 1);
     const unsigned yb = (unsigned)((pairs + ft.lines_per_block - 1) / ft.lines_per_block);
-    for (int c0 = 0; c0 < B; c0 += p->chunk) {
-        const int nb = (B - c0 < p->chunk) ? (B - c0) : p->chunk;
+    const bool pipe = p->pipe_depth > 1 && B > p->pipe_group;
+    const int group = pipe ? p->pipe_group : p->chunk;
+    const int depth = pipe ? p->pipe_depth : 1;
+    cudaError_t e = cudaSuccess;
+    if (pipe) {
+        e = cudaEventRecord(p->ev_fork, st);
+        for (int d = 1; d < depth && e == cudaSuccess; ++d) e = cudaStreamWaitEvent(p->aux[d], p->ev_fork, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+    }
+    int i = 0;
+    for (int c0 = 0; c0 < B; c0 += group, ++i) {
+        const int nb = (B - c0 < group) ? (B - c0) : group;
+        const int d = i % depth;
+        cudaStream_t s = d == 0 ? st : p->aux[d];
         FArgs a{};
         a.f = f + c0 * g;
         a.out = out + c0 * g;
-        a.s = (float4*)p->scratch;
+        a.s = (float4*)p->scratch + (size_t)d * group * (p->s_pstride / 2);
         a.s_pstride = (long long)(p->s_pstride / 2);
-        a.tp4 = p->tp / 2;
         a.twN = (const float2*)p->twN;
         a.twM = (const float2*)p->twM;
         a.k = k;
         a.c_pstride = cps;
         a.ls_pstride = lps;
         a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
-        for (int i = 0; i < k; ++i) {
-            a.C[i] = (const float2*)coeffs[i] + c0 * cps;
-            a.ls[i] = (log_scales && log_scales[i]) ? log_scales[i] + c0 * lps : nullptr;
+        for (int q = 0; q < k; ++q) {
+            a.C[q] = (const float2*)coeffs[q] + c0 * cps;
+            a.ls[q] = (log_scales && log_scales[q]) ? log_scales[q] + c0 * lps : nullptr;
         }
-        ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
-        ft.lines<<<dim3(yb, nb), kThreads, ft.smem_y, st>>>(a);
-        ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+        ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);
+        ft.lines<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);
+        ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (pipe) {
+        for (int d = 1; d < depth && e == cudaSuccess; ++d) {
+            e = cudaEventRecord(p->ev_join[d], p->aux[d]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_join[d], 0);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "stream join");
+    }
     return SE2_OK;
 }
 
@@ -592,6 +631,26 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     p->nslots = chunk < 2 ? 2 : (int)chunk;
     e = cudaMalloc(&p->scratch, per * p->nslots);
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "scratch (%zu bytes): %s", per * p->nslots, cudaGetErrorString(e)); }
+    if (p->fast) {
+        // pipelined groups (SE2_PIPE_DEPTH / SE2_PIPE_GROUP in the environment
+        // override the defaults); depth * group scratch slots must exist
+        int depth = kPipeDepth, group = kPipeGroup;
+        if (const char* v = getenv("SE2_PIPE_DEPTH")) depth = (int)strtol(v, nullptr, 10);
+        if (const char* v = getenv("SE2_PIPE_GROUP")) group = (int)strtol(v, nullptr, 10);
+        if (depth > kMaxPipe) depth = kMaxPipe;
+        if (group < 1) group = 1;
+        while (depth > 1 && depth * group > p->nslots) --depth;
+        if (depth > 1) {
+            e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+            for (int d = 1; d < depth && e == cudaSuccess; ++d) {
+                e = cudaStreamCreateWithFlags(&p->aux[d], cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[d], cudaEventDisableTiming);
+            }
+            if (e != cudaSuccess) { plan_free(p); delete p; return cuda_fail(e, "pipeline streams"); }
+            p->pipe_depth = depth;
+            p->pipe_group = group;
+        }
+    }
     e = cudaMalloc((void**)&p->tab, sizeof(double) * 2 * ((size_t)N + M));
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "tables: %s", cudaGetErrorString(e)); }
     e = cudaMalloc((void**)&p->abs_sum, sizeof(double) * chunk);

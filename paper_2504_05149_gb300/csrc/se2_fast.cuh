@@ -14,10 +14,15 @@
 // this scratch are twice the true ones (the factor 1/2 of the real-FFT split
 // is folded into the product's scale).
 //
-// Shared-memory slab (units A and C): M rows of pitch P = Q + 1 entries, row r
-// at r * P + (r >> 3); with P = 1 (mod 8) the strided row accesses of the
+// Shared-memory slab (units A and C): M rows of odd pitch P >= Q + 1 entries,
+// row r at r * P + (r >> 3); with P odd the strided row accesses of the
 // angular teams fall in distinct 16-byte bank groups.  The x FFTs exchange
-// through their own four slab rows (no separate buffer).
+// through their own four slab rows (no separate buffer), so 4 P also covers a
+// padded exchange of R1 (R2 + 1) entries.
+//
+// Global accesses use the cache-hint intrinsics (scratch: .cg, through L2
+// only; inputs, coefficients and outputs: .cs, streamed) so that the compiler
+// folds address offsets and forms 128-bit register quads itself.
 #pragma once
 #include "se2_kernels.cuh"
 
@@ -100,10 +105,13 @@ __device__ __forceinline__ void ptw(float2& re, float2& im, float2 wr, float2 wi
     }
 }
 
-// Exchange slot of step-A output k1 of lane t: row k1 of R2 slots, XOR
-// swizzled so that both the row writes and the column reads are conflict-free.
+// Exchange slot of step-A output k1 of lane t: rows of R2 + 1 slots, so that
+// both the row writes and the column reads of 8 lanes (one 128-bit access
+// phase) hit distinct bank groups, with compile-time offsets from a per-lane
+// base.
 template <int R1, int R2>
-__device__ __forceinline__ int xslot(int k1, int t) { return k1 * R2 + (t ^ (k1 & (R2 - 1))); }
+__device__ __forceinline__ constexpr int xslot(int k1, int t) { return k1 * (R2 + 1) + t; }
+template <int R1, int R2> __host__ __device__ constexpr int xslots() { return R1 * (R2 + 1); }
 
 // Paired team FFT of length L = R1 * R2 (two lines, one per register half).
 //  in : lane t < R2 holds x[t + R2 j], j < R1
@@ -147,8 +155,22 @@ __device__ __forceinline__ void team_fft2(float2* re, float2* im, int lane, bool
     }
 }
 
-__device__ __forceinline__ constexpr int frow(int r, int P) { return r * P + (r >> 3); }
-template <int N, int M> __host__ __device__ constexpr int fslab4() { return M * (N / 4 + 1) + (M >> 3) + 1; }
+__host__ __device__ __forceinline__ constexpr int frow(int r, int P) { return r * P + (r >> 3); }
+// Slab pitch: odd, >= N/4 + 1, and four rows hold the padded x exchange and
+// the N + 1 linear slots of the real-FFT split.
+template <int N> __host__ __device__ constexpr int fpitch() {
+    constexpr int x = xslots<Fac<N>::R1, Fac<N>::R2>() > N + 1 ? xslots<Fac<N>::R1, Fac<N>::R2>() : N + 1;
+    constexpr int p = (x + 3) / 4 > N / 4 + 1 ? (x + 3) / 4 : N / 4 + 1;
+    return p | 1;
+}
+template <int N, int M> __host__ __device__ constexpr int fslab4() { return M * fpitch<N>() + (M >> 3) + 1; }
+// Scratch row pitch (float4) of the paired layout: the plan's pitch of
+// round_up(N/2 + 1, 16) complex elements.
+template <int N> __host__ __device__ constexpr int ftp4() { return ((N / 2 + 1 + 15) / 16 * 16) / 2; }
+// Lane part of frow(lane + R j) for lane < R, R a power of two: the row
+// shift (lane + R j) >> 3 equals (lane >> 3) + ((R j) >> 3), so frow(lane + R j)
+// = frow_lane(lane) + frow(R j) with the second term a compile-time constant.
+__device__ __forceinline__ int frow_lane(int lane, int P) { return lane * P + (lane >> 3); }
 
 // Paired in-place FFT of slab column pair u (rows r at frow(r, P) + u) by a
 // team of team_size<L>() lanes; (wr, wi): this lane's step-A twiddles
@@ -167,10 +189,15 @@ __device__ __forceinline__ void column_fft2(float4* S, int u, int lane, bool act
             for (int r = 0; r < L; ++r) S[frow(r, P) + u] = make_float4(re[r].x, re[r].y, im[r].x, im[r].y);
         }
     } else {
+        // rows lane + R2 j, k1 + R1 lane and lane + R1 t: (a + b) >> 3 splits
+        // into a >> 3 plus b >> 3 because R1, R2 are powers of two and lane < R
+        float4* Su = S + u;
+        float4* SA = Su + frow_lane(lane, P);                              // rows lane + R * j
+        float4* SS = Su + lane * (R1 * P) + ((R1 * lane) >> 3);            // rows k1 + R1 lane
         if (act && lane < R2) {
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
-                const float4 v = S[frow(lane + R2 * j, P) + u];
+                const float4 v = SA[R2 * j * P + ((R2 * j) >> 3)];
                 re[j] = pf(v.x, v.y);
                 im[j] = pf(v.z, v.w);
             }
@@ -182,19 +209,19 @@ __device__ __forceinline__ void column_fft2(float4* S, int u, int lane, bool act
         if (act && lane < R2) {
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1)
-                S[frow(k1 + R1 * lane, P) + u] = make_float4(re[k1].x, re[k1].y, im[k1].x, im[k1].y);
+                SS[k1 * P + (k1 >> 3)] = make_float4(re[k1].x, re[k1].y, im[k1].x, im[k1].y);
         }
         sync();
         if (act && lane < R1) {
 #pragma unroll
             for (int t = 0; t < R2; ++t) {
-                const float4 v = S[frow(lane + R1 * t, P) + u];
+                const float4 v = SA[R1 * t * P + ((R1 * t) >> 3)];
                 re[t] = pf(v.x, v.y);
                 im[t] = pf(v.z, v.w);
             }
             fft2_reg<R2, DIR>(re, im);
 #pragma unroll
-            for (int k = 0; k < R2; ++k) S[frow(lane + R1 * k, P) + u] = make_float4(re[k].x, re[k].y, im[k].x, im[k].y);
+            for (int k = 0; k < R2; ++k) SA[R1 * k * P + ((R1 * k) >> 3)] = make_float4(re[k].x, re[k].y, im[k].x, im[k].y);
         }
     }
 }
@@ -203,8 +230,7 @@ struct FArgs {
     const float* f;
     float* out;
     float4* s;                   // paired scratch of the first problem of the launch
-    long long s_pstride;         // float4 entries per problem
-    int tp4;                     // scratch row pitch (float4)
+    long long s_pstride;         // float4 entries per problem (rows of ftp4<N>() entries)
     const float2* twN;           // forward twiddles of length N and M
     const float2* twM;
     int k;                       // kernels in the chain
@@ -249,7 +275,7 @@ __device__ __forceinline__ void angular_twiddles(const float2* twM, int lm, floa
 // ---------------------------------------------------------------------------
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
-    constexpr int Q = N / 4, P = Q + 1;
+    constexpr int Q = N / 4, P = fpitch<N>(), TP4 = ftp4<N>();
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
     constexpr int TEAMS = kThreads / TS, JOBS = M / 4;
     constexpr int QK = Q / R1;            // register distance between x bins u and u + Q
@@ -261,7 +287,6 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
     float4* TW = fsm + fslab4<N, M>();
     float2* TWM = reinterpret_cast<float2*>(TW + N);
     const int tid = threadIdx.x, j = blockIdx.x, b = blockIdx.y;
-    const uint64_t pin = pol_stream(), pk = pol_keep();
     const float* fb = a.f + (size_t)b * NN * M + (size_t)j * N;
     const int team = tid / TS, lane = tid % TS;
     for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
@@ -275,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
 #pragma unroll
             for (int jj = 0; jj < R1; ++jj) {
                 const int x = lane + R2 * jj;
-                re[jj] = pf(ld_in(r0 + x, pin), ld_in(r0 + 2 * NN + x, pin));
-                im[jj] = pf(ld_in(r0 + NN + x, pin), ld_in(r0 + 3 * NN + x, pin));
+                re[jj] = pf(__ldcs(r0 + x), __ldcs(r0 + 2 * NN + x));
+                im[jj] = pf(__ldcs(r0 + NN + x), __ldcs(r0 + 3 * NN + x));
             }
         }
         if (q0 == 0) {   // the table fills overlap the first loads
@@ -290,15 +315,15 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
         if (act && lane < R1) {
 #pragma unroll
             for (int k = 0; k < R2; ++k) xb[lane + R1 * k] = make_float4(re[k].x, re[k].y, im[k].x, im[k].y);
+            if (lane == 0) xb[N] = make_float4(re[0].x, re[0].y, im[0].x, im[0].y);   // Z[N] = Z[0]
         }
         __syncwarp();
         float4 zm[HK + 1];
         if (act && lane < R1) {
+            const float4* zb = xb + (N - lane);
 #pragma unroll
-            for (int k = 0; k <= HK; ++k) {
-                const int kk = lane + R1 * k;
-                zm[k] = kk <= N / 2 ? xb[(N - kk) & (N - 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            for (int k = 0; k < HK; ++k) zm[k] = zb[-R1 * k];
+            zm[HK] = lane == 0 ? xb[N / 2] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncwarp();   // every read of Z is done before the rows take the spectra
         if (act && lane < R1) {
@@ -360,10 +385,11 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
     }
     __syncthreads();
     {
-        float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * a.tp4;
-        for (int e = tid; e < M * P; e += kThreads) {
-            const int r = e / P, u = e - r * P;
-            st_s4(sb + (size_t)r * N * a.tp4 + u, S[frow(r, P) + u], pk);
+        constexpr int E = Q + 1;
+        float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * TP4;
+        for (int e = tid; e < M * E; e += kThreads) {
+            const int r = e / E, u = e - r * E;
+            __stcg(sb + (size_t)r * N * TP4 + u, S[frow(r, P) + u]);
         }
     }
 }
@@ -373,12 +399,18 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
 // along y, multiply by W^k C_1 ... C_k exp(sum ls) / |L| (and the 1/2 of the
 // split), inverse FFT along y, in place.
 // ---------------------------------------------------------------------------
-template <int N> __host__ __device__ constexpr int fast_xs() { return N + 1; }   // = 1 (mod 8) float4
+// Exchange entries per line pair of the y pass: both factorisations' padded
+// slots, rounded to 1 (mod 8) so that 8 consecutive line pairs start in
+// distinct bank groups.
+template <int N> __host__ __device__ constexpr int fast_xs() {
+    constexpr int a = xslots<Fac<N>::R1, Fac<N>::R2>(), b = xslots<Fac<N>::R2, Fac<N>::R1>();
+    return ((a > b ? a : b) + 7) / 8 * 8 + 1;
+}
 template <int N> __host__ __device__ constexpr int fast_lines() { return kThreads / team_size<N>(); }
 
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
-    constexpr int Q = N / 4, P1 = Q + 1, CP = N / 2 + 1;
+    constexpr int Q = N / 4, P1 = Q + 1, CP = N / 2 + 1, TP4 = ftp4<N>();
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, RM = reg_count<N>();
     constexpr int LINES = fast_lines<N>(), XS = fast_xs<N>();
     static_assert(R1 % 2 == 0, "ky parity is the lane parity");
@@ -392,16 +424,15 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     const int pl = blockIdx.x * LINES + c;
     const bool act = pl < M * P1;
     const int o = act ? pl / P1 : 0, u = act ? pl - (pl / P1) * P1 : 0;
-    float4* base = a.s + (size_t)b * a.s_pstride + (size_t)o * N * a.tp4 + u;
+    float4* base = a.s + (size_t)b * a.s_pstride + (size_t)o * N * TP4 + u + (size_t)t * TP4;
     float4* xb = XB + c * XS;
-    const uint64_t pk = pol_keep(), pin = pol_stream();
     float2 re[RM], im[RM];
 #pragma unroll
     for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
     if (act && t < R2) {
 #pragma unroll
         for (int jj = 0; jj < R1; ++jj) {
-            const float4 v = ld_s4(base + (size_t)(t + R2 * jj) * a.tp4, pk);
+            const float4 v = __ldcg(base + (size_t)(R2 * jj) * TP4);
             re[jj] = pf(v.x, v.y);
             im[jj] = pf(v.z, v.w);
         }
@@ -429,8 +460,8 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
             float2 ca[R2], cq[R2];
 #pragma unroll
             for (int k = 0; k < R2; ++k) {
-                ca[k] = ld_in(cb + (size_t)(R1 * k) * CP, pin);
-                cq[k] = hasb ? ld_in(cb + (size_t)(R1 * k) * CP + Q, pin) : pf(0.f, 0.f);
+                ca[k] = __ldcs(cb + (size_t)(R1 * k) * CP);
+                cq[k] = hasb ? __ldcs(cb + (size_t)(R1 * k) * CP + Q) : pf(0.f, 0.f);
             }
 #pragma unroll
             for (int k = 0; k < R2; ++k) {
@@ -450,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     if (act && t < R2) {
 #pragma unroll
         for (int k = 0; k < R1; ++k)
-            st_s4(base + (size_t)(t + R2 * k) * a.tp4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y), pk);
+            __stcg(base + (size_t)(R2 * k) * TP4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y));
     }
 }
 
@@ -461,30 +492,29 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
 // ---------------------------------------------------------------------------
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
-    constexpr int Q = N / 4, P = Q + 1;
+    constexpr int Q = N / 4, P = fpitch<N>(), TP4 = ftp4<N>(), E = Q + 1;
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
     constexpr int TEAMS = kThreads / TS, JOBS = M / 4;
     constexpr int QJ = Q / R2, HJ = N / (2 * R2);
     constexpr size_t NN = (size_t)N * N;
-    constexpr int LOADS = (M * P + kThreads - 1) / kThreads;
+    constexpr int LOADS = (M * E + kThreads - 1) / kThreads;
     extern __shared__ float4 fsm[];
     float4* S = fsm;
     float4* TW = fsm + fslab4<N, M>();
     float2* TWM = reinterpret_cast<float2*>(TW + N);
     const int tid = threadIdx.x, j = blockIdx.x, b = blockIdx.y;
-    const uint64_t pk = pol_keep(), po = pol_stream();
     {
         // batches of at most ~20 loads in flight per thread (registers)
         constexpr int CH = LOADS <= 20 ? LOADS : (LOADS + 1) / 2;
-        const float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * a.tp4;
+        const float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * TP4;
         for (int i0 = 0; i0 < LOADS; i0 += CH) {
             float4 v[CH];
 #pragma unroll
             for (int i = 0; i < CH; ++i) {
                 const int e = tid + kThreads * (i0 + i);
-                if (i0 + i < LOADS && e < M * P) {
-                    const int r = e / P, u = e - r * P;
-                    v[i] = ld_s4(sb + (size_t)r * N * a.tp4 + u, pk);
+                if (i0 + i < LOADS && e < M * E) {
+                    const int r = e / E, u = e - r * E;
+                    v[i] = __ldcg(sb + (size_t)r * N * TP4 + u);
                 }
             }
             if (i0 == 0) {   // the table fills overlap the loads
@@ -494,8 +524,8 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
 #pragma unroll
             for (int i = 0; i < CH; ++i) {
                 const int e = tid + kThreads * (i0 + i);
-                if (i0 + i < LOADS && e < M * P) {
-                    const int r = e / P, u = e - r * P;
+                if (i0 + i < LOADS && e < M * E) {
+                    const int r = e / E, u = e - r * E;
                     S[frow(r, P) + u] = v[i];
                 }
             }
@@ -575,10 +605,10 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
 #pragma unroll
             for (int k = 0; k < R2; ++k) {
                 const int x = lane + R1 * k;
-                st_out(o0 + x, re[k].x, po);
-                st_out(o0 + NN + x, im[k].x, po);
-                st_out(o0 + 2 * NN + x, re[k].y, po);
-                st_out(o0 + 3 * NN + x, im[k].y, po);
+                __stcs(o0 + x, re[k].x);
+                __stcs(o0 + NN + x, im[k].x);
+                __stcs(o0 + 2 * NN + x, re[k].y);
+                __stcs(o0 + 3 * NN + x, im[k].y);
             }
         }
     }

@@ -222,6 +222,44 @@ def test_paired_and_generic_fp32_kernels_agree(se2):
     _sub({"SE2_MAX_CHUNK": "2"}, code)
 
 
+def test_pipelined_groups_on_several_streams(se2):
+    """FP32 fast path with the batch in groups on 3 streams (ragged last
+    group), and the same call captured in a CUDA graph and replayed."""
+    code = _RAGGED.replace("N, M, B = 64, 16, 5", "N, M, B = 64, 16, 7")
+    _sub({"SE2_PIPE_DEPTH": "3", "SE2_PIPE_GROUP": "2"}, code)
+    graph = r"""
+import numpy as np, torch, sys
+sys.path.insert(0, '.')
+import paper_2504_05149_gb300 as se2
+from oracle import se2_oracle as O
+N, M, B = 32, 8, 6
+rng = np.random.default_rng(5)
+F = rng.standard_normal((B, M, N, N)).astype(np.float32)
+P = rng.random((B, M, N, N)).astype(np.float32)
+plan = se2.Plan(N, M, batch=B)
+C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
+f = torch.from_numpy(F).cuda()
+out = torch.empty_like(f)
+s = torch.cuda.Stream()
+s.wait_stream(torch.cuda.current_stream())
+with torch.cuda.stream(s):
+    se2.convolve(plan, f, C, out=out)
+torch.cuda.current_stream().wait_stream(s)
+g = torch.cuda.CUDAGraph()
+with torch.cuda.graph(g):
+    se2.convolve(plan, f, C, out=out)
+out.zero_()
+g.replay()
+torch.cuda.synchronize()
+got = out.double().cpu().numpy()
+err = max(np.abs(got[b] - O.convolve(F[b].astype(float), P[b].astype(float))).max()
+          / np.abs(O.convolve(F[b].astype(float), P[b].astype(float))).max() for b in range(B))
+assert err < 1e-5, err
+print("ok", err)
+"""
+    _sub({"SE2_PIPE_DEPTH": "2", "SE2_PIPE_GROUP": "2"}, graph)
+
+
 def test_invalid_arguments_on_gpu_plan(se2):
     plan = se2.Plan(32, 16, batch=2)
     f = torch.zeros((3, 16, 32, 32), device="cuda")
