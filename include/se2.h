@@ -212,6 +212,30 @@ se2_status se2_debug_wait_timeout(se2_plan_t plan, const void* f, const void* co
                                   void* stream);
 
 /*
+ * se2_convolve_host -- se2_convolve with f and out in HOST memory.  The batch
+ * goes through device staging buffers owned by the plan in groups of
+ * problems; the copy of one group to the device, the convolution of the
+ * previous group and the copy of the one before back to the host run on
+ * separate streams and overlap.  The paper has no counterpart: this is a
+ * deployment variant of Algorithm 3 at N = L for data that lives on the host.
+ *   f          host, [B][M][N][N] (float, or double for SE2_F64 plans);
+ *              page-locked memory (cudaHostAlloc / cudaHostRegister) lets
+ *              the copies run asynchronously, pageable memory works but the
+ *              copies then serialise with the host
+ *   coeffs     device, as in se2_convolve
+ *   log_scale  device or NULL, as in se2_convolve
+ *   out        host, [B][M][N][N], must not overlap f
+ *   stream     the call is ordered after earlier work on `stream`; on
+ *              return all of its work is enqueued and `stream` waits for it,
+ *              so synchronise `stream` before reading out
+ * The first call allocates the staging buffers (three groups of f and out)
+ * and two copy streams; later calls reuse them.  Not for stream capture.
+ * Errors: as se2_convolve.
+ */
+se2_status se2_convolve_host(se2_plan_t plan, const void* f, int B, const void* coeffs, const double* log_scale,
+                             void* out, void* stream);
+
+/*
  * se2_convolve_noalloc -- the same result as se2_convolve (FP32, one kernel
  * spectrum per problem, no log scale) for callers that cannot create a plan
  * because creating one allocates device memory: for instance code running

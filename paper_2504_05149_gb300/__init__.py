@@ -56,6 +56,7 @@ def load_library(path: str = LIB_PATH):
     lib.se2_plan_workspace_bytes.restype = ctypes.c_size_t
     lib.se2_coeffs.argtypes = [vp, vp, ip, vp, vp, vp]
     lib.se2_convolve.argtypes = [vp, vp, ip, vp, vp, vp, vp]
+    lib.se2_convolve_host.argtypes = [vp, vp, ip, vp, vp, vp, vp]
     lib.se2_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp, vp]
     lib.se2_plan_status.argtypes = [vp, vp]
     lib.se2_separable_tables.argtypes = [vp, vp, vp, ip, ip, vp, vp]
@@ -65,7 +66,8 @@ def load_library(path: str = LIB_PATH):
     lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
     lib.se2_last_error.restype = ctypes.c_char_p
     lib.se2_version.restype = ctypes.c_char_p
-    for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_chain",
+    for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_host",
+                 "se2_convolve_chain",
                  "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
                  "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
@@ -166,6 +168,31 @@ def convolve(plan: Plan, f: torch.Tensor, C: torch.Tensor, log_scale: Optional[t
              out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """S_K[f, rho] on Omega_L for a batch f [B, M, N, N]."""
     return convolve_chain(plan, f, [C], None if log_scale is None else [log_scale], out)
+
+
+def convolve_host(plan: Plan, f: torch.Tensor, C: torch.Tensor, log_scale: Optional[torch.Tensor] = None,
+                  out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """se2_convolve with f and out in host memory (se2_convolve_host): copies
+    in, convolutions and copies out of problem groups overlap on the device.
+    f: contiguous CPU tensor [B, M, N, N] of the plan's real type (pin it for
+    asynchronous copies); out: same, allocated pinned if not given.  Returns
+    out after synchronising the current stream."""
+    if f.dim() != 4 or tuple(f.shape[1:]) != (plan.M, plan.N, plan.N) or f.dtype != plan.dtype \
+            or f.is_cuda or not f.is_contiguous():
+        raise ValueError(f"f: need a contiguous CPU {plan.dtype} tensor [B, {plan.M}, {plan.N}, {plan.N}]")
+    B = f.shape[0]
+    if out is None:
+        out = torch.empty(f.shape, dtype=f.dtype, pin_memory=True)
+    elif tuple(out.shape) != tuple(f.shape) or out.dtype != f.dtype or out.is_cuda or not out.is_contiguous():
+        raise ValueError("out: need a contiguous CPU tensor shaped like f")
+    C = plan._check_spec(C, "coeffs", B)
+    if log_scale is not None and (log_scale.dtype != torch.float64 or not log_scale.is_cuda
+                                  or not log_scale.is_contiguous()):
+        raise ValueError("log_scale: need a contiguous float64 CUDA tensor")
+    stream = _stream(plan.device)
+    _check(load_library().se2_convolve_host(plan.handle, _ptr(f), B, _ptr(C), _ptr(log_scale), _ptr(out), stream))
+    torch.cuda.current_stream(plan.device).synchronize()
+    return out
 
 
 def convolve_chain(plan: Plan, f: torch.Tensor, Cs: Sequence[torch.Tensor],
@@ -291,6 +318,7 @@ class SE2Conv(torch.autograd.Function):
         return gf, gp.to(ctx.params_device, ctx.params_dtype), None
 
 
-__all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_chain", "backward", "sample_radial_gaussian",
+__all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_chain", "backward",
+           "sample_radial_gaussian",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
            "SHARED_KERNEL", "PERSISTENT"]

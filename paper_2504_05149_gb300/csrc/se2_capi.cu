@@ -57,6 +57,7 @@ void se2::set_last_error(const char* msg) { g_err = msg; }
 
 constexpr int kMaxPipe = 4;
 constexpr int kPipeDepth = 2, kPipeGroup = 2;   // default pipelining of the FP32 fast path
+constexpr int kHostBufs = 3, kHostGroup = 2;    // staging of se2_convolve_host
 
 struct se2_plan_s {
     int N = 0, M = 0, batch = 0, dev = 0;
@@ -97,6 +98,12 @@ struct se2_plan_s {
     int pipe_depth = 1, pipe_group = 0;
     cudaStream_t aux[kMaxPipe] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxPipe] = {};
+    // se2_convolve_host: device staging for kHostBufs groups of host_group
+    // problems (f then out per group), copy streams and their events
+    int host_group = 0;
+    void* hstage = nullptr;
+    cudaStream_t hin = nullptr, hout = nullptr;
+    cudaEvent_t hev_start = nullptr, hev_in[kHostBufs] = {}, hev_done[kHostBufs] = {}, hev_out[kHostBufs] = {};
 };
 
 bool se2::get_fast(int N, int M, FastTable* t) {
@@ -212,6 +219,19 @@ se2_status plan_init(se2_plan_s* p) {
 }
 
 void plan_free(se2_plan_s* p) {
+    for (int k = 0; k < kHostBufs; ++k) {
+        if (p->hev_in[k]) cudaEventDestroy(p->hev_in[k]);
+        if (p->hev_done[k]) cudaEventDestroy(p->hev_done[k]);
+        if (p->hev_out[k]) cudaEventDestroy(p->hev_out[k]);
+        p->hev_in[k] = p->hev_done[k] = p->hev_out[k] = nullptr;
+    }
+    if (p->hev_start) cudaEventDestroy(p->hev_start);
+    if (p->hin) cudaStreamDestroy(p->hin);
+    if (p->hout) cudaStreamDestroy(p->hout);
+    if (p->hstage) cudaFree(p->hstage);
+    p->hev_start = nullptr;
+    p->hin = p->hout = nullptr;
+    p->hstage = nullptr;
     for (int d = 0; d < kMaxPipe; ++d) {
         if (p->aux[d]) cudaStreamDestroy(p->aux[d]);
         if (p->ev_join[d]) cudaEventDestroy(p->ev_join[d]);
@@ -712,6 +732,77 @@ se2_status se2_convolve_chain(se2_plan_t p, const void* f, int B, const void* co
     cudaStream_t s = (cudaStream_t)stream;
     return !is_f64(p) ? run_chain<float>(p, f, B, coeffs, log_scales, k, out, s)
                               : run_chain<double>(p, f, B, coeffs, log_scales, k, out, s);
+}
+
+se2_status se2_convolve_host(se2_plan_t p, const void* f, int B, const void* coeffs, const double* log_scale,
+                             void* out, void* stream) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    if (f == nullptr || out == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (B < 1 || B > p->batch) return fail(SE2_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, p->batch);
+    if (!aligned(coeffs, p->elem)) return fail(SE2_ERR_INVALID_ARG, "coeffs misaligned");
+    if (log_scale && !aligned(log_scale, 8)) return fail(SE2_ERR_INVALID_ARG, "log_scale misaligned");
+    const size_t re = p->elem / 2;
+    const size_t gbytes = (size_t)p->N * p->N * p->M * re;   // one grid
+    const uintptr_t fa = (uintptr_t)f, oa = (uintptr_t)out, len = gbytes * (size_t)B;
+    if (fa < oa + len && oa < fa + len) return fail(SE2_ERR_INVALID_ARG, "out overlaps f");
+    DeviceGuard guard(p->dev);
+    cudaError_t e = cudaSuccess;
+    if (p->hstage == nullptr) {   // first call: staging buffers, copy streams, events
+        int G = kHostGroup;   // SE2_HOST_GROUP (environment) overrides the group size
+        if (const char* v = getenv("SE2_HOST_GROUP")) G = (int)strtol(v, nullptr, 10);
+        if (G < 1) G = 1;
+        if (G > p->batch) G = p->batch;
+        e = cudaMalloc(&p->hstage, 2 * gbytes * (size_t)G * kHostBufs);
+        if (e != cudaSuccess) { p->hstage = nullptr; return fail(SE2_ERR_OOM, "host staging: %s", cudaGetErrorString(e)); }
+        p->host_group = G;
+        e = cudaStreamCreateWithFlags(&p->hin, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->hout, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_start, cudaEventDisableTiming);
+        for (int k = 0; k < kHostBufs && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&p->hev_in[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_done[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_out[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "host staging streams");
+    }
+    const int G = p->host_group;
+    const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
+    const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaEventRecord(p->hev_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hin, p->hev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hout, p->hev_start, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "host staging fork");
+    int g = 0;
+    for (int c0 = 0; c0 < B; c0 += G, ++g) {
+        const int k = g % kHostBufs, nb = (B - c0 < G) ? (B - c0) : G;
+        unsigned char* fdev = (unsigned char*)p->hstage + 2 * gbytes * (size_t)G * k;
+        unsigned char* odev = fdev + gbytes * (size_t)G;
+        const size_t bytes = gbytes * (size_t)nb, off = gbytes * (size_t)c0;
+        // in: slot k's f is free once the convolution of the group before finished
+        e = cudaStreamWaitEvent(p->hin, p->hev_done[k], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(fdev, (const unsigned char*)f + off, bytes, cudaMemcpyHostToDevice, p->hin);
+        if (e == cudaSuccess) e = cudaEventRecord(p->hev_in[k], p->hin);
+        // convolve after the copy in, and after slot k's previous out left
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->hev_in[k], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->hev_out[k], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "host staging copy in");
+        const void* cg[1] = {(const unsigned char*)coeffs + (size_t)c0 * cps * p->elem};
+        const double* lg[1] = {log_scale ? log_scale + (size_t)c0 * lps : nullptr};
+        st = !is_f64(p) ? run_chain<float>(p, fdev, nb, cg, lg, 1, odev, s)
+                        : run_chain<double>(p, fdev, nb, cg, lg, 1, odev, s);
+        if (st != SE2_OK) return st;
+        e = cudaEventRecord(p->hev_done[k], s);
+        // out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hout, p->hev_done[k], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((unsigned char*)out + off, odev, bytes, cudaMemcpyDeviceToHost, p->hout);
+        if (e == cudaSuccess) e = cudaEventRecord(p->hev_out[k], p->hout);
+        if (e != cudaSuccess) return cuda_fail(e, "host staging copy out");
+    }
+    for (int k = 0; k < kHostBufs && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s, p->hev_out[k], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "host staging join");
+    return SE2_OK;
 }
 
 se2_status se2_backward(se2_plan_t p, const void* grad_out, const void* f, int B, const void* coeffs,

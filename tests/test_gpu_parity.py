@@ -260,6 +260,31 @@ print("ok", err)
     _sub({"SE2_PIPE_DEPTH": "2", "SE2_PIPE_GROUP": "2"}, graph)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_convolution(se2, pinned):
+    """se2_convolve_host: f and out on the host, groups of 4 through three
+    staging slots (B = 9: five groups of at most 2, slots reused)."""
+    N, M, B = 64, 16, 9
+    rng = np.random.default_rng(13)
+    F = rng.standard_normal((B, M, N, N)).astype(np.float32)
+    P = rng.random((B, M, N, N)).astype(np.float32)
+    plan = se2.Plan(N, M, batch=B)
+    C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
+    hf = torch.from_numpy(F)
+    if pinned:
+        hf = hf.pin_memory()
+    for _ in range(2):   # the second call reuses the staging buffers
+        out = se2.convolve_host(plan, hf, C).double().numpy()
+        for b in range(B):
+            want = O.convolve(F[b].astype(float), P[b].astype(float))
+            assert _rel(out[b], want) < 1e-5
+    import ctypes
+    lib = se2.load_library()
+    st = lib.se2_convolve_host(plan.handle, ctypes.c_void_p(hf.data_ptr()), 2, ctypes.c_void_p(C.data_ptr()), None,
+                               ctypes.c_void_p(hf.data_ptr() + 4), None)
+    assert st == 1      # out overlaps f
+
+
 def test_invalid_arguments_on_gpu_plan(se2):
     plan = se2.Plan(32, 16, batch=2)
     f = torch.zeros((3, 16, 32, 32), device="cuda")
