@@ -15,7 +15,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -225,10 +224,12 @@ def main():
     t_wall0 = time.time()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = plan.launches()
     e0.record(stream)
     for _ in range(args.steps):
         se2.convolve(plan, f, C, out=out)
     e1.record(stream)
+    launches_timed = plan.launches() - launches0
     barrier()
     t_wall1 = time.time()
     ms = e0.elapsed_time(e1)
@@ -267,8 +268,6 @@ def main():
     hbm, src = peaks()
     alg_bytes = B * (4 * L + 4 * L + 8 * M * N * (N // 2 + 1))   # read f, write out, read half spectrum
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
-    chunks = math.ceil(B / plan_chunk(plan, N, M, B))
-    launches_per_step = chunks * 3
 
     line = None
     if rank == 0:
@@ -290,7 +289,7 @@ def main():
             "cpu_baseline": base,
             "e2e": {"value": e2e_val, "unit": "conv/s", "h2d_bytes_per_step": int(F.nbytes),
                     "d2h_bytes_per_step": int(F.nbytes)},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": launches_timed,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -300,20 +299,10 @@ def main():
         dist.destroy_process_group()
 
 
-def plan_chunk(plan, N, M, B):
-    """Problems per scratch pass (mirrors the library's choice: up to 1 GiB)."""
-    tp = ((N // 2 + 1) + 15) // 16 * 16
-    per = M * N * tp * 8
-    env = os.environ.get("SE2_MAX_CHUNK")
-    c = max(1, (1 << 30) // per)
-    if env and 1 <= int(env) < c:
-        c = int(env)
-    return min(c, B)
-
-
-def _clock_and_time(fn, steps, warmup, dev, settle=0.6):
+def _clock_and_time(fn, steps, warmup, dev, settle=0.6, plans=()):
     """Warm up, settle ~0.6 s under load (clock sampling), then time `steps`
-    calls of fn with CUDA events on the current stream."""
+    calls of fn with CUDA events on the current stream.  Returns (ms, clocks,
+    kernels the given plans launched in the timed region)."""
     import torch
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     sampler = ClockSampler(vis.split(",")[dev.index or 0].strip() if vis else (dev.index or 0))
@@ -327,14 +316,16 @@ def _clock_and_time(fn, steps, warmup, dev, settle=0.6):
         torch.cuda.synchronize(dev)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sum(p.launches() for p in plans)
     e0.record(stream)
     for _ in range(steps):
         fn()
     e1.record(stream)
+    launched = sum(p.launches() for p in plans) - l0
     torch.cuda.synchronize(dev)
     t1 = time.time()
     sampler.stop()
-    return e0.elapsed_time(e1), sampler.summary(t0, t1)
+    return e0.elapsed_time(e1), sampler.summary(t0, t1), launched
 
 
 def _line(metric, value, unit, args, ms, cfg, extra):
@@ -363,7 +354,8 @@ def run_chain8(args):
     f = torch.stack(Fs).to(dev)
     C = [se2.coeffs(plan, torch.stack(c).to(dev))[0] for c in Cs]
     out = torch.empty_like(f)
-    ms, clocks = _clock_and_time(lambda: se2.convolve_chain(plan, f, C, out=out), args.steps, args.warmup, dev)
+    ms, clocks, launched = _clock_and_time(lambda: se2.convolve_chain(plan, f, C, out=out), args.steps, args.warmup,
+                                           dev, plans=(plan,))
     L = N * N * M
     alg = B * (8 * L + k * 8 * M * N * (N // 2 + 1))
     hbm, src = peaks()
@@ -372,7 +364,7 @@ def run_chain8(args):
           {"workload": f"se2_convolve_chain k=8 distinct kernels, batch {B}", "grid": [M, N, N]},
           {"roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "traffic": None, "peak_source": src, "alg_bytes_per_chain": alg / B},
-           "gpu_launches": 3 * args.steps, "clocks": clocks})
+           "gpu_launches": launched, "clocks": clocks})
 
 
 def run_batch(args):
@@ -401,7 +393,7 @@ def run_batch(args):
     runner.build_tables()
     runner.tune()
     runner.capture()
-    ms, clocks = _clock_and_time(runner.replay, args.steps, args.warmup, dev)
+    ms, clocks, _ = _clock_and_time(runner.replay, args.steps, args.warmup, dev)
     pts = runner.points()
     hbm, src = peaks()
     alg = 8 * pts                                     # read f, write out (factored coefficients)
@@ -442,7 +434,7 @@ def run_precision(args):
         plan = se2.Plan(N, M, batch=B, precision=prec)
         tab = se2.separable_tables(plan, params, kk)
         out = torch.empty_like(f)
-        ms, clocks = _clock_and_time(lambda: se2.convolve_separable(plan, f, tab, out), args.steps, args.warmup, dev)
+        ms, clocks, _ = _clock_and_time(lambda: se2.convolve_separable(plan, f, tab, out), args.steps, args.warmup, dev)
         plan.status()
         res[prec] = (B * args.steps / (ms / 1e3), ms, out[0].double().cpu().numpy(), clocks)
         plan.close()
@@ -480,12 +472,12 @@ def run_adjoint(args):
         out = se2.SE2Conv.apply(f, params, plan)
         loss = 0.5 * ((out - target) ** 2).sum()
         loss.backward()
-    ms, clocks = _clock_and_time(step, args.steps, args.warmup, dev)
+    ms, clocks, launched = _clock_and_time(step, args.steps, args.warmup, dev, plans=(plan,))
     _line("SE(2) forward+adjoint convolutions/s at N=256, M=64, batch 64 (FP32)", B * args.steps / (ms / 1e3),
           "conv/s", args, ms, {"workload": "loss = 1/2||f * rho(sigma, sigma_theta) - target||^2, grads wrt f and "
                                "(sigma, sigma_theta); includes kernel sampling, 3 coefficient transforms, forward, adjoint",
                                "grid": [M, N, N], "global_batch": B},
-          {"clocks": clocks})
+          {"clocks": clocks, "gpu_launches": launched})
 
 
 if __name__ == "__main__":

@@ -191,6 +191,15 @@ se2_status se2_convolve_separable(se2_plan_t plan, const void* f, int B, const v
                                   void* stream);
 
 /*
+ * se2_plan_launches -- the number of kernels the plan's entry points have
+ * launched so far (host-side count, updated as launches are enqueued; plan
+ * creation's own set-up launches are not counted).  0 for a NULL plan.
+ * Lets a caller state how many kernels a call or a timed loop ran.  The paper
+ * has no counterpart.
+ */
+unsigned long long se2_plan_launches(se2_plan_t plan);
+
+/*
  * se2_plan_status -- synchronise `stream`, then report and clear the plan's
  * device error word.  The persistent convolution kernel waits on counters
  * that other blocks of the same launch update; each wait is bounded (about a

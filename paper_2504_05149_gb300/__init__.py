@@ -64,6 +64,8 @@ def load_library(path: str = LIB_PATH):
     lib.se2_backward.argtypes = [vp, vp, vp, ip, vp, vp, ip, ctypes.POINTER(vp), vp, vp, vp]
     lib.se2_sample_radial_gaussian.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
+    lib.se2_plan_launches.argtypes = [vp]
+    lib.se2_plan_launches.restype = ctypes.c_ulonglong
     lib.se2_last_error.restype = ctypes.c_char_p
     lib.se2_version.restype = ctypes.c_char_p
     for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_host",
@@ -108,6 +110,10 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    def launches(self) -> int:
+        """Kernels launched through this plan so far (se2_plan_launches)."""
+        return int(load_library().se2_plan_launches(self._h))
 
     def workspace_bytes(self) -> int:
         return int(load_library().se2_plan_workspace_bytes(self._h))

@@ -201,10 +201,16 @@ class BatchRunner:
         self.run()                                   # warm-up outside capture
         torch.cuda.synchronize(self.dev)
         g = torch.cuda.CUDAGraph()
+        before = self._launch_count()
         with torch.cuda.graph(g):
             self.run()
+        self._graph_launches = self._launch_count() - before
         self.graph = g
         return g
+
+    def _launch_count(self) -> int:
+        used = {self._plan_for(c, *self.config[c]) for c in self.order}
+        return sum(p.launches() for p in used)
 
     def replay(self):
         if self.graph is None:
@@ -212,24 +218,14 @@ class BatchRunner:
         self.graph.replay()
 
     def launches_per_run(self) -> int:
-        """Kernel launches of one run() with the chosen configuration (the
-        library's scratch chunking mirrored here: up to 1 GiB per pass; every
-        class of this runner is a fused size, three kernels per pass)."""
-        total = 0
-        for c in self.order:
-            path, per = self.config[c]
-            n = len(self.classes[c])
-            calls = -(-n // per)
-            if path == "persistent":
-                total += calls
-            else:
-                N, M = c
-                tp = ((N // 2 + 1) + 15) // 16 * 16
-                chunk = max(1, min(per, (1 << 30) // (M * N * tp * 8)))
-                for s in range(0, n, per):
-                    nb = min(per, n - s)
-                    total += 3 * (-(-nb // chunk))
-        return total
+        """Kernel launches of one run() with the chosen configuration, as
+        counted by the plans (se2_plan_launches) while the graph was captured,
+        or over one eager run()."""
+        if getattr(self, "_graph_launches", None) is not None:
+            return self._graph_launches
+        before = self._launch_count()
+        self.run()
+        return self._launch_count() - before
 
     def points(self) -> int:
         return sum(N * N * M * len(v) for (N, M), v in self.classes.items())

@@ -57,6 +57,7 @@ void se2::set_last_error(const char* msg) { g_err = msg; }
 
 constexpr int kMaxPipe = 4;
 constexpr int kPipeDepth = 2, kPipeGroup = 2;   // default pipelining of the FP32 fast path
+constexpr long long kPipePoints = 2ll * 256 * 256 * 64;
 constexpr int kHostBufs = 3, kHostGroup = 2;    // staging of se2_convolve_host
 
 struct se2_plan_s {
@@ -89,6 +90,7 @@ struct se2_plan_s {
     KTable<float> kf;
     KTable<double> kd;
     bool fused = false;
+    unsigned long long launches = 0;   // kernels launched by this plan so far
     // FP32 paired-FFT kernels for the convolution and chain (null: generic ones)
     bool fast = false;
     FastTable ft;
@@ -206,6 +208,8 @@ se2_status plan_init(se2_plan_s* p) {
                 r = cudaFuncSetAttribute((const void*)p->ft.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_xt);
             if (r == cudaSuccess)
                 r = cudaFuncSetAttribute((const void*)p->ft.lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute((const void*)p->ft.lines_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
             if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
             p->fast = true;
         }
@@ -311,9 +315,11 @@ void launch_forward(se2_plan_s* p, const T* f, int nb, double* abs_sum, cudaStre
     a.abs_sum = abs_sum;
     if (p->fused) {
         kt.fwd_xt<<<dim3(p->N, nb), kThreads, kt.smem_xt, st>>>(a);
+        ++p->launches;
     } else {
         const int pairs = p->M / 2;
         kt.fwd_x<<<dim3(p->N, (pairs + kt.teams_x - 1) / kt.teams_x, nb), kThreads, kt.smem_x, st>>>(a);
+        ++p->launches;
         LArgs<T> l{};
         l.s = a.s;
         l.s_pstride = p->s_pstride;
@@ -326,6 +332,7 @@ void launch_forward(se2_plan_s* p, const T* f, int nb, double* abs_sum, cudaStre
         const long long lines = (long long)p->N * (p->N / 2 + 1);
         if (p->tc) launch_tc<T>(p, a.s, nb, -1, st);
         else kt.t_fwd<<<dim3((unsigned)((lines + kt.lines_t - 1) / kt.lines_t), nb), kThreads, kt.smem_t, st>>>(l);
+        ++p->launches;
     }
 }
 
@@ -336,6 +343,7 @@ void launch_inverse(se2_plan_s* p, T* out, int nb, cudaStream_t st, int slot0 = 
     a.out = out;
     if (p->fused) {
         kt.inv_tx<<<dim3(p->N, nb), kThreads, kt.smem_xt, st>>>(a);
+        ++p->launches;
     } else {
         LArgs<T> l{};
         l.s = a.s;
@@ -349,8 +357,10 @@ void launch_inverse(se2_plan_s* p, T* out, int nb, cudaStream_t st, int slot0 = 
         const long long lines = (long long)p->N * (p->N / 2 + 1);
         if (p->tc) launch_tc<T>(p, a.s, nb, +1, st);
         else kt.t_inv<<<dim3((unsigned)((lines + kt.lines_t - 1) / kt.lines_t), nb), kThreads, kt.smem_t, st>>>(l);
+        ++p->launches;
         const int pairs = p->M / 2;
         kt.inv_x<<<dim3(p->N, (pairs + kt.teams_x - 1) / kt.teams_x, nb), kThreads, kt.smem_x, st>>>(a);
+        ++p->launches;
     }
 }
 
@@ -416,6 +426,7 @@ se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* c
     const int grid = (int)(units < p->persist_grid ? units : p->persist_grid);
     if (sep_tables) kt.persist_sep<<<grid, kThreads, kt.smem_persist, st>>>(a);
     else kt.persist<<<grid, kThreads, kt.smem_persist, st>>>(a);
+    ++p->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SE2_OK;
@@ -427,7 +438,8 @@ se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* c
 // each stream with its own scratch slots; a group's three kernels stay in
 // order on its stream while groups on other streams overlap them.
 se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* const* coeffs,
-                          const double* const* log_scales, int k, float* out, cudaStream_t st) {
+                          const double* const* log_scales, int k, float* out, cudaStream_t st,
+                          const float2* sep_tables = nullptr) {
     const FastTable& ft = p->ft;
     const size_t g = (size_t)p->N * p->N * p->M;
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
@@ -459,13 +471,22 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
         a.c_pstride = cps;
         a.ls_pstride = lps;
         a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
-        for (int q = 0; q < k; ++q) {
-            a.C[q] = (const float2*)coeffs[q] + c0 * cps;
-            a.ls[q] = (log_scales && log_scales[q]) ? log_scales[q] + c0 * lps : nullptr;
+        if (sep_tables != nullptr) {
+            const long long tps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)(p->N / 2 + 1 + p->N + p->M);
+            a.sep = sep_tables + c0 * tps;
+            a.sep_pstride = tps;
+        } else {
+            for (int q = 0; q < k; ++q) {
+                a.C[q] = (const float2*)coeffs[q] + c0 * cps;
+                a.ls[q] = (log_scales && log_scales[q]) ? log_scales[q] + c0 * lps : nullptr;
+            }
         }
         ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);
-        ft.lines<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);
+        ++p->launches;
+        (sep_tables != nullptr ? ft.lines_sep : ft.lines)<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);
+        ++p->launches;
         ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);
+        ++p->launches;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -502,6 +523,7 @@ se2_status run_chain(se2_plan_s* p, const void* f, int B, const void* const* coe
             l.ls[i] = (log_scales && log_scales[i]) ? log_scales[i] + c0 * lps : nullptr;
         }
         kt.y_conv<<<dim3(y_blocks<T>(p), nb), kThreads, kt.smem_y, st>>>(l);
+        ++p->launches;
         launch_inverse<T>(p, (T*)out + c0 * g, nb, st);
     }
     cudaError_t e = cudaGetLastError();
@@ -529,6 +551,7 @@ se2_status run_coeffs(se2_plan_s* p, const void* samples, int n, void* coeffs, d
         l.log_scale = log_scale;
         l.problem0 = c0;
         kt.y_coef<<<dim3(y_blocks<T>(p), nb), kThreads, kt.smem_y, st>>>(l);
+        ++p->launches;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -560,6 +583,7 @@ se2_status run_backward(se2_plan_s* p, const void* g, const void* f, int B, cons
         for (int i = 0; i < n_params; ++i) l.dC[i] = (const c2<T>*)dcoeffs[i] + c0 * cps;
         l.grad_params = grad_params;
         kt.y_adj<<<dim3(y_blocks<T>(p), nb), kThreads, kt.smem_y, st>>>(l);
+        ++p->launches;
         if (grad_f) launch_inverse<T>(p, (T*)grad_f + c0 * gs, nb, st, 0);
     }
     cudaError_t e = cudaGetLastError();
@@ -571,6 +595,9 @@ template <typename T>
 se2_status run_sep(se2_plan_s* p, const void* f, int B, const void* tables, void* out, cudaStream_t st) {
     KTable<T>& kt = table<T>(p);
     if (p->persist) return run_persist<T>(p, f, B, nullptr, nullptr, 1, out, st, 0, kSpinLimit, tables);
+    if constexpr (sizeof(T) == 4) {
+        if (p->fast) return run_chain_fast(p, (const float*)f, B, nullptr, nullptr, 1, (float*)out, st, (const float2*)tables);
+    }
     const size_t g = (size_t)p->N * p->N * p->M;
     const long long tps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)(p->N / 2 + 1 + p->N + p->M);
     for (int c0 = 0; c0 < B; c0 += p->chunk) {
@@ -581,6 +608,7 @@ se2_status run_sep(se2_plan_s* p, const void* f, int B, const void* tables, void
         l.sep = (const c2<T>*)tables + c0 * tps;
         l.sep_pstride = tps;
         kt.y_sep<<<dim3(y_blocks<T>(p), nb), kThreads, kt.smem_y, st>>>(l);
+        ++p->launches;
         launch_inverse<T>(p, (T*)out + c0 * g, nb, st);
     }
     cudaError_t e = cudaGetLastError();
@@ -654,7 +682,11 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (p->fast) {
         // pipelined groups (SE2_PIPE_DEPTH / SE2_PIPE_GROUP in the environment
         // override the defaults); depth * group scratch slots must exist
-        int depth = kPipeDepth, group = kPipeGroup;
+        // a group holds at least kPipePoints grid points (2 problems at
+        // 256^2 x 64), so that small problems are not split into tiny launches
+        const long long pts = (long long)N * N * M;
+        int depth = kPipeDepth, group = (int)((kPipePoints + pts - 1) / pts);
+        if (group < kPipeGroup) group = kPipeGroup;
         if (const char* v = getenv("SE2_PIPE_DEPTH")) depth = (int)strtol(v, nullptr, 10);
         if (const char* v = getenv("SE2_PIPE_GROUP")) group = (int)strtol(v, nullptr, 10);
         if (depth > kMaxPipe) depth = kMaxPipe;
@@ -842,12 +874,14 @@ se2_status se2_sample_radial_gaussian(se2_plan_t p, double sigma, double sigma_t
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
     k_gauss_tables<<<(p->N + p->M + 127) / 128, 128, 0, s>>>(p->tab, p->N, p->M, sigma, sigma_theta, nu);
+    ++p->launches;
     const long long total = (long long)p->N * p->N * p->M;
     const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
     if (!is_f64(p))
         k_gauss_fill<float><<<blocks, 256, 0, s>>>(p->tab, p->N, p->M, (float*)P, (float*)dP_dsigma, (float*)dP_dsigma_theta);
     else
         k_gauss_fill<double><<<blocks, 256, 0, s>>>(p->tab, p->N, p->M, (double*)P, (double*)dP_dsigma, (double*)dP_dsigma_theta);
+    ++p->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SE2_OK;
@@ -868,6 +902,7 @@ se2_status se2_separable_tables(se2_plan_t p, const double* params, const int* k
         k_sep_tables<float><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (float2*)tables, tps);
     else
         k_sep_tables<double><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (double2*)tables, tps);
+    ++p->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SE2_OK;
@@ -913,6 +948,8 @@ se2_status se2_debug_wait_timeout(se2_plan_t p, const void* f, const void* coeff
     // one problem whose A->B wait can never be met; 4096 polls end it quickly
     return run_persist<float>(p, f, 1, c, nullptr, 1, out, (cudaStream_t)stream, 1u, 4096);
 }
+
+unsigned long long se2_plan_launches(se2_plan_t p) { return p == nullptr ? 0ull : p->launches; }
 
 se2_status se2_convolve(se2_plan_t p, const void* f, int B, const void* coeffs, const double* log_scale,
                         void* out, void* stream) {

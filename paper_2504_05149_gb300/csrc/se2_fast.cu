@@ -11,10 +11,11 @@ namespace se2 {
 namespace {
 template <int N, int M>
 bool fill_fast_nm(FastTable* t) {
-    constexpr size_t sx = fast_xt_smem<N, M>(), sy = fast_lines_smem<N>();
+    constexpr size_t sx = fast_xt_smem<N, M>(), sy = fast_lines_smem<N, M>();
     if constexpr (sx <= kMaxDynSmem && sy <= kMaxDynSmem) {
         t->fwd = kf_fwd_xt<N, M>;
-        t->lines = kf_lines<N, M>;
+        t->lines = kf_lines<N, M, false>;
+        t->lines_sep = kf_lines<N, M, true>;
         t->inv = kf_inv_tx<N, M>;
         t->smem_xt = sx;
         t->smem_y = sy;

@@ -238,6 +238,11 @@ struct FArgs {
     const double* ls[kMaxChain]; // per-problem log scales (or null)
     long long c_pstride, ls_pstride;
     double inv_L;
+    // separable coefficients instead of C (kf_lines<.., true>): per problem
+    // tables tx[N/2+1], ty[N], tt[M] with C = tx[kx] ty[ky] tt[m], W^(k-1)
+    // folded in (the multiply applies W once)
+    const float2* sep;
+    long long sep_pstride;
 };
 
 // Step-A twiddle table of the team FFT of length L = R1 * R2 (layout of
@@ -408,9 +413,10 @@ template <int N> __host__ __device__ constexpr int fast_xs() {
 }
 template <int N> __host__ __device__ constexpr int fast_lines() { return kThreads / team_size<N>(); }
 
-template <int N, int M>
+template <int N, int M, bool SEP>
 __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     constexpr int Q = N / 4, P1 = Q + 1, CP = N / 2 + 1, TP4 = ftp4<N>();
+    constexpr int TL = N / 2 + 1 + N + M;    // separable table length
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, RM = reg_count<N>();
     constexpr int LINES = fast_lines<N>(), XS = fast_xs<N>();
     static_assert(R1 % 2 == 0, "ky parity is the lane parity");
@@ -418,6 +424,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     float4* XB = fsm;
     float4* TWF = fsm + LINES * XS;     // forward (R1 x R2) and inverse (R2 x R1) tables
     float4* TWI = TWF + N;
+    float2* TSEP = reinterpret_cast<float2*>(TWI + N);   // this problem's separable tables
     __shared__ double sh_scale;
     const int tid = threadIdx.x, b = blockIdx.y;
     const int c = tid % LINES, t = tid / LINES;
@@ -440,7 +447,10 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     // table fills and the scale overlap the loads
     fill_tw4<R1, R2>(TWF, a.twN);
     fill_tw4<R2, R1>(TWI, a.twN);
-    if (tid == 0) {
+    if constexpr (SEP) {
+        copy_tw(TSEP, a.sep + (size_t)b * a.sep_pstride, TL);
+        if (tid == 0) sh_scale = 0.5 * a.inv_L;
+    } else if (tid == 0) {
         double lsum = 0;
         for (int i = 0; i < a.k; ++i)
             if (a.ls[i] != nullptr) lsum += a.ls[i][b * a.ls_pstride];
@@ -453,9 +463,25 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
         const bool hasb = u < Q;
         const int kxa = hasb ? u : N / 2;
         const float sc = (float)sh_scale;
-        const bool neg = (a.k & 1) && ((u + t) & 1);        // W^k at (kx, ky), both halves alike
+        const bool neg = (SEP || (a.k & 1)) && ((u + t) & 1);   // W^k at (kx, ky), both halves alike
         const float2 s2 = bc2(neg ? -sc : sc);
-        for (int i = 0; i < a.k; ++i) {
+        if constexpr (SEP) {
+            // C = (tx[kx] tt[m]) ty[ky]: the x and theta factors once per lane
+            const float2 ct = TSEP[N / 2 + 1 + N + o];
+            const float2 xa = TSEP[kxa], xq = hasb ? TSEP[kxa + Q] : pf(0.f, 0.f);
+            const float2 xr = pf(xa.x * ct.x - xa.y * ct.y, xq.x * ct.x - xq.y * ct.y);
+            const float2 xi = pf(xa.x * ct.y + xa.y * ct.x, xq.x * ct.y + xq.y * ct.x);
+#pragma unroll
+            for (int k = 0; k < R2; ++k) {
+                const float2 ty = TSEP[N / 2 + 1 + t + R1 * k];
+                const float2 tyr = bc2(ty.x), tyi = bc2(ty.y);
+                const float2 cr = pfma(xr, tyr, pneg(pmul(xi, tyi))), ci = pfma(xr, tyi, pmul(xi, tyr));
+                const float2 r = pfma(re[k], cr, pneg(pmul(im[k], ci)));
+                im[k] = pfma(re[k], ci, pmul(im[k], cr));
+                re[k] = r;
+            }
+        }
+        for (int i = 0; i < (SEP ? 0 : a.k); ++i) {
             const float2* cb = a.C[i] + (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa + (size_t)t * CP;
             float2 ca[R2], cq[R2];
 #pragma unroll
@@ -615,6 +641,8 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
 }
 
 template <int N, int M> constexpr size_t fast_xt_smem() { return (size_t)(fslab4<N, M>() + N + M / 2) * sizeof(float4); }
-template <int N> constexpr size_t fast_lines_smem() { return (size_t)(fast_lines<N>() * fast_xs<N>() + 2 * N) * sizeof(float4); }
+template <int N, int M> constexpr size_t fast_lines_smem() {
+    return (size_t)(fast_lines<N>() * fast_xs<N>() + 2 * N) * sizeof(float4) + (size_t)(N / 2 + 1 + N + M) * sizeof(float2);
+}
 
 }  // namespace se2

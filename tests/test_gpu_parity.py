@@ -222,6 +222,21 @@ def test_paired_and_generic_fp32_kernels_agree(se2):
     _sub({"SE2_MAX_CHUNK": "2"}, code)
 
 
+@pytest.mark.parametrize("k", [2, 3])
+def test_pipelined_chains_with_log_scale(se2, k):
+    """Fast path at 256^2 x 64 with B = 5 (pipeline groups 2, 2, 1): chains of
+    k distinct kernels (W^k for odd and even k) with normalised spectra and
+    FP64 log scales, against the oracle's chain."""
+    N, M, B = 256, 64, 5
+    rng = np.random.default_rng(100 + k)
+    Fs = [rng.standard_normal((M, N, N)).astype(np.float32).astype(np.float64) for _ in range(B)]
+    Ps = [[(rng.random((M, N, N)) * 10.0 ** (i - 1)).astype(np.float32).astype(np.float64) for i in range(k)]
+          for _ in range(B)]
+    out, _, Ls = _run(se2, "f32", Fs, Ps, normalize=True)
+    for b in range(B):
+        assert _rel(out[b], O.convolve_chain(Fs[b], Ps[b])) < 1e-5
+
+
 def test_pipelined_groups_on_several_streams(se2):
     """FP32 fast path with the batch in groups on 3 streams (ragged last
     group), and the same call captured in a CUDA graph and replayed."""
