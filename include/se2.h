@@ -202,11 +202,12 @@ unsigned long long se2_plan_launches(se2_plan_t plan);
 /*
  * se2_plan_status -- synchronise `stream`, then report and clear the plan's
  * device error word.  The persistent convolution kernel waits on counters
- * that other blocks of the same launch update; each wait is bounded (about a
- * second).  A wait that gives up sets the error word, the launch stops taking
- * work, and its output is undefined.  Returns SE2_ERR_TIMEOUT in that case,
- * SE2_OK otherwise.  Until it is read, later launches on the plan also stop
- * at once.
+ * that other blocks of the same launch update and the tensor-core DFT on
+ * its matrix products; each wait is bounded (about a second).  A wait that
+ * gives up sets the error word, the kernel stops, and the call's output is
+ * undefined.  Returns
+ * SE2_ERR_TIMEOUT in that case, SE2_OK otherwise.  Until it is read, later
+ * launches of the persistent kernel also stop at once.
  */
 se2_status se2_plan_status(se2_plan_t plan, void* stream);
 

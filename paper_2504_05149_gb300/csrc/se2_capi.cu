@@ -933,7 +933,7 @@ se2_status se2_plan_status(se2_plan_t p, void* stream) {
     if (h != 0) {
         e = cudaMemset(p->err, 0, sizeof(int));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
-        return fail(SE2_ERR_TIMEOUT, "a device-side wait of the persistent kernel gave up (code %d)", h);
+        return fail(SE2_ERR_TIMEOUT, "a bounded device-side wait gave up (code %d: 1 persistent kernel, 2 tensor cores)", h);
     }
     return SE2_OK;
 }

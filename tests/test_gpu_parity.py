@@ -228,10 +228,13 @@ def test_pipelined_chains_with_log_scale(se2, k):
     k distinct kernels (W^k for odd and even k) with normalised spectra and
     FP64 log scales, against the oracle's chain."""
     N, M, B = 256, 64, 5
-    rng = np.random.default_rng(100 + k)
-    Fs = [rng.standard_normal((M, N, N)).astype(np.float32).astype(np.float64) for _ in range(B)]
-    Ps = [[(rng.random((M, N, N)) * 10.0 ** (i - 1)).astype(np.float32).astype(np.float64) for i in range(k)]
-          for _ in range(B)]
+    Fs, Ps = [], []
+    for b in range(B):
+        prob = synth.make_problem(2, 700 + 10 * k + b, N, M, n_bumps=16, n_kernels=k)
+        Fs.append(synth.sample_bumps(N, M, prob.bumps).astype(np.float32).astype(np.float64))
+        # kernel i scaled by 10^(i-1): the log scales carry the magnitudes
+        Ps.append([(synth.sample_kernel(N, M, kp) * 10.0 ** (i - 1)).astype(np.float32).astype(np.float64)
+                   for i, kp in enumerate(prob.kernels)])
     out, _, Ls = _run(se2, "f32", Fs, Ps, normalize=True)
     for b in range(B):
         assert _rel(out[b], O.convolve_chain(Fs[b], Ps[b])) < 1e-5
@@ -298,6 +301,24 @@ def test_host_buffer_convolution(se2, pinned):
     st = lib.se2_convolve_host(plan.handle, ctypes.c_void_p(hf.data_ptr()), 2, ctypes.c_void_p(C.data_ptr()), None,
                                ctypes.c_void_p(hf.data_ptr() + 4), None)
     assert st == 1      # out overlaps f
+
+
+def test_input_offset_by_one_float(se2):
+    """f starting 4 bytes past a 16-byte boundary (a view one float into a
+    buffer) still matches the oracle."""
+    N, M, B = 64, 16, 3
+    rng = np.random.default_rng(17)
+    F = rng.standard_normal((B, M, N, N)).astype(np.float32)
+    P = rng.random((B, M, N, N)).astype(np.float32)
+    plan = se2.Plan(N, M, batch=B)
+    C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
+    big = torch.zeros(F.size + 1, dtype=torch.float32, device="cuda")
+    f = big[1:].view(B, M, N, N)
+    f.copy_(torch.from_numpy(F))
+    assert f.data_ptr() % 16 == 4
+    out = se2.convolve(plan, f, C).double().cpu().numpy()
+    for b in range(B):
+        assert _rel(out[b], O.convolve(F[b].astype(float), P[b].astype(float))) < 1e-5
 
 
 def test_invalid_arguments_on_gpu_plan(se2):
