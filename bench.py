@@ -145,6 +145,15 @@ def cpu_baseline(N, M, seconds=12.0):
             "sample": f"{n} single convolutions N={N} M={M} (numpy FFT route, FP64, precomputed kernel spectrum), {el:.1f} s"}
 
 
+METRIC_C2 = "SE(2) convolutions/s at N=256, M=64 (FP32) and fraction of HBM roofline"
+
+
+def c2_config(N, M, B, world):
+    return {"workload": f"se2_convolve, batch of {B} independent problems per GPU, N={N}, M={M}, "
+                        f"one radial kernel per problem (precomputed spectra), 16-bump f1",
+            "global_batch": B * world, "grid": [M, N, N], "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -162,11 +171,11 @@ def run_reference(args):
         O.convolve_chain(F, None, coeffs=[C])
     el = time.perf_counter() - t0
     v = args.steps / el
-    line = {"metric": "SE(2) convolutions/s at N=256, M=64", "value": v, "unit": "conv/s", "impl": "reference",
+    line = {"metric": METRIC_C2, "value": v, "unit": "conv/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"single SE(2) convolution N={N} M={M}, one problem per step (bounded sample)",
-                       "l2": "host"},
+            "config": {**c2_config(N, M, args.batch, 1),
+                       "sample": f"one of the {args.batch} problems per step (bounded sample on the host)"},
             "cpu_baseline": {"value": v, "unit": "conv/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} single convolutions, numpy FFT route, FP64"},
             "e2e": {"value": v, "unit": "conv/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -278,19 +287,18 @@ def main():
     if rank == 0:
         base = None if args.no_cpu_baseline or world > 1 else cpu_baseline(N, M)
         line = {
-            "metric": "SE(2) convolutions/s at N=256, M=64 (FP32) and fraction of HBM roofline",
+            "metric": METRIC_C2,
             "value": value, "unit": "conv/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "f32" else f"f32 storage, {args.precision} tensor-core angular DFT",
             "data": "synthetic",
-            "config": {"workload": f"se2_convolve, batch of {B} independent problems per GPU, N={N}, M={M}, "
-                                   f"one radial kernel per problem (precomputed spectra), 16-bump f1",
-                       "global_batch": B * world, "grid": [M, N, N], "parallelism": f"replicas x{world}",
+            "config": {**c2_config(N, M, B, world),
                        "l2": f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB moved per step)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                         "frac": achieved / hbm, "peak_source": src,
                          "scope": "whole se2_convolve step (all kernels)",
-                         "alg_bytes_per_conv": alg_bytes / B},
+                         "alg_bytes_per_conv": alg_bytes / B,
+                         **traffic_fields(N, M, args.precision)},
             "cpu_baseline": base,
             "e2e": {"value": e2e_val, "unit": "conv/s", "h2d_bytes_per_step": int(F.nbytes),
                     "d2h_bytes_per_step": int(F.nbytes)},
@@ -302,6 +310,24 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# DRAM bytes per convolution of the FP32 paired kernels at 256^2 x 64: the sum
+# of dram__bytes_read.sum + dram__bytes_write.sum of kf_fwd_xt, kf_lines and
+# kf_inv_tx from one `ncu --set full` capture (one launch each, 2 problems
+# per launch), profiles/kf_units_f32_256x256x64_b4_full.md.  ncu flushes the
+# caches before each kernel, so the scratch that the live run keeps in L2 is
+# counted as DRAM traffic: an upper bound.
+NCU_TRAFFIC_PER_CONV = {(256, 64, "f32"): (33.603072 + 0.489472 + 71.603456 + 1.072128 + 37.776896 + 0.946432) * 1e6 / 2}
+
+
+def traffic_fields(N, M, precision):
+    t = NCU_TRAFFIC_PER_CONV.get((N, M, precision))
+    if t is None:
+        return {"traffic": None}
+    return {"traffic": t, "traffic_unit": "bytes per convolution",
+            "traffic_source": "ncu --set full, caches flushed per kernel (upper bound); "
+                              "profiles/kf_units_f32_256x256x64_b4_full.md"}
 
 
 def _clock_and_time(fn, steps, warmup, dev, settle=0.6, plans=()):
