@@ -51,12 +51,26 @@ def parse():
     return ap.parse_args()
 
 
+def rank_problem_ids(rank, B):
+    """Seeds of the B problems rank `rank` works on (disjoint across ranks for
+    B <= 100): each replica gets its own independent problems (weak scaling)."""
+    return [100 * rank + b for b in range(B)]
+
+
+def aggregate(ms_local, units_per_rank, world, reduce_max=None):
+    """Whole-job throughput: units processed by all ranks / the slowest rank's
+    time.  reduce_max(float) -> float takes the maximum over ranks (identity
+    for one rank)."""
+    ms = ms_local if reduce_max is None else reduce_max(ms_local)
+    return ms, units_per_rank * world / (ms / 1e3)
+
+
 def workload_inputs(N, M, B, rank):
     """Seeded synthetic batch: f1 (16 bumps) and one kernel per problem."""
     import synth
     Fs, Ps = [], []
-    for b in range(B):
-        prob = synth.make_problem(2, 100 * rank + b, N, M, n_bumps=16, n_kernels=1)
+    for b in rank_problem_ids(rank, B):
+        prob = synth.make_problem(2, b, N, M, n_bumps=16, n_kernels=1)
         Fs.append(synth.sample_bumps(N, M, prob.bumps).astype(np.float32))
         Ps.append(synth.sample_kernel(N, M, prob.kernels[0]).astype(np.float32))
     return np.stack(Fs), np.stack(Ps)
@@ -245,13 +259,14 @@ def main():
     sampler.stop()
     clocks = sampler.summary(t_settle, t_wall1)
 
-    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms = float(tmax.item())
+    def reduce_max(v):
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms, value = aggregate(ms, B * args.steps, world, reduce_max)
     ms_step = ms / args.steps
-    convs = B * args.steps * world
-    value = convs / (ms / 1e3)
 
     # end to end through the public API with host buffers (se2_convolve_host):
     # pinned host f -> device, convolve, device -> host out, overlapped by groups
@@ -273,10 +288,7 @@ def main():
         e3.record(stream)
         barrier()
         reps.append(e2.elapsed_time(e3))
-    me = torch.tensor([sorted(reps)[1]], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(me, op=dist.ReduceOp.MAX)
-    e2e_val = B * ke * world / (float(me.item()) / 1e3)
+    _, e2e_val = aggregate(sorted(reps)[1], B * ke, world, reduce_max)
     assert np.isfinite(hout.numpy()).all()
 
     hbm, src = peaks()
