@@ -210,6 +210,10 @@ se2_status plan_init(se2_plan_s* p) {
                 r = cudaFuncSetAttribute((const void*)p->ft.lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
             if (r == cudaSuccess)
                 r = cudaFuncSetAttribute((const void*)p->ft.lines_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute((const void*)p->ft.lines_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute((const void*)p->ft.lines_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
             if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
             p->fast = true;
         }
@@ -558,11 +562,74 @@ se2_status run_coeffs(se2_plan_s* p, const void* samples, int n, void* coeffs, d
     return SE2_OK;
 }
 
+// The adjoint on the FP32 paired kernels: unit A on grad_out (slots 0..nb-1)
+// and on f (slots nb..2nb-1), the forward y FFT of f's spectrum, the adjoint y
+// pass (partials + correlation spectrum), unit C into grad_f.
+se2_status run_backward_fast(se2_plan_s* p, const float* g, const float* f, int B, const void* coeffs,
+                             const double* log_scale, int n_params, const void* const* dcoeffs,
+                             double* grad_params, float* grad_f, cudaStream_t st) {
+    const FastTable& ft = p->ft;
+    const size_t gs = (size_t)p->N * p->N * p->M;
+    const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
+    const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
+    const long long pairs = (long long)p->M * (p->N / 4 + 1);
+    const unsigned yb = (unsigned)((pairs + ft.lines_per_block - 1) / ft.lines_per_block);
+    const int per_pass = n_params > 0 ? p->nslots / 2 : p->nslots;
+    for (int c0 = 0; c0 < B; c0 += per_pass) {
+        const int nb = (B - c0 < per_pass) ? (B - c0) : per_pass;
+        FArgs a{};
+        a.s_pstride = (long long)(p->s_pstride / 2);
+        a.twN = (const float2*)p->twN;
+        a.twM = (const float2*)p->twM;
+        a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
+        float4* s0 = (float4*)p->scratch;
+        float4* s1 = s0 + (size_t)nb * (p->s_pstride / 2);
+        a.f = g + c0 * gs;
+        a.s = s0;
+        ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+        ++p->launches;
+        if (n_params > 0) {
+            a.f = f + c0 * gs;
+            a.s = s1;
+            ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+            ++p->launches;
+            ft.lines_fwd<<<dim3(yb, nb), kThreads, ft.smem_y, st>>>(a);
+            ++p->launches;
+        }
+        a.s = s0;
+        a.s2 = s1;
+        a.k = 1;
+        a.c_pstride = cps;
+        a.ls_pstride = lps;
+        a.C[0] = (const float2*)coeffs + c0 * cps;
+        a.ls[0] = log_scale ? log_scale + c0 * lps : nullptr;
+        a.n_params = n_params;
+        for (int i = 0; i < n_params; ++i) a.dC[i] = (const float2*)dcoeffs[i] + c0 * cps;
+        a.grad_params = grad_params;
+        a.want_grad = grad_f != nullptr;
+        ft.lines_adj<<<dim3(yb, nb), kThreads, ft.smem_y, st>>>(a);
+        ++p->launches;
+        if (grad_f) {
+            a.out = grad_f + c0 * gs;
+            ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+            ++p->launches;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
+}
+
 template <typename T>
 se2_status run_backward(se2_plan_s* p, const void* g, const void* f, int B, const void* coeffs,
                         const double* log_scale, int n_params, const void* const* dcoeffs,
                         double* grad_params, void* grad_f, cudaStream_t st) {
     KTable<T>& kt = table<T>(p);
+    if constexpr (sizeof(T) == 4) {
+        if (p->fast)
+            return run_backward_fast(p, (const float*)g, (const float*)f, B, coeffs, log_scale, n_params, dcoeffs,
+                                     grad_params, (float*)grad_f, st);
+    }
     const size_t gs = (size_t)p->N * p->N * p->M;
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
     const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;

@@ -14,8 +14,10 @@ bool fill_fast_nm(FastTable* t) {
     constexpr size_t sx = fast_xt_smem<N, M>(), sy = fast_lines_smem<N, M>();
     if constexpr (sx <= kMaxDynSmem && sy <= kMaxDynSmem) {
         t->fwd = kf_fwd_xt<N, M>;
-        t->lines = kf_lines<N, M, false>;
-        t->lines_sep = kf_lines<N, M, true>;
+        t->lines = kf_lines<N, M, FL_CONV>;
+        t->lines_sep = kf_lines<N, M, FL_SEP>;
+        t->lines_fwd = kf_lines<N, M, FL_FWD>;
+        t->lines_adj = kf_lines<N, M, FL_ADJ>;
         t->inv = kf_inv_tx<N, M>;
         t->smem_xt = sx;
         t->smem_y = sy;

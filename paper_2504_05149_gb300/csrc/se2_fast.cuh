@@ -243,7 +243,19 @@ struct FArgs {
     // folded in (the multiply applies W once)
     const float2* sep;
     long long sep_pstride;
+    // adjoint y pass (kf_lines<.., FL_ADJ>): s2 = the y-transformed paired
+    // spectrum of f; dC = derivative spectra; partials accumulate (FP64
+    // atomics) into grad_params; want_grad: also the correlation spectrum
+    const float4* s2;
+    int n_params;
+    const float2* dC[kMaxParams];
+    double* grad_params;
+    int want_grad;
 };
+
+// y-pass modes: the convolution / chain product, the separable product, the
+// forward y FFT only (in place), the adjoint (correlation + parameter partials)
+enum FastLineMode { FL_CONV = 0, FL_SEP = 1, FL_FWD = 2, FL_ADJ = 3 };
 
 // Step-A twiddle table of the team FFT of length L = R1 * R2 (layout of
 // team_fft2) from the forward table src of length L.
@@ -413,8 +425,9 @@ template <int N> __host__ __device__ constexpr int fast_xs() {
 }
 template <int N> __host__ __device__ constexpr int fast_lines() { return kThreads / team_size<N>(); }
 
-template <int N, int M, bool SEP>
+template <int N, int M, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
+    constexpr bool SEP = MODE == FL_SEP;
     constexpr int Q = N / 4, P1 = Q + 1, CP = N / 2 + 1, TP4 = ftp4<N>();
     constexpr int TL = N / 2 + 1 + N + M;    // separable table length
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, RM = reg_count<N>();
@@ -426,6 +439,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     float4* TWI = TWF + N;
     float2* TSEP = reinterpret_cast<float2*>(TWI + N);   // this problem's separable tables
     __shared__ double sh_scale;
+    __shared__ double red[kThreads / 32];
     const int tid = threadIdx.x, b = blockIdx.y;
     const int c = tid % LINES, t = tid / LINES;
     const int pl = blockIdx.x * LINES + c;
@@ -459,6 +473,80 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     __syncthreads();
     team_fft2<R1, R2, -1>(re, im, t, act, xb, TWF, SyncBlock());
     // lane s < R1 holds ky = s + R1 k, k < R2
+    if constexpr (MODE == FL_FWD) {
+        if (act && t < R1) {
+#pragma unroll
+            for (int k = 0; k < R2; ++k)
+                __stcg(base + (size_t)(R1 * k) * TP4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y));
+        }
+        return;
+    }
+    if constexpr (MODE == FL_ADJ) {
+        // parameter partials sum_k m_k W Re(dC_i conj(G) F) over this lane's bins
+        // (m_k = 1 at x bins 0 and N/2, 2 elsewhere; both spectra are doubled)
+        float2 acc[kMaxParams];
+#pragma unroll
+        for (int i = 0; i < kMaxParams; ++i) acc[i] = pf(0.f, 0.f);
+        if (a.n_params > 0 && act && t < R1) {
+            const bool hasb = u < Q;
+            const int kxa = hasb ? u : N / 2;
+            const float sg = ((u + t) & 1) ? -1.f : 1.f;
+            const float2 mw = pf(sg * ((u == 0 || u == Q) ? 1.f : 2.f), sg * 2.f);
+            // F at this lane's bins, staged in the (now idle) exchange area
+            const float4* fb2 = a.s2 + (size_t)b * a.s_pstride + (size_t)o * N * TP4 + u + (size_t)t * TP4;
+#pragma unroll
+            for (int k = 0; k < R2; ++k)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             :: "r"((unsigned)__cvta_generic_to_shared(xb + t + R1 * k)), "l"(fb2 + (size_t)(R1 * k) * TP4)
+                             : "memory");
+            asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+            const size_t coff = (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa + (size_t)t * CP;
+#pragma unroll
+            for (int i = 0; i < kMaxParams; ++i) {
+                if (i < a.n_params) {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        constexpr int KH = R2 / 4;
+                        float2 da[KH], dq[KH];
+#pragma unroll
+                        for (int kk = 0; kk < KH; ++kk) {
+                            const float2* db = a.dC[i] + coff + (size_t)(R1 * (h * KH + kk)) * CP;
+                            da[kk] = __ldcs(db);
+                            dq[kk] = hasb ? __ldcs(db + Q) : pf(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < KH; ++kk) {
+                            const int k = h * KH + kk;
+                            const float4 v = xb[t + R1 * k];
+                            const float2 fr = pf(v.x, v.y), fi = pf(v.z, v.w);
+                            const float2 pr = pfma(re[k], fr, pmul(im[k], fi));      // conj(G) F
+                            const float2 pi = pfma(re[k], fi, pneg(pmul(im[k], fr)));
+                            const float2 vv = pfma(pf(da[kk].x, dq[kk].x), pr, pneg(pmul(pf(da[kk].y, dq[kk].y), pi)));
+                            acc[i] = pfma(vv, mw, acc[i]);
+                        }
+                        asm volatile("" ::: "memory");   // bounds the loads in flight
+                    }
+                }
+            }
+        }
+        __syncthreads();   // the exchange area is free again before the inverse FFT
+#pragma unroll
+        for (int i = 0; i < kMaxParams; ++i) {
+            if (i < a.n_params) {   // uniform over the block
+                double v = (double)acc[i].x + (double)acc[i].y;
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if ((tid & 31) == 0) red[tid >> 5] = v;
+                __syncthreads();
+                if (tid == 0) {
+                    double tsum = 0;
+                    for (int w = 0; w < kThreads / 32; ++w) tsum += red[w];
+                    atomicAdd(a.grad_params + i, 0.25 * a.inv_L * tsum);
+                }
+                __syncthreads();
+            }
+        }
+        if (!a.want_grad) return;
+    }
     if (act && t < R1) {
         const bool hasb = u < Q;
         const int kxa = hasb ? u : N / 2;
@@ -481,20 +569,29 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
                 re[k] = r;
             }
         }
+        // coefficient loads in chunks of CK bins (the adjoint keeps fewer in flight)
+        constexpr int CK = MODE == FL_ADJ ? R2 / 2 : R2;
         for (int i = 0; i < (SEP ? 0 : a.k); ++i) {
             const float2* cb = a.C[i] + (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa + (size_t)t * CP;
-            float2 ca[R2], cq[R2];
 #pragma unroll
-            for (int k = 0; k < R2; ++k) {
-                ca[k] = __ldcs(cb + (size_t)(R1 * k) * CP);
-                cq[k] = hasb ? __ldcs(cb + (size_t)(R1 * k) * CP + Q) : pf(0.f, 0.f);
-            }
+            for (int k0 = 0; k0 < R2; k0 += CK) {
+                float2 ca[CK], cq[CK];
 #pragma unroll
-            for (int k = 0; k < R2; ++k) {
-                const float2 cr = pf(ca[k].x, cq[k].x), ci = pf(ca[k].y, cq[k].y);
-                const float2 r = pfma(re[k], cr, pneg(pmul(im[k], ci)));
-                im[k] = pfma(re[k], ci, pmul(im[k], cr));
-                re[k] = r;
+                for (int kk = 0; kk < CK; ++kk) {
+                    ca[kk] = __ldcs(cb + (size_t)(R1 * (k0 + kk)) * CP);
+                    cq[kk] = hasb ? __ldcs(cb + (size_t)(R1 * (k0 + kk)) * CP + Q) : pf(0.f, 0.f);
+                }
+#pragma unroll
+                for (int kk = 0; kk < CK; ++kk) {
+                    const int k = k0 + kk;
+                    const float2 cr = pf(ca[kk].x, cq[kk].x);
+                    // the adjoint multiplies by conj(C)
+                    const float2 ci = MODE == FL_ADJ ? pf(-ca[kk].y, -cq[kk].y) : pf(ca[kk].y, cq[kk].y);
+                    const float2 r = pfma(re[k], cr, pneg(pmul(im[k], ci)));
+                    im[k] = pfma(re[k], ci, pmul(im[k], cr));
+                    re[k] = r;
+                }
+                if (CK < R2) asm volatile("" ::: "memory");
             }
         }
 #pragma unroll
