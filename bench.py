@@ -275,7 +275,7 @@ def main():
     for _ in range(2):
         se2.convolve_host(plan, hf, C, out=hout)
     barrier()
-    # the host link's throughput varies between runs on this machine: the median
+    # the host link's throughput varies from run to run: the median
     # of three timed repetitions of ke steps
     ke = max(3, min(args.steps, 10))
     reps = []

@@ -36,9 +36,11 @@
 
 static inline long idx3(long l, long j, long i, long N) { return (l * N + j) * N + i; }
 
-void se2_direct_conv(const double* F, const double* P, int N, int M, double* out) {
+/* The same sum with the kernel index shifted by c in x and y: c = N/2 on
+ * Omega_L (x_i = -1/2 + i/N), c = 0 for grids sampled at x_i = i/N (the plain
+ * cyclic convolution). */
+void se2_direct_conv_shift(const double* F, const double* P, int N, int M, int c, double* out) {
     const long L = (long)N * N * M;
-    const int c = N / 2;
     for (int ln = 0; ln < M; ++ln)
         for (int jn = 0; jn < N; ++jn)
             for (int in = 0; in < N; ++in) {
@@ -57,6 +59,10 @@ void se2_direct_conv(const double* F, const double* P, int N, int M, double* out
                 }
                 out[idx3(ln, jn, in, N)] = acc / (double)L;
             }
+}
+
+void se2_direct_conv(const double* F, const double* P, int N, int M, double* out) {
+    se2_direct_conv_shift(F, P, N, M, N / 2, out);
 }
 
 /* Only the listed output points (flat indices into [M][N][N]). */

@@ -32,6 +32,7 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         lp = ctypes.POINTER(ctypes.c_long)
         lib.se2_direct_conv.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
+        lib.se2_direct_conv_shift.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
         lib.se2_direct_conv_points.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, lp, ctypes.c_long, dp]
         lib.se2_group_quadrature.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                              ctypes.c_int, dp]
@@ -43,15 +44,16 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def direct_conv(F: np.ndarray, P: np.ndarray) -> np.ndarray:
-    """out[n] = (1/|L|) sum_m F[m] P[n - m + (0, N/2, N/2)] (even N)."""
+def direct_conv(F: np.ndarray, P: np.ndarray, origin_zero: bool = False) -> np.ndarray:
+    """out[n] = (1/|L|) sum_m F[m] P[n - m + (0, c, c)] (even N), c = N/2 on
+    Omega_L and c = 0 for grids sampled at x_i = i/N."""
     lib = _load()
     M, N, N2 = F.shape
     assert N == N2 and N % 2 == 0 and P.shape == F.shape
     F = np.ascontiguousarray(F, dtype=np.float64)
     P = np.ascontiguousarray(P, dtype=np.float64)
     out = np.empty_like(F)
-    lib.se2_direct_conv(_ptr(F), _ptr(P), N, M, _ptr(out))
+    lib.se2_direct_conv_shift(_ptr(F), _ptr(P), N, M, 0 if origin_zero else N // 2, _ptr(out))
     return out
 
 

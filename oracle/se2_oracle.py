@@ -27,7 +27,7 @@ What it computes, with the passage of arXiv 2504.05149 each function follows:
   the paper; derived here: the transpose of iDFT(W.C.DFT(.)) is
   iDFT(W.conj(C).DFT(.)) for real arrays).
 
-Readings where the paper is silent (all written down in the design doc):
+Readings where the paper is silent:
 even grid sizes use the N = L closed form unchanged, W(k) = (-1)^(k1+k2) with
 k the signed frequency of the bin; the output is the real part.
 
@@ -144,18 +144,25 @@ def coeffs_separable(gx: np.ndarray, gy: np.ndarray, gt: np.ndarray) -> np.ndarr
     return ct[:, None, None] * cy[None, :, None] * cx[None, None, :]
 
 
-def convolve_complex(F: np.ndarray, P: np.ndarray, route: str = "fft") -> np.ndarray:
+def _weight(Nx: int, M: int, Ny: int, origin_zero: bool):
+    """W of Eq. W for grids on Omega_L (x_i = -1/2 + i/N); 1 for grids sampled
+    at x_i = i/N, where the rectangle rule is the plain cyclic convolution
+    (the -1/2 offset is what the half-period shift W undoes)."""
+    return 1.0 if origin_zero else weight_W(Nx, M, Ny)
+
+
+def convolve_complex(F: np.ndarray, P: np.ndarray, route: str = "fft", origin_zero: bool = False) -> np.ndarray:
     """Algorithm 3 at output grid N = L: (1/|L|) iDFT(W . DFT(F) . DFT(P))
     (closed form below Eq. MatSKfgonG), before taking the real part."""
     M, Ny, Nx = F.shape[-3:]
     L = M * Ny * Nx
-    H = weight_W(Nx, M, Ny) * dft3(F, route) * dft3(P, route)
+    H = _weight(Nx, M, Ny, origin_zero) * dft3(F, route) * dft3(P, route)
     return idft3(H, route) / L
 
 
-def convolve(F: np.ndarray, P: np.ndarray, route: str = "fft") -> np.ndarray:
+def convolve(F: np.ndarray, P: np.ndarray, route: str = "fft", origin_zero: bool = False) -> np.ndarray:
     """Re S_K[f, rho] on Omega_L (Algorithm 3; the paper plots the real part)."""
-    return convolve_complex(F, P, route).real
+    return convolve_complex(F, P, route, origin_zero).real
 
 
 def convolve_power(F: np.ndarray, P: np.ndarray, q: int, route: str = "fft") -> np.ndarray:
@@ -171,7 +178,7 @@ def convolve_power(F: np.ndarray, P: np.ndarray, q: int, route: str = "fft") -> 
     return (idft3(H, route) / float(L) ** q).real
 
 
-def convolve_chain(F: np.ndarray, Ps, route: str = "fft", coeffs=None) -> np.ndarray:
+def convolve_chain(F: np.ndarray, Ps, route: str = "fft", coeffs=None, origin_zero: bool = False) -> np.ndarray:
     """f * rho_1 * ... * rho_q for q radial kernels: iDFT(W^q . F^ . prod_i C_i)
     with C_i = DFT(P_i)/|L| (Eq. MatSqKfgG with the power replaced by the
     product of the coefficient arrays).  `coeffs` may pass the C_i directly."""
@@ -183,7 +190,7 @@ def convolve_chain(F: np.ndarray, Ps, route: str = "fft", coeffs=None) -> np.nda
     for C in coeffs:
         H = H * C
     if q % 2 == 1:
-        H = weight_W(Nx, M, Ny) * H
+        H = _weight(Nx, M, Ny, origin_zero) * H
     return idft3(H, route).real
 
 
@@ -204,7 +211,7 @@ def convolve_all(F: np.ndarray, Ps, route: str = "fft"):
     return outs
 
 
-def adjoint(G: np.ndarray, Ps, route: str = "fft", coeffs=None) -> np.ndarray:
+def adjoint(G: np.ndarray, Ps, route: str = "fft", coeffs=None, origin_zero: bool = False) -> np.ndarray:
     """Transpose of f -> convolve_chain(f, Ps) applied to G (the gradient of a
     loss with respect to f given its gradient G with respect to the output):
     iDFT(W^q . conj(prod_i C_i) . DFT(G)).  For q = 1 this is the discrete
@@ -216,7 +223,7 @@ def adjoint(G: np.ndarray, Ps, route: str = "fft", coeffs=None) -> np.ndarray:
     for C in coeffs:
         H = H * np.conj(C)
     if len(coeffs) % 2 == 1:
-        H = weight_W(Nx, M, Ny) * H
+        H = _weight(Nx, M, Ny, origin_zero) * H
     return idft3(H, route).real
 
 
@@ -241,8 +248,9 @@ def grad_kernel_samples(F: np.ndarray, G: np.ndarray, route: str = "fft") -> np.
 # Independent of synth/ (which only samples the values).
 # ---------------------------------------------------------------------------
 
-def _kernel_1d(N: int, M: int, sigma: float, sigma_t: float, nu: float = 0.0, images: int = 2, terms: int = 4):
-    x = -0.5 + np.arange(N) / N
+def _kernel_1d(N: int, M: int, sigma: float, sigma_t: float, nu: float = 0.0, images: int = 2, terms: int = 4,
+               origin_zero: bool = False):
+    x = (0.0 if origin_zero else -0.5) + np.arange(N) / N
     d = np.mod(x + 0.5, 1.0) - 0.5
     g = np.zeros(N)
     dg = np.zeros(N)
@@ -267,9 +275,11 @@ def _kernel_1d(N: int, M: int, sigma: float, sigma_t: float, nu: float = 0.0, im
     return g, dg, t, dt
 
 
-def kernel_samples_and_derivs(N: int, M: int, sigma: float, sigma_t: float, nu: float = 0.0):
-    """P, dP/dsigma, dP/dsigma_theta sampled on Omega_L, each [M][N][N]."""
-    g, dg, t, dt = _kernel_1d(N, M, sigma, sigma_t, nu)
+def kernel_samples_and_derivs(N: int, M: int, sigma: float, sigma_t: float, nu: float = 0.0,
+                              origin_zero: bool = False):
+    """P, dP/dsigma, dP/dsigma_theta sampled on Omega_L (or at x_i = i/N),
+    each [M][N][N]."""
+    g, dg, t, dt = _kernel_1d(N, M, sigma, sigma_t, nu, origin_zero=origin_zero)
     P = t[:, None, None] * g[None, :, None] * g[None, None, :]
     dPs = t[:, None, None] * (dg[None, :, None] * g[None, None, :] + g[None, :, None] * dg[None, None, :])
     dPt = dt[:, None, None] * g[None, :, None] * g[None, None, :]

@@ -94,9 +94,10 @@ class Problem:
     kernels: List[KernelParams] = field(default_factory=list)
 
 
-def grid_axes(N: int, M: int):
-    """The three axes of Omega_L for even N (0-based indices)."""
-    x = -0.5 + np.arange(N, dtype=np.float64) / N
+def grid_axes(N: int, M: int, origin_zero: bool = False):
+    """The three axes of Omega_L for even N (0-based indices); with
+    origin_zero the spatial axes are x_i = i/N instead of -1/2 + i/N."""
+    x = (0.0 if origin_zero else -0.5) + np.arange(N, dtype=np.float64) / N
     th = 2.0 * math.pi * np.arange(M, dtype=np.float64) / M
     return x, x.copy(), th
 
@@ -136,9 +137,9 @@ def _wrapped_normal(th: np.ndarray, nu: float, s: float, terms: int = 4) -> np.n
     return acc / (s * math.sqrt(2.0 * math.pi))
 
 
-def sample_bumps(N: int, M: int, bumps: Sequence[Bump]) -> np.ndarray:
-    """f1 sampled on Omega_L as float64 [M][N][N] (theta, y, x)."""
-    x, y, th = grid_axes(N, M)
+def sample_bumps(N: int, M: int, bumps: Sequence[Bump], origin_zero: bool = False) -> np.ndarray:
+    """f1 sampled on Omega_L (or at x_i = i/N) as float64 [M][N][N] (theta, y, x)."""
+    x, y, th = grid_axes(N, M, origin_zero)
     nb = len(bumps)
     X = np.empty((N, nb))
     Y = np.empty((N, nb))
@@ -152,18 +153,18 @@ def sample_bumps(N: int, M: int, bumps: Sequence[Bump]) -> np.ndarray:
     return (G @ X.T).reshape(M, N, N)
 
 
-def kernel_factors(N: int, M: int, k: KernelParams):
+def kernel_factors(N: int, M: int, k: KernelParams, origin_zero: bool = False):
     """The three 1-D factors of the sampled kernel: rho = kx (x) ky (x) kt."""
-    x, y, th = grid_axes(N, M)
+    x, y, th = grid_axes(N, M, origin_zero)
     s = k.sigma
     gx = _periodic_gauss_1d(x, 0.0, s) / (math.sqrt(2.0 * math.pi) * s)
     gt = 2.0 * math.pi * _wrapped_normal(th, k.nu, k.sigma_theta)
     return gx, gx.copy(), gt
 
 
-def sample_kernel(N: int, M: int, k: KernelParams) -> np.ndarray:
-    """Radial kernel f2 sampled on Omega_L as float64 [M][N][N]."""
-    gx, gy, gt = kernel_factors(N, M, k)
+def sample_kernel(N: int, M: int, k: KernelParams, origin_zero: bool = False) -> np.ndarray:
+    """Radial kernel f2 sampled on Omega_L (or at x_i = i/N) as float64 [M][N][N]."""
+    gx, gy, gt = kernel_factors(N, M, k, origin_zero)
     return gt[:, None, None] * gy[None, :, None] * gx[None, None, :]
 
 

@@ -318,3 +318,39 @@ def test_ffc_error_bound_deformed_gaussian_E2():
         errs.append(err)
     # and the error actually decays with K
     assert errs[-1] < 0.1 * errs[0]
+
+
+def test_origin_zero_is_the_plain_cyclic_convolution():
+    """Grids sampled at x_i = i/N: the scheme without W equals the direct
+    cyclic sum (1/|L|) sum_m F[m] P[n - m] (brute force, shift 0), on both
+    DFT routes."""
+    from oracle import direct
+    N, M = 16, 8
+    F = RNG.random((M, N, N))
+    P = RNG.random((M, N, N))
+    want = direct.direct_conv(F, P, origin_zero=True)
+    for route in ("fft", "matrix"):
+        got = O.convolve(F, P, route, origin_zero=True)
+        assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+    # and it is not the Omega_L result (W matters)
+    assert np.max(np.abs(O.convolve(F, P) - want)) > 1e-3 * np.max(np.abs(want))
+
+
+def test_origin_conventions_differ_by_a_half_period_shift():
+    """The same periodic bumps and kernel sampled on Omega_L and at x_i = i/N:
+    the Omega_L output (with W) is the origin-zero output (without W) shifted
+    by N/2 in x and y, and a 3-kernel chain equals three successive singles."""
+    N, M = 32, 16
+    prob = synth.make_problem(1, 7, N, M, n_bumps=3, n_kernels=3)
+    F1 = synth.sample_bumps(N, M, prob.bumps)
+    F0 = synth.sample_bumps(N, M, prob.bumps, origin_zero=True)
+    P1 = [synth.sample_kernel(N, M, k) for k in prob.kernels]
+    P0 = [synth.sample_kernel(N, M, k, origin_zero=True) for k in prob.kernels]
+    out1 = O.convolve(F1, P1[0])
+    out0 = O.convolve(F0, P0[0], origin_zero=True)
+    assert np.max(np.abs(out1 - np.roll(out0, (N // 2, N // 2), axis=(1, 2)))) < 1e-12 * np.max(np.abs(out1))
+    chain = O.convolve_chain(F0, P0, origin_zero=True)
+    seq = F0
+    for P in P0:
+        seq = O.convolve(seq, P, origin_zero=True)
+    assert np.max(np.abs(chain - seq)) < 1e-12 * np.max(np.abs(seq))
