@@ -68,6 +68,15 @@ typedef enum {
 /* Plan flags */
 #define SE2_SHARED_KERNEL 0x1u  /* one coefficient array serves the whole batch */
 #define SE2_PERSISTENT    0x2u  /* FP32: run se2_convolve(_chain) as one persistent dataflow kernel */
+/* Grids (f, kernel samples, output) sampled at x_i = i/N instead of on
+ * Omega_L (x_i = -1/2 + i/N, Eq. OmL), theta unchanged.  The rectangle rule of
+ * the convolution is then the plain cyclic convolution
+ *   out[n] = (1/|L|) sum_m F[m] P[n - m],
+ * i.e. the scheme without the weight W of Eq. W (which undoes the -1/2
+ * offset): convolutions, chains, separable chains and the adjoint drop W, and
+ * the kernel samplers (se2_sample_radial_gaussian, se2_separable_tables)
+ * sample at x_i = i/N.  se2_coeffs is unaffected (C = DFT(P)/|L| either way). */
+#define SE2_GRID_ORIGIN_ZERO 0x4u
 
 /*
  * se2_plan_create -- validate sizes, build FP64-accurate twiddle tables and

@@ -381,6 +381,7 @@ LArgs<T> yargs(se2_plan_s* p) {
     l.tw = (const c2<T>*)p->twN;
     l.cp = p->N / 2 + 1;
     l.inv_L = 1.0 / ((double)p->N * p->N * p->M);
+    l.wsign = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0 : 1;
     return l;
 }
 
@@ -475,6 +476,7 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
         a.c_pstride = cps;
         a.ls_pstride = lps;
         a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
+        a.wsign = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0 : 1;
         if (sep_tables != nullptr) {
             const long long tps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)(p->N / 2 + 1 + p->N + p->M);
             a.sep = sep_tables + c0 * tps;
@@ -582,6 +584,7 @@ se2_status run_backward_fast(se2_plan_s* p, const float* g, const float* f, int 
         a.twN = (const float2*)p->twN;
         a.twM = (const float2*)p->twM;
         a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
+        a.wsign = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0 : 1;
         float4* s0 = (float4*)p->scratch;
         float4* s1 = s0 + (size_t)nb * (p->s_pstride / 2);
         a.f = g + c0 * gs;
@@ -705,7 +708,8 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (batch < 1) return fail(SE2_ERR_INVALID_ARG, "batch=%d must be >= 1", batch);
     if (precision != SE2_F32 && precision != SE2_F64 && precision != SE2_SPLIT_BF16 && precision != SE2_BF16)
         return fail(SE2_ERR_UNSUPPORTED, "precision %d not supported", (int)precision);
-    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT)) return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT | SE2_GRID_ORIGIN_ZERO))
+        return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -940,7 +944,8 @@ se2_status se2_sample_radial_gaussian(se2_plan_t p, double sigma, double sigma_t
         return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
-    k_gauss_tables<<<(p->N + p->M + 127) / 128, 128, 0, s>>>(p->tab, p->N, p->M, sigma, sigma_theta, nu);
+    const double x0 = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0.0 : -0.5;
+    k_gauss_tables<<<(p->N + p->M + 127) / 128, 128, 0, s>>>(p->tab, p->N, p->M, sigma, sigma_theta, nu, x0);
     ++p->launches;
     const long long total = (long long)p->N * p->N * p->M;
     const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
@@ -965,10 +970,13 @@ se2_status se2_separable_tables(se2_plan_t p, const double* params, const int* k
     cudaStream_t s = (cudaStream_t)stream;
     const long long tps = (long long)(p->N / 2 + 1 + p->N + p->M);
     const size_t sm = sizeof(double) * 3 * ((size_t)p->N + p->M);
+    const bool oz = (p->flags & SE2_GRID_ORIGIN_ZERO) != 0;
+    const double x0 = oz ? 0.0 : -0.5;
+    const int wfold = oz ? 0 : 1;
     if (!is_f64(p))
-        k_sep_tables<float><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (float2*)tables, tps);
+        k_sep_tables<float><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (float2*)tables, tps, x0, wfold);
     else
-        k_sep_tables<double><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (double2*)tables, tps);
+        k_sep_tables<double><<<B, 128, sm, s>>>(params, k, kmax, p->N, p->M, (double2*)tables, tps, x0, wfold);
     ++p->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");

@@ -251,6 +251,7 @@ struct FArgs {
     const float2* dC[kMaxParams];
     double* grad_params;
     int want_grad;
+    int wsign;                   // 1: apply W (grids on Omega_L); 0: grids at x_i = i/N
 };
 
 // y-pass modes: the convolution / chain product, the separable product, the
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
         if (a.n_params > 0 && act && t < R1) {
             const bool hasb = u < Q;
             const int kxa = hasb ? u : N / 2;
-            const float sg = ((u + t) & 1) ? -1.f : 1.f;
+            const float sg = (a.wsign && ((u + t) & 1)) ? -1.f : 1.f;
             const float2 mw = pf(sg * ((u == 0 || u == Q) ? 1.f : 2.f), sg * 2.f);
             // F at this lane's bins, staged in the (now idle) exchange area
             const float4* fb2 = a.s2 + (size_t)b * a.s_pstride + (size_t)o * N * TP4 + u + (size_t)t * TP4;
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
         const bool hasb = u < Q;
         const int kxa = hasb ? u : N / 2;
         const float sc = (float)sh_scale;
-        const bool neg = (SEP || (a.k & 1)) && ((u + t) & 1);   // W^k at (kx, ky), both halves alike
+        const bool neg = a.wsign && (SEP || (a.k & 1)) && ((u + t) & 1);   // W^k at (kx, ky), both halves alike
         const float2 s2 = bc2(neg ? -sc : sc);
         if constexpr (SEP) {
             // C = (tx[kx] tt[m]) ty[ky]: the x and theta factors once per lane

@@ -230,6 +230,7 @@ struct LArgs {
     // tables [problem][(N/2+1) + N + M] complex (tx, ty, tt), W^(k-1) folded in
     const c2<T>* sep;
     long long sep_pstride;
+    int wsign;                 // 1: apply W (grids on Omega_L); 0: grids at x_i = i/N
 };
 
 // ---------------------------------------------------------------------------
@@ -504,7 +505,7 @@ __device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int 
                 const T cr = xr * cy[k].x - xi * cy[k].y, ci = xr * cy[k].y + xi * cy[k].x;
                 const T r = re[k] * cr - im[k] * ci;
                 const T i2 = re[k] * ci + im[k] * cr;
-                const bool neg = (kx + ky) & 1;                           // W
+                const bool neg = a.wsign && ((kx + ky) & 1);              // W
                 re[k] = neg ? -r * sc : r * sc;
                 im[k] = neg ? -i2 * sc : i2 * sc;
             }
@@ -556,7 +557,7 @@ __device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int 
 #pragma unroll
                 for (int k = 0; k < TO::regs; ++k) {
                     const int ky = TO::idx(t, k);
-                    const T w = ((kx + ky) & 1) ? (T)-1 : (T)1;
+                    const T w = (a.wsign && ((kx + ky) & 1)) ? (T)-1 : (T)1;
                     // Re(W dC conj(G^) F^)
                     const T pr = re[k] * fr[k] + im[k] * fi[k];
                     const T pi = re[k] * fi[k] - im[k] * fr[k];
@@ -573,7 +574,7 @@ __device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int 
 #pragma unroll
                 for (int k = 0; k < TO::regs; ++k) {
                     const int ky = TO::idx(t, k);
-                    const T w = ((kx + ky) & 1) ? (T)-1 : (T)1;
+                    const T w = (a.wsign && ((kx + ky) & 1)) ? (T)-1 : (T)1;
                     // W conj(C) G^ * scale
                     const T xr = (cv[k].x * re[k] + cv[k].y * im[k]) * sc * w;
                     const T xi = (cv[k].x * im[k] - cv[k].y * re[k]) * sc * w;
@@ -633,7 +634,7 @@ __device__ __forceinline__ void unit_lines(const LArgs<T>& a, c2<T>* sprob, int 
 #pragma unroll
             for (int k = 0; k < TO::regs; ++k) {
                 const int ky = TO::idx(t, k);
-                const bool neg = (a.k & 1) && ((kx + ky) & 1);           // W^k
+                const bool neg = a.wsign && (a.k & 1) && ((kx + ky) & 1);   // W^k
                 re[k] = neg ? -re[k] * sc : re[k] * sc;
                 im[k] = neg ? -im[k] * sc : im[k] * sc;
             }
@@ -692,11 +693,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_lines(LArg
 // Omega_L; plus the derivatives in sigma and sigma_t.  The 1-D factors are
 // computed in FP64 (tables: gx, dgx [N], gt, dgt [M]), then multiplied out.
 // ---------------------------------------------------------------------------
-static __global__ void k_gauss_tables(double* tab, int N, int M, double sigma, double sigma_t, double nu) {
+static __global__ void k_gauss_tables(double* tab, int N, int M, double sigma, double sigma_t, double nu,
+                                      double x0) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double PI = 3.14159265358979323846;
     if (i < N) {
-        const double d = -0.5 + (double)i / N;              // x_i, already in [-1/2, 1/2)
+        const double d = x0 + (double)i / N;                // x_i (x0 = -1/2 on Omega_L, 0 at origin zero)
         double g = 0, dg = 0;
         for (int n = -2; n <= 2; ++n) {
             const double u2 = (d + n) * (d + n);
@@ -730,7 +732,7 @@ static __global__ void k_gauss_tables(double* tab, int N, int M, double sigma, d
 // the convolution applies W once.  One block per problem.
 template <typename T>
 __global__ void k_sep_tables(const double* params, const int* kcount, int kmax, int N, int M,
-                             c2<T>* tab, long long tab_pstride) {
+                             c2<T>* tab, long long tab_pstride, double x0, int wfold) {
     const int b = blockIdx.x;
     const int k = kcount[b];
     const double PI = 3.14159265358979323846;
@@ -757,7 +759,7 @@ __global__ void k_sep_tables(const double* params, const int* kcount, int kmax, 
         __syncthreads();
         for (int i = threadIdx.x; i < N + M; i += blockDim.x) {
             if (i < N) {
-                const double d = -0.5 + (double)i / N;
+                const double d = x0 + (double)i / N;
                 double acc = 0;
                 for (int n = -2; n <= 2; ++n) acc += exp(-(d + n) * (d + n) / (2 * sigma * sigma));
                 g[i] = acc / (sqrt(2 * PI) * sigma);
@@ -799,7 +801,7 @@ __global__ void k_sep_tables(const double* params, const int* kcount, int kmax, 
         const int e = threadIdx.x + q * blockDim.x;
         if (e >= tot) break;
         double sgn = 1.0;
-        if (e < H + N && ((k - 1) & 1)) {
+        if (wfold && e < H + N && ((k - 1) & 1)) {
             const int kk = e < H ? e : e - H;
             if (kk & 1) sgn = -1.0;
         }

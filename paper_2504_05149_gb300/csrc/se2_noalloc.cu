@@ -168,6 +168,7 @@ extern "C" se2_status se2_convolve_noalloc(const void* f, const void* coeffs, vo
         yl.tw = twN;
         yl.cp = N / 2 + 1;
         yl.inv_L = 1.0 / ((double)N * N * M);
+        yl.wsign = 1;                      // grids on Omega_L
         yl.k = 1;
         yl.C[0] = (const float2*)coeffs + c0 * cps;
         yl.ls[0] = nullptr;

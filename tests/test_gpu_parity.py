@@ -321,6 +321,66 @@ def test_input_offset_by_one_float(se2):
         assert _rel(out[b], O.convolve(F[b].astype(float), P[b].astype(float))) < 1e-5
 
 
+_ORIGIN = r"""
+import numpy as np, torch, sys
+sys.path.insert(0, '.')
+import paper_2504_05149_gb300 as se2
+import synth
+from oracle import se2_oracle as O
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+for N, M, B, k in ((64, 16, 3, 1), (256, 64, 3, 2), (256, 64, 3, 3), (32, 8, 2, 1)):
+    plan = se2.Plan(N, M, batch=B, flags=se2.GRID_ORIGIN_ZERO)
+    Fs, Ps = [], []
+    for b in range(B):
+        prob = synth.make_problem(6, 10 * N + b, N, M, n_bumps=6, n_kernels=k)
+        Fs.append(synth.sample_bumps(N, M, prob.bumps, origin_zero=True).astype(np.float32))
+        Ps.append([synth.sample_kernel(N, M, kp, origin_zero=True).astype(np.float32) for kp in prob.kernels])
+    f = torch.from_numpy(np.stack(Fs)).cuda()
+    Cs = [se2.coeffs(plan, torch.from_numpy(np.stack([p[i] for p in Ps])).cuda())[0] for i in range(k)]
+    out = se2.convolve_chain(plan, f, Cs).double().cpu().numpy()
+    for b in range(B):
+        want = O.convolve_chain(Fs[b].astype(np.float64), [P.astype(np.float64) for P in Ps[b]], origin_zero=True)
+        assert rel(out[b], want) < 1e-5, (N, M, k, rel(out[b], want))
+# the adjoint without W
+N, M, B = 64, 16, 2
+plan = se2.Plan(N, M, batch=B, flags=se2.GRID_ORIGIN_ZERO | se2.SHARED_KERNEL)
+P, dPs, dPt = se2.sample_radial_gaussian(plan, 0.04, 0.3, derivs=True)
+wP, _, _ = O.kernel_samples_and_derivs(N, M, 0.04, 0.3, origin_zero=True)
+assert rel(P[0].double().cpu().numpy(), wP) < 1e-6
+C, _ = se2.coeffs(plan, P)
+G = np.random.default_rng(3).standard_normal((B, M, N, N)).astype(np.float32)
+gf, _ = se2.backward(plan, torch.from_numpy(G).cuda(), C)
+for b in range(B):
+    want = O.adjoint(G[b].astype(np.float64), [P[0].double().cpu().numpy()], origin_zero=True)
+    assert rel(gf[b].double().cpu().numpy(), want) < 1e-5
+# separable chain tables sampled at x_i = i/N, no W folded in
+N, M, B, k = 64, 32, 2, 3
+plan = se2.Plan(N, M, batch=B, flags=se2.GRID_ORIGIN_ZERO)
+rng = synth.SplitMix64(91)
+kernels = [synth.draw_kernel(rng) for _ in range(k)]
+params = torch.zeros((B, 16, 3), dtype=torch.float64)
+for j, kp in enumerate(kernels):
+    params[:, j] = torch.tensor([kp.sigma, kp.sigma_theta, kp.nu], dtype=torch.float64)
+tab = se2.separable_tables(plan, params.cuda(), torch.tensor([k] * B, dtype=torch.int32).cuda())
+F = np.stack([synth.sample_bumps(N, M, synth.make_problem(7, b, N, M, n_bumps=4).bumps, origin_zero=True)
+              for b in range(B)]).astype(np.float32)
+out = se2.convolve_separable(plan, torch.from_numpy(F).cuda(), tab).double().cpu().numpy()
+Ps = [synth.sample_kernel(N, M, kp, origin_zero=True) for kp in kernels]
+for b in range(B):
+    assert rel(out[b], O.convolve_chain(F[b].astype(np.float64), Ps, origin_zero=True)) < 1e-5
+print("ok")
+"""
+
+
+def test_grid_origin_zero_flag(se2):
+    """SE2_GRID_ORIGIN_ZERO: grids sampled at x_i = i/N, single convolutions
+    and chains without W, the sampler on that grid and the adjoint, on the fast
+    kernels and (SE2_FAST=0) on the generic ones."""
+    _sub({}, _ORIGIN)
+    _sub({"SE2_FAST": "0"}, _ORIGIN)
+
+
 def test_invalid_arguments_on_gpu_plan(se2):
     plan = se2.Plan(32, 16, batch=2)
     f = torch.zeros((3, 16, 32, 32), device="cuda")
