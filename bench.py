@@ -291,6 +291,35 @@ def main():
     _, e2e_val = aggregate(sorted(reps)[1], B * ke, world, reduce_max)
     assert np.isfinite(hout.numpy()).all()
 
+    # comparator (context only, not the product): the same convolution written
+    # with torch.fft (cuFFT) on the same batch: irfftn(W . rfftn(f) . C)
+    comp = None
+    if args.precision == "f32":
+        ky = torch.arange(N, device=dev)
+        kx = torch.arange(N // 2 + 1, device=dev)
+        W = torch.where(((ky[:, None] + kx[None, :]) % 2) == 1, -1.0, 1.0).to(torch.complex64)
+
+        def torch_fft_step():
+            H = torch.fft.rfftn(f, dim=(-3, -2, -1)) * C * W
+            return torch.fft.irfftn(H, s=(M, N, N), dim=(-3, -2, -1))
+
+        ref_out = torch_fft_step()
+        se2.convolve(plan, f, C, out=out)
+        torch.cuda.synchronize(dev)
+        agree = float((ref_out - out).abs().max() / ref_out.abs().max())
+        for _ in range(3):
+            torch_fft_step()
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        for _ in range(args.steps):
+            torch_fft_step()
+        e5.record(stream)
+        torch.cuda.synchronize(dev)
+        comp = {"torch_fft": {"value": B * args.steps / (e4.elapsed_time(e5) / 1e3), "unit": "conv/s",
+                              "what": "torch.fft.rfftn/irfftn (cuFFT) pipeline on the same batch, "
+                                      "a comparator for context, not the product",
+                              "max_rel_diff_vs_se2": agree}}
+
     hbm, src = peaks()
     alg_bytes = B * (4 * L + 4 * L + 8 * M * N * (N // 2 + 1))   # read f, write out, read half spectrum
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
@@ -315,6 +344,7 @@ def main():
             "e2e": {"value": e2e_val, "unit": "conv/s", "h2d_bytes_per_step": int(F.nbytes),
                     "d2h_bytes_per_step": int(F.nbytes)},
             "gpu_launches": launches_timed,
+            "comparators": comp,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
