@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--N", type=int, default=N_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c2chain", "c3", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c2chain", "c2all", "c3", "c4", "c5"],
                     help="c2: single convolutions at 256^2x64 (the headline); c2chain: 8-fold chains; "
+                         "c2all: 8-fold chains emitting every intermediate (Algorithm 6); "
                          "c4: 4096 uneven problems with separable chains (CUDA graph); c5: forward+adjoint")
     ap.add_argument("--problems", type=int, default=4096, help="c4 batch size")
     ap.add_argument("--precision", default="f32", choices=["f32", "split_bf16", "bf16"],
@@ -203,7 +204,8 @@ def main():
         return
     if args.config != "c2":
         from functools import partial
-        {"c2chain": run_chain8, "c3": run_precision, "c4": run_batch, "c5": run_adjoint}[args.config](args)
+        {"c2chain": run_chain8, "c2all": partial(run_chain8, emit_all=True), "c3": run_precision,
+         "c4": run_batch, "c5": run_adjoint}[args.config](args)
         return
     import torch
     import torch.distributed as dist
@@ -409,9 +411,10 @@ def _line(metric, value, unit, args, ms, cfg, extra):
     print(json.dumps(d), flush=True)
 
 
-def run_chain8(args):
+def run_chain8(args, emit_all=False):
     """8-fold chains f * rho_1 * ... * rho_8 at 256^2 x 64 (the chain's second
-    config), one chain of distinct kernels per problem."""
+    config), one chain of distinct kernels per problem; with emit_all every
+    intermediate V_1..V_8 (Algorithm 6) is written."""
     import torch
     import paper_2504_05149_gb300 as se2
     import synth
@@ -426,15 +429,24 @@ def run_chain8(args):
             Cs[i].append(torch.from_numpy(synth.sample_kernel(N, M, kp).astype(np.float32)))
     f = torch.stack(Fs).to(dev)
     C = [se2.coeffs(plan, torch.stack(c).to(dev))[0] for c in Cs]
-    out = torch.empty_like(f)
-    ms, clocks, launched = _clock_and_time(lambda: se2.convolve_chain(plan, f, C, out=out), args.steps, args.warmup,
-                                           dev, plans=(plan,))
     L = N * N * M
-    alg = B * (8 * L + k * 8 * M * N * (N // 2 + 1))
+    if emit_all:
+        out = torch.empty((k,) + tuple(f.shape), dtype=f.dtype, device=dev)
+        fn = lambda: se2.convolve_chain_all(plan, f, C, out=out)                  # noqa: E731
+        alg = B * (4 * L + k * (4 * L + 8 * M * N * (N // 2 + 1)))                # read f; per step read C_p, write V_p
+        metric, what = "8-fold SE(2) convolution chains/s with all 8 intermediates at N=256, M=64 (FP32)", \
+            f"se2_convolve_chain_all k=8 distinct kernels, V_1..V_8 written, batch {B}"
+    else:
+        out = torch.empty_like(f)
+        fn = lambda: se2.convolve_chain(plan, f, C, out=out)                      # noqa: E731
+        alg = B * (8 * L + k * 8 * M * N * (N // 2 + 1))
+        metric, what = "8-fold SE(2) convolution chains/s at N=256, M=64 (FP32)", \
+            f"se2_convolve_chain k=8 distinct kernels, batch {B}"
+    ms, clocks, launched = _clock_and_time(fn, args.steps, args.warmup, dev, plans=(plan,))
     hbm, src = peaks()
     ach = alg / (ms / args.steps / 1e3) / 1e9
-    _line("8-fold SE(2) convolution chains/s at N=256, M=64 (FP32)", B * args.steps / (ms / 1e3), "chain/s", args, ms,
-          {"workload": f"se2_convolve_chain k=8 distinct kernels, batch {B}", "grid": [M, N, N]},
+    _line(metric, B * args.steps / (ms / 1e3), "chain/s", args, ms,
+          {"workload": what, "grid": [M, N, N]},
           {"roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "traffic": None, "peak_source": src, "alg_bytes_per_chain": alg / B},
            "gpu_launches": launched, "clocks": clocks})

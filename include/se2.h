@@ -140,6 +140,18 @@ se2_status se2_convolve_chain(se2_plan_t plan, const void* f, int B,
                               int k, void* out, void* stream);
 
 /*
+ * se2_convolve_chain_all -- every intermediate result of a chain (Algorithm 6,
+ * the fast recursion): V_p = f * rho_1 * ... * rho_p for p = 1..k from one
+ * forward transform, V_p = iDFT(W^p . DFT(f) . C_1 ... C_p) exp(ls_1 + ... + ls_p).
+ * Arguments as se2_convolve_chain; out is [k][B][M][N][N] (V_p at p - 1).
+ * FP32 plans with N in {32, 64, 128, 256} only (SE2_ERR_UNSUPPORTED
+ * otherwise); B must fit half the plan's scratch slots (the running product
+ * and its inverse y transform live side by side), larger B runs in groups.
+ */
+se2_status se2_convolve_chain_all(se2_plan_t plan, const void* f, int B, const void* const* coeffs,
+                                  const double* const* log_scales, int k, void* out, void* stream);
+
+/*
  * se2_backward -- adjoint of se2_convolve (not in the paper; derived from it):
  * for a loss with gradient G_b = dLoss/dout_b of out_b = iDFT(W . DFT(F_b) . C_b)
  * * exp(ls_b),

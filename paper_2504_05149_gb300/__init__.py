@@ -58,6 +58,7 @@ def load_library(path: str = LIB_PATH):
     lib.se2_coeffs.argtypes = [vp, vp, ip, vp, vp, vp]
     lib.se2_convolve.argtypes = [vp, vp, ip, vp, vp, vp, vp]
     lib.se2_convolve_host.argtypes = [vp, vp, ip, vp, vp, vp, vp]
+    lib.se2_convolve_chain_all.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp, vp]
     lib.se2_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp, vp]
     lib.se2_plan_status.argtypes = [vp, vp]
     lib.se2_separable_tables.argtypes = [vp, vp, vp, ip, ip, vp, vp]
@@ -70,7 +71,7 @@ def load_library(path: str = LIB_PATH):
     lib.se2_last_error.restype = ctypes.c_char_p
     lib.se2_version.restype = ctypes.c_char_p
     for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_host",
-                 "se2_convolve_chain",
+                 "se2_convolve_chain", "se2_convolve_chain_all",
                  "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
                  "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
@@ -227,6 +228,28 @@ def convolve_chain(plan: Plan, f: torch.Tensor, Cs: Sequence[torch.Tensor],
     return out
 
 
+def convolve_chain_all(plan: Plan, f: torch.Tensor, Cs: Sequence[torch.Tensor],
+                       log_scales: Optional[Sequence[Optional[torch.Tensor]]] = None,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Every intermediate V_p = f * rho_1 * ... * rho_p, p = 1..k (Algorithm 6),
+    from one forward transform: returns [k, B, M, N, N]."""
+    B = plan._check_grid(f, "f")
+    k = len(Cs)
+    if out is None:
+        out = torch.empty((k,) + tuple(f.shape), dtype=f.dtype, device=f.device)
+    elif tuple(out.shape) != (k,) + tuple(f.shape) or out.dtype != f.dtype or not out.is_contiguous():
+        raise ValueError("out: need a contiguous tensor [k, B, M, N, N] like f")
+    Cs = [plan._check_spec(C, f"coeffs[{i}]", B) for i, C in enumerate(Cs)]
+    cp = (ctypes.c_void_p * k)(*[C.data_ptr() for C in Cs])
+    lp = None
+    if log_scales is not None:
+        if len(log_scales) != k:
+            raise ValueError("log_scales must have one entry per kernel")
+        lp = (ctypes.c_void_p * k)(*[0 if ls is None else ls.data_ptr() for ls in log_scales])
+    _check(load_library().se2_convolve_chain_all(plan.handle, _ptr(f), B, cp, lp, k, _ptr(out), _stream(f.device)))
+    return out
+
+
 def backward(plan: Plan, grad_out: torch.Tensor, C: torch.Tensor, f: Optional[torch.Tensor] = None,
              dCs: Sequence[torch.Tensor] = (), log_scale: Optional[torch.Tensor] = None,
              want_grad_f: bool = True):
@@ -325,7 +348,8 @@ class SE2Conv(torch.autograd.Function):
         return gf, gp.to(ctx.params_device, ctx.params_dtype), None
 
 
-__all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_chain", "backward",
+__all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_chain", "convolve_chain_all",
+           "backward",
            "sample_radial_gaussian",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
            "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO"]

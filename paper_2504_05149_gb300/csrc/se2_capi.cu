@@ -214,6 +214,8 @@ se2_status plan_init(se2_plan_s* p) {
                 r = cudaFuncSetAttribute((const void*)p->ft.lines_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
             if (r == cudaSuccess)
                 r = cudaFuncSetAttribute((const void*)p->ft.lines_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute((const void*)p->ft.lines_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
             if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
             p->fast = true;
         }
@@ -905,6 +907,71 @@ se2_status se2_convolve_host(se2_plan_t p, const void* f, int B, const void* coe
     }
     for (int k = 0; k < kHostBufs && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s, p->hev_out[k], 0);
     if (e != cudaSuccess) return cuda_fail(e, "host staging join");
+    return SE2_OK;
+}
+
+se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void* const* coeffs,
+                                  const double* const* log_scales, int k, void* out, void* stream) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    if (f == nullptr || out == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (B < 1 || B > p->batch) return fail(SE2_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, p->batch);
+    if (k < 1 || k > kMaxChain) return fail(SE2_ERR_INVALID_ARG, "chain length k=%d outside [1, %d]", k, kMaxChain);
+    if (!p->fast) return fail(SE2_ERR_UNSUPPORTED, "the emit-all chain needs an FP32 plan with N in {32..256}");
+    if (!aligned(f, 4) || !aligned(out, 4)) return fail(SE2_ERR_INVALID_ARG, "misaligned f/out");
+    for (int i = 0; i < k; ++i) {
+        if (coeffs[i] == nullptr) return fail(SE2_ERR_INVALID_ARG, "coeffs[%d] is NULL", i);
+        if (!aligned(coeffs[i], p->elem)) return fail(SE2_ERR_INVALID_ARG, "coeffs[%d] misaligned", i);
+        if (log_scales && log_scales[i] && !aligned(log_scales[i], 8)) return fail(SE2_ERR_INVALID_ARG, "log_scales[%d] misaligned", i);
+    }
+    const size_t gs = (size_t)p->N * p->N * p->M;
+    const uintptr_t fa = (uintptr_t)f, oa = (uintptr_t)out;
+    if (fa < oa + gs * 4 * (size_t)k * B && oa < fa + gs * 4 * (size_t)B) return fail(SE2_ERR_INVALID_ARG, "out overlaps f");
+    DeviceGuard guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const FastTable& ft = p->ft;
+    const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
+    const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
+    const long long pairs = (long long)p->M * (p->N / 4 + 1);
+    const unsigned yb = (unsigned)((pairs + ft.lines_per_block - 1) / ft.lines_per_block);
+    const int per_pass = p->nslots / 2;
+    for (int c0 = 0; c0 < B; c0 += per_pass) {
+        const int nb = (B - c0 < per_pass) ? (B - c0) : per_pass;
+        FArgs a{};
+        a.s_pstride = (long long)(p->s_pstride / 2);
+        a.twN = (const float2*)p->twN;
+        a.twM = (const float2*)p->twM;
+        a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
+        a.wsign = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0 : 1;
+        a.k = k;
+        a.c_pstride = cps;
+        a.ls_pstride = lps;
+        for (int i = 0; i < k; ++i) {
+            a.C[i] = (const float2*)coeffs[i] + c0 * cps;
+            a.ls[i] = (log_scales && log_scales[i]) ? log_scales[i] + c0 * lps : nullptr;
+        }
+        float4* s0 = (float4*)p->scratch;
+        float4* s1 = s0 + (size_t)nb * (p->s_pstride / 2);
+        a.f = (const float*)f + c0 * gs;
+        a.s = s0;
+        a.sout = s1;
+        ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);       // x, theta
+        ++p->launches;
+        ft.lines_fwd<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);     // y: the full spectrum of f
+        ++p->launches;
+        for (int q = 1; q <= k; ++q) {
+            a.p = q;
+            ft.lines_acc<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);   // R_q = R_{q-1} C_q; iDFT_y -> s1
+            ++p->launches;
+            FArgs c = a;
+            c.s = s1;
+            c.out = (float*)out + ((size_t)(q - 1) * B + c0) * gs;
+            ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(c);
+            ++p->launches;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SE2_OK;
 }
 

@@ -18,6 +18,7 @@ bool fill_fast_nm(FastTable* t) {
         t->lines_sep = kf_lines<N, M, FL_SEP>;
         t->lines_fwd = kf_lines<N, M, FL_FWD>;
         t->lines_adj = kf_lines<N, M, FL_ADJ>;
+        t->lines_acc = kf_lines<N, M, FL_ACC>;
         t->inv = kf_inv_tx<N, M>;
         t->smem_xt = sx;
         t->smem_y = sy;

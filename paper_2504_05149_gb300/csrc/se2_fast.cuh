@@ -252,11 +252,16 @@ struct FArgs {
     double* grad_params;
     int want_grad;
     int wsign;                   // 1: apply W (grids on Omega_L); 0: grids at x_i = i/N
+    // running-product y pass (kf_lines<.., FL_ACC>): s holds the full spectrum
+    // product R_{p-1} in ky order; R_p = R_{p-1} C_p is stored back and the
+    // inverse y FFT of W^p R_p exp(sum_{i<=p} ls_i) / |L| goes to sout
+    float4* sout;
+    int p;                       // 1-based index of C_p in C[] (chain step)
 };
 
 // y-pass modes: the convolution / chain product, the separable product, the
 // forward y FFT only (in place), the adjoint (correlation + parameter partials)
-enum FastLineMode { FL_CONV = 0, FL_SEP = 1, FL_FWD = 2, FL_ADJ = 3 };
+enum FastLineMode { FL_CONV = 0, FL_SEP = 1, FL_FWD = 2, FL_ADJ = 3, FL_ACC = 4 };
 
 // Step-A twiddle table of the team FFT of length L = R1 * R2 (layout of
 // team_fft2) from the forward table src of length L.
@@ -451,7 +456,16 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     float2 re[RM], im[RM];
 #pragma unroll
     for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
-    if (act && t < R2) {
+    if constexpr (MODE == FL_ACC) {
+        if (act && t < R1) {
+#pragma unroll
+            for (int k = 0; k < R2; ++k) {
+                const float4 v = __ldcg(base + (size_t)(R1 * k) * TP4);
+                re[k] = pf(v.x, v.y);
+                im[k] = pf(v.z, v.w);
+            }
+        }
+    } else if (act && t < R2) {
 #pragma unroll
         for (int jj = 0; jj < R1; ++jj) {
             const float4 v = __ldcg(base + (size_t)(R2 * jj) * TP4);
@@ -467,12 +481,13 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
         if (tid == 0) sh_scale = 0.5 * a.inv_L;
     } else if (tid == 0) {
         double lsum = 0;
-        for (int i = 0; i < a.k; ++i)
+        const int upto = MODE == FL_ACC ? a.p : a.k;
+        for (int i = 0; i < upto; ++i)
             if (a.ls[i] != nullptr) lsum += a.ls[i][b * a.ls_pstride];
         sh_scale = 0.5 * a.inv_L * exp(lsum);
     }
     __syncthreads();
-    team_fft2<R1, R2, -1>(re, im, t, act, xb, TWF, SyncBlock());
+    if constexpr (MODE != FL_ACC) team_fft2<R1, R2, -1>(re, im, t, act, xb, TWF, SyncBlock());
     // lane s < R1 holds ky = s + R1 k, k < R2
     if constexpr (MODE == FL_FWD) {
         if (act && t < R1) {
@@ -552,7 +567,8 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
         const bool hasb = u < Q;
         const int kxa = hasb ? u : N / 2;
         const float sc = (float)sh_scale;
-        const bool neg = a.wsign && (SEP || (a.k & 1)) && ((u + t) & 1);   // W^k at (kx, ky), both halves alike
+        const int kpar = MODE == FL_ACC ? a.p : a.k;
+        const bool neg = a.wsign && (SEP || (kpar & 1)) && ((u + t) & 1);   // W^k at (kx, ky), both halves alike
         const float2 s2 = bc2(neg ? -sc : sc);
         if constexpr (SEP) {
             // C = (tx[kx] tt[m]) ty[ky]: the x and theta factors once per lane
@@ -572,7 +588,8 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
         }
         // coefficient loads in chunks of CK bins (the adjoint keeps fewer in flight)
         constexpr int CK = MODE == FL_ADJ ? R2 / 2 : R2;
-        for (int i = 0; i < (SEP ? 0 : a.k); ++i) {
+        const int i0 = MODE == FL_ACC ? a.p - 1 : 0, i1 = SEP ? 0 : (MODE == FL_ACC ? a.p : a.k);
+        for (int i = i0; i < i1; ++i) {
             const float2* cb = a.C[i] + (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa + (size_t)t * CP;
 #pragma unroll
             for (int k0 = 0; k0 < R2; k0 += CK) {
@@ -595,6 +612,11 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
                 if (CK < R2) asm volatile("" ::: "memory");
             }
         }
+        if constexpr (MODE == FL_ACC) {   // keep the running product R_p (unscaled, no W)
+#pragma unroll
+            for (int k = 0; k < R2; ++k)
+                __stcg(base + (size_t)(R1 * k) * TP4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y));
+        }
 #pragma unroll
         for (int k = 0; k < R2; ++k) {
             re[k] = pmul(re[k], s2);
@@ -603,9 +625,10 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     }
     team_fft2<R2, R1, +1>(re, im, t, act, xb, TWI, SyncBlock());
     if (act && t < R2) {
+        float4* dst = MODE == FL_ACC ? a.sout + (base - a.s) : base;
 #pragma unroll
         for (int k = 0; k < R1; ++k)
-            __stcg(base + (size_t)(R2 * k) * TP4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y));
+            __stcg(dst + (size_t)(R2 * k) * TP4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y));
     }
 }
 

@@ -56,7 +56,8 @@ bool get_kernels(int N, int M, KTable<T>* kt) {
 // M in {8, ..., 128}.
 struct FastTable {
     using FK = void (*)(FArgs);
-    FK fwd = nullptr, lines = nullptr, lines_sep = nullptr, lines_fwd = nullptr, lines_adj = nullptr, inv = nullptr;
+    FK fwd = nullptr, lines = nullptr, lines_sep = nullptr, lines_fwd = nullptr, lines_adj = nullptr, lines_acc = nullptr,
+       inv = nullptr;
     size_t smem_xt = 0, smem_y = 0;
     int lines_per_block = 0;
 };

@@ -381,6 +381,31 @@ def test_grid_origin_zero_flag(se2):
     _sub({"SE2_FAST": "0"}, _ORIGIN)
 
 
+@pytest.mark.parametrize("N,M,B,k,normalize", [(64, 16, 3, 4, False), (256, 64, 2, 3, True), (32, 8, 5, 2, False)])
+def test_chain_emit_all_intermediates(se2, N, M, B, k, normalize):
+    """se2_convolve_chain_all: V_1..V_k of Algorithm 6 from one forward
+    transform, against the oracle's fast recursion (with FP64 log scales in
+    one case); B = 5 at 32^2 x 8 runs through scratch groups."""
+    Fs, Ps = [], []
+    for b in range(B):
+        prob = synth.make_problem(8, 100 * N + b, N, M, n_bumps=6, n_kernels=k)
+        Fs.append(synth.sample_bumps(N, M, prob.bumps).astype(np.float32).astype(np.float64))
+        Ps.append([(synth.sample_kernel(N, M, kp) * (10.0 ** i if normalize else 1.0)).astype(np.float32).astype(np.float64)
+                   for i, kp in enumerate(prob.kernels)])
+    plan = se2.Plan(N, M, batch=B)
+    Cs, Ls = [], []
+    for i in range(k):
+        C, ls = se2.coeffs(plan, _dev(np.stack([p[i] for p in Ps]), "f32"), normalize=normalize)
+        Cs.append(C)
+        Ls.append(ls)
+    out = se2.convolve_chain_all(plan, _dev(np.stack(Fs), "f32"), Cs, Ls if normalize else None)
+    out = out.double().cpu().numpy()
+    for b in range(B):
+        want = O.convolve_all(Fs[b], Ps[b])
+        for p in range(k):
+            assert _rel(out[p, b], want[p]) < 1e-5, (b, p)
+
+
 def test_invalid_arguments_on_gpu_plan(se2):
     plan = se2.Plan(32, 16, batch=2)
     f = torch.zeros((3, 16, 32, 32), device="cuda")
