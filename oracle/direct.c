@@ -26,6 +26,8 @@
  *      params = {sigma, sigma_t, nu}
  *   1: anisotropic Gaussian (s1 along x, s2 along y) * 2pi * wrapped normal;
  *      params = {s1, s2, sigma_t, nu}  -- NOT radial
+ *   2: the SE(2) Gaussian via the matrix logarithm (Eq. gbS0), shifted by nu
+ *      in the rotations; radial in translations; params = {sigma^2, nu}
  */
 #include <math.h>
 #include <stddef.h>
@@ -110,6 +112,19 @@ static double kernel_eval(int kind, const double* p, double vx, double vy, doubl
         const double s = p[0];
         const double g = exp(-(vx * vx + vy * vy) / (2.0 * s * s)) / (2.0 * M_PI * s * s);
         return g * 2.0 * M_PI * wrapped_normal(t - p[2], p[1]);
+    } else if (kind == 2) {
+        /* rho of Eq. gbS0 shifted by p[1] in the rotations, variance p[0]:
+         * exp(-(|v|^2 + phi^2) / (2 sigma^2)) with (v, phi) = log(x, R_phi)^v.
+         * Half-angle form: V(phi) = (2 sin(phi/2)/phi) R_{phi/2}, so
+         * |v| = |x| (phi/2) / sin(phi/2). */
+        double phi = fmod(t - p[1] + M_PI, 2.0 * M_PI);
+        if (phi < 0) phi += 2.0 * M_PI;
+        phi -= M_PI;
+        if (phi == -M_PI) phi = M_PI;
+        const double h = 0.5 * phi;
+        const double a = (h == 0.0) ? 1.0 : h / sin(h);
+        const double r2 = a * a * (vx * vx + vy * vy);
+        return exp(-(r2 + phi * phi) / (2.0 * p[0]));
     } else {
         const double s1 = p[0], s2 = p[1];
         const double g = exp(-vx * vx / (2.0 * s1 * s1) - vy * vy / (2.0 * s2 * s2)) /
