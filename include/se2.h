@@ -188,6 +188,38 @@ se2_status se2_sample_radial_gaussian(se2_plan_t plan, double sigma, double sigm
                                       void* P, void* dP_dsigma, void* dP_dsigma_theta, void* stream);
 
 /*
+ * se2_sample_se2_gaussian -- the Gaussian on SE(2) with mean beta and
+ * covariance Sigma (Section 5, Eq. fbS):
+ *   f(g) = exp(-1/2 w^T Sigma^-1 w),  w = log(beta^-1 o g)^v = (v1, v2, phi),
+ * with log the principal matrix logarithm of the matrices of Eq. gxyt (phi in
+ * (-pi, pi]; +pi at the branch point) and ^v the identification se(2) -> R^3.
+ * The kernel rho of Eq. gbS0 shifted by nu in the rotations (the paper's chain
+ * experiments) is beta = {0, 0, nu}, Sigma = sigma^2 I.
+ *   beta:   host, 3 doubles {b1, b2, nu}: beta = (b, R_nu).
+ *   Sigma:  host, 9 doubles, row major, symmetric positive definite.
+ *   images: 0..8; the samples sum the left translates by lattice vectors
+ *           |n1|, |n2| <= images (0 samples the function on the grid as it is).
+ *   P:      device, [M][N][N] of the plan's real type, on the plan's grid
+ *           (Omega_L, or x_i = i/N with SE2_GRID_ORIGIN_ZERO).
+ * Evaluated in FP64, rounded once.  Errors: SE2_ERR_INVALID_ARG for NULL or
+ * misaligned pointers, a Sigma that is not symmetric positive definite, or
+ * images out of range.
+ */
+se2_status se2_sample_se2_gaussian(se2_plan_t plan, const double* beta, const double* Sigma, int images, void* P,
+                                   void* stream);
+
+/*
+ * se2_sample_deformed_gaussian -- the 3D deformed Gaussian of Eq. fHsnu,
+ *   f(x, R_theta) = exp(-x^T H x) exp(-(theta - nu)^2 / s),
+ * with theta the grid angle 2 pi l / M in [0, 2 pi) as printed (no wrapping).
+ *   H: host, 4 doubles, row major 2x2; only its symmetric part enters and it
+ *      must be positive definite.  s > 0.
+ *   images, P, errors: as se2_sample_se2_gaussian.
+ */
+se2_status se2_sample_deformed_gaussian(se2_plan_t plan, const double* H, double nu, double s, int images, void* P,
+                                        void* stream);
+
+/*
  * se2_separable_tables -- coefficients of a chain of separable radial kernels
  * in factored form.  The kernel family of se2_sample_radial_gaussian is a
  * product of 1-D factors, so its C = DFT(P)/|L| is tt (x) ty (x) tx, and the

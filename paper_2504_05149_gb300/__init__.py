@@ -65,6 +65,9 @@ def load_library(path: str = LIB_PATH):
     lib.se2_convolve_separable.argtypes = [vp, vp, ip, vp, vp, vp]
     lib.se2_backward.argtypes = [vp, vp, vp, ip, vp, vp, ip, ctypes.POINTER(vp), vp, vp, vp]
     lib.se2_sample_radial_gaussian.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
+    dptr = ctypes.POINTER(ctypes.c_double)
+    lib.se2_sample_se2_gaussian.argtypes = [vp, dptr, dptr, ctypes.c_int, vp, vp]
+    lib.se2_sample_deformed_gaussian.argtypes = [vp, dptr, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
     lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
     lib.se2_plan_launches.argtypes = [vp]
     lib.se2_plan_launches.restype = ctypes.c_ulonglong
@@ -73,6 +76,7 @@ def load_library(path: str = LIB_PATH):
     for name in ("se2_plan_create", "se2_plan_destroy", "se2_coeffs", "se2_convolve", "se2_convolve_host",
                  "se2_convolve_chain", "se2_convolve_chain_all",
                  "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
+                 "se2_sample_se2_gaussian", "se2_sample_deformed_gaussian",
                  "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -284,6 +288,42 @@ def sample_radial_gaussian(plan: Plan, sigma: float, sigma_theta: float, nu: flo
     return (P, dPs, dPt) if derivs else P
 
 
+def _host_doubles(vals, n: int, name: str):
+    if len(vals) != n:
+        raise ValueError(f"{name} needs {n} values")
+    return (ctypes.c_double * n)(*[float(v) for v in vals])
+
+
+def sample_se2_gaussian(plan: Plan, beta=(0.0, 0.0, 0.0), Sigma=None, sigma2: float | None = None,
+                        images: int = 1):
+    """The Gaussian on SE(2) (Eq. fbS) with mean beta = (b1, b2, nu) and
+    covariance Sigma (3x3), or Sigma = sigma2 * I (the kernel of Eq. gbS0
+    shifted by nu), sampled on the plan's grid ([1, M, N, N])."""
+    if (Sigma is None) == (sigma2 is None):
+        raise ValueError("give exactly one of Sigma and sigma2")
+    if Sigma is None:
+        S = [float(sigma2) if r == c else 0.0 for r in range(3) for c in range(3)]
+    else:
+        S = [float(v) for row in Sigma for v in row]
+    dev = torch.device("cuda", plan.device)
+    P = torch.empty(plan.grid_shape(1), dtype=plan.dtype, device=dev)
+    _check(load_library().se2_sample_se2_gaussian(plan.handle, _host_doubles(list(beta), 3, "beta"),
+                                                  _host_doubles(S, 9, "Sigma"), int(images), _ptr(P),
+                                                  _stream(dev)))
+    return P
+
+
+def sample_deformed_gaussian(plan: Plan, H, nu: float, s: float, images: int = 1):
+    """The 3D deformed Gaussian exp(-x^T H x) exp(-(theta - nu)^2 / s)
+    (Eq. fHsnu) on the plan's grid ([1, M, N, N])."""
+    Hs = [float(v) for row in H for v in row]
+    dev = torch.device("cuda", plan.device)
+    P = torch.empty(plan.grid_shape(1), dtype=plan.dtype, device=dev)
+    _check(load_library().se2_sample_deformed_gaussian(plan.handle, _host_doubles(Hs, 4, "H"), float(nu), float(s),
+                                                       int(images), _ptr(P), _stream(dev)))
+    return P
+
+
 def table_len(plan: Plan) -> int:
     return plan.N // 2 + 1 + plan.N + plan.M
 
@@ -350,6 +390,6 @@ class SE2Conv(torch.autograd.Function):
 
 __all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_chain", "convolve_chain_all",
            "backward",
-           "sample_radial_gaussian",
+           "sample_radial_gaussian", "sample_se2_gaussian", "sample_deformed_gaussian",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
            "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO"]

@@ -824,6 +824,88 @@ __global__ void k_gauss_fill(const double* tab, int N, int M, T* P, T* dPs, T* d
 }
 
 // ---------------------------------------------------------------------------
+// Analytic inputs of the paper's experiments, sampled in FP64 on the plan's
+// grid: the Gaussian on SE(2) (Section 5, Eq. fbS; Eq. gbS0 is the case
+// beta = (0, R_nu), Sigma = sigma^2 I) and the 3D deformed Gaussian (Eq. fHsnu).
+// Both sum the left translates by lattice vectors |n1|, |n2| <= images, which
+// makes them functions on Z^2\SE(2).
+// ---------------------------------------------------------------------------
+struct GaussSE2Args {
+    int N, M, images;
+    double x0;          // first grid coordinate: -1/2 on Omega_L, 0 at x_i = i/N
+    double b1, b2;      // translation of the mean beta
+    double nu_turns;    // rotation of the mean beta, in turns (nu / 2 pi)
+    double q11, q12, q13, q22, q23, q33;  // Sigma^-1 (symmetric)
+};
+
+// f(g) = exp(-w^T Sigma^-1 w / 2) with w = log(beta^-1 o g)^v = (v, phi).
+// beta^-1 o (x, R_theta) = (R_-nu (x - b), R_(theta - nu)); phi is the angle of
+// R_(theta - nu) in (-pi, pi].  V(phi) = int_0^1 exp(t phi J) dt equals
+// (2 sin(phi/2) / phi) R_(phi/2), so v = V(phi)^-1 R_-nu (x - b)
+// = ((phi/2) / sin(phi/2)) R_-(nu + phi/2) (x - b).
+template <typename T>
+__global__ void k_se2_gauss_fill(GaussSE2Args a, T* P) {
+    const long long total = (long long)a.M * a.N * a.N;
+    const double inv_n = 1.0 / a.N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % a.N), j = (int)((e / a.N) % a.N), l = (int)(e / ((long long)a.N * a.N));
+        // angle of theta_l - nu in turns, reduced to (-1/2, 1/2]
+        double t = (double)l / a.M - a.nu_turns;
+        t -= rint(t);
+        if (t == -0.5) t = 0.5;
+        const double PI = 3.14159265358979323846;
+        const double phi = 2.0 * PI * t;
+        const double ah = (t == 0.0) ? 1.0 : (PI * t) / sinpi(t);  // (phi/2)/sin(phi/2)
+        double sr, cr;
+        sincospi(2.0 * a.nu_turns + t, &sr, &cr);  // rotation by nu + phi/2
+        const double px = a.x0 + i * inv_n - a.b1, py = a.x0 + j * inv_n - a.b2;
+        double acc = 0.0;
+        for (int n2 = -a.images; n2 <= a.images; ++n2) {
+            for (int n1 = -a.images; n1 <= a.images; ++n1) {
+                const double d1 = px + n1, d2 = py + n2;
+                const double v1 = ah * (cr * d1 + sr * d2);
+                const double v2 = ah * (-sr * d1 + cr * d2);
+                const double q = a.q11 * v1 * v1 + a.q22 * v2 * v2 + a.q33 * phi * phi +
+                                 2.0 * (a.q12 * v1 * v2 + a.q13 * v1 * phi + a.q23 * v2 * phi);
+                acc += exp(-0.5 * q);
+            }
+        }
+        P[e] = (T)acc;
+    }
+}
+
+struct DeformedArgs {
+    int N, M, images;
+    double x0, nu, s;
+    double h11, h12, h22;  // symmetric part of H
+};
+
+// f(x, R_theta) = exp(-x^T H x) exp(-(theta - nu)^2 / s), theta = 2 pi l / M
+// taken as it is (no wrapping), as Eq. fHsnu is printed.
+template <typename T>
+__global__ void k_deformed_fill(DeformedArgs a, T* P) {
+    const long long total = (long long)a.M * a.N * a.N;
+    const double inv_n = 1.0 / a.N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % a.N), j = (int)((e / a.N) % a.N), l = (int)(e / ((long long)a.N * a.N));
+        const double PI = 3.14159265358979323846;
+        const double dt = 2.0 * PI * l / a.M - a.nu;
+        const double ang = exp(-dt * dt / a.s);
+        const double px = a.x0 + i * inv_n, py = a.x0 + j * inv_n;
+        double acc = 0.0;
+        for (int n2 = -a.images; n2 <= a.images; ++n2) {
+            for (int n1 = -a.images; n1 <= a.images; ++n1) {
+                const double u1 = px + n1, u2 = py + n2;
+                acc += exp(-(a.h11 * u1 * u1 + 2.0 * a.h12 * u1 * u2 + a.h22 * u2 * u2));
+            }
+        }
+        P[e] = (T)(ang * acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Split path: x only (forward real FFT of packed theta-row pairs), runtime M.
 // grid = (N rows y, ceil(M/2 / TEAMS), problems)
 // ---------------------------------------------------------------------------

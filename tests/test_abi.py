@@ -65,3 +65,15 @@ def test_null_plan_and_null_pointers_rejected(lib):
     assert lib.se2_plan_create(None, 32, 16, 1, 1, 0, 0) == 1
     lib.se2_plan_destroy.argtypes = [vp]
     assert lib.se2_plan_destroy(None) == 0
+
+
+def test_samplers_reject_null_plan_on_host(lib):
+    vp = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.se2_sample_se2_gaussian.argtypes = [vp, dp, dp, ctypes.c_int, vp, vp]
+    lib.se2_sample_deformed_gaussian.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
+    beta = (ctypes.c_double * 3)(0, 0, 0)
+    S = (ctypes.c_double * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1)
+    H = (ctypes.c_double * 4)(1, 0, 0, 1)
+    assert lib.se2_sample_se2_gaussian(None, beta, S, 1, None, None) == 1
+    assert lib.se2_sample_deformed_gaussian(None, H, 0.0, 0.1, 1, None, None) == 1
