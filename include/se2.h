@@ -324,6 +324,61 @@ se2_status se2_convolve_noalloc(const void* f, const void* coeffs, void* out, in
                                 void* stream);
 
 /* Thread-local text of the last error (never NULL). */
+/*
+ * Odd sampling grids and upsampled output (Section 4.2, Eq. MatSKfonG and
+ * Algorithm SKLAlg; Section 6.1, Eqs. Qf, W, MatSKfgonG).
+ *
+ * A grid plan samples on Omega_L with L = (Lx, Ly, Lr) = 2K + 1 per axis
+ * (x_i = -1/2 + i/Lx, y_j = -1/2 + j/Ly, theta_l = 2 pi l / Lr) and evaluates
+ * the convolutional finite Fourier series
+ *   S_K[f, rho_1..rho_k](w) = sum_{|k| <= K} f^[k;L] rho_1^[k;L] .. rho_k^[k;L] phi_k(w)
+ * on the N-grid (x'_n = -1/2 + n/Nx, y'_m = -1/2 + m/Ny, theta'_l = 2 pi l / Nr),
+ * N >= L per axis.  With k = 0 the result is S_K[f] itself (the finite
+ * Fourier series of f on the N-grid).  N = L gives the plain scheme on an odd
+ * grid.  Arrays are x fastest: samples [n][Lr][Ly][Lx] and outputs
+ * [B][Nr][Ny][Nx] of the plan's real type; coefficients [n][Lr][Ly][Kx+1]
+ * complex (DFT bins; kx = 0..Kx, the rest follows from Hermitian symmetry).
+ * The kernels must be radial in translations for S_K[f, rho] to approximate
+ * f * rho (Theorem f*gP); the series itself is computed for any input.
+ */
+typedef struct se2_grid_plan_s* se2_grid_plan_t;
+
+/*
+ * se2_grid_plan_create -- L: host int[3] {Lx, Ly, Lr}, each odd in [1, 255];
+ * N: host int[3] {Nx, Ny, Nr} with L <= N <= 1024 per axis; batch >= 1;
+ * precision SE2_F32 or SE2_F64; flags 0 or SE2_SHARED_KERNEL (one coefficient
+ * array per kernel for the whole batch).  Allocates the DFT tables (FP64
+ * sincospi, rounded) and 2 * batch * Nr * Ny * (Kx+1) complex of workspace.
+ * Errors: SE2_ERR_UNSUPPORTED (even L, precision, flags), SE2_ERR_INVALID_ARG
+ * (N < L, batch, device), SE2_ERR_OOM; *plan is NULL on failure.
+ */
+se2_status se2_grid_plan_create(se2_grid_plan_t* plan, const int* L, const int* N, int batch, int precision,
+                                unsigned flags, int device);
+se2_status se2_grid_plan_destroy(se2_grid_plan_t plan);
+
+/* Kernel launches issued by this plan so far. */
+unsigned long long se2_grid_plan_launches(se2_grid_plan_t plan);
+
+/*
+ * se2_grid_coeffs -- C = DFT(P) / |L| (Eq. FkLv without its sign) of n <= batch
+ * real sample arrays [n][Lr][Ly][Lx] into coeffs [n][Lr][Ly][Kx+1] complex.
+ * Device pointers; asynchronous on `stream`.
+ */
+se2_status se2_grid_coeffs(se2_grid_plan_t plan, const void* samples, int n, void* coeffs, void* stream);
+
+/*
+ * se2_grid_convolve_chain -- out = Re S_K[f, rho_1..rho_k] on the N-grid for
+ * B <= batch problems: f [B][Lr][Ly][Lx] real, coeffs[t] from se2_grid_coeffs
+ * ([B][..] or, with SE2_SHARED_KERNEL, [1][..]), 0 <= k <= 32, out
+ * [B][Nr][Ny][Nx] real (must not alias f).  Computed as
+ *   sum over the stored bins of W^k (DFT(F)/|L|) C_1 .. C_k e^{+2 pi i k.n/N}
+ * (Proposition LtoN1D: the zero-padded iDFT of Eq. MatSKfgonG without forming
+ * the padded array).  Device pointers (host array of k coefficient pointers);
+ * asynchronous on `stream`.  Errors: SE2_ERR_INVALID_ARG.
+ */
+se2_status se2_grid_convolve_chain(se2_grid_plan_t plan, const void* f, int B, const void* const* coeffs, int k,
+                                   void* out, void* stream);
+
 const char* se2_last_error(void);
 
 /* Library version string. */

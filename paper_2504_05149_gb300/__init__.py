@@ -68,6 +68,13 @@ def load_library(path: str = LIB_PATH):
     dptr = ctypes.POINTER(ctypes.c_double)
     lib.se2_sample_se2_gaussian.argtypes = [vp, dptr, dptr, ctypes.c_int, vp, vp]
     lib.se2_sample_deformed_gaussian.argtypes = [vp, dptr, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
+    i3 = ctypes.POINTER(ctypes.c_int)
+    lib.se2_grid_plan_create.argtypes = [ctypes.POINTER(vp), i3, i3, ip, ip, ctypes.c_uint, ip]
+    lib.se2_grid_plan_destroy.argtypes = [vp]
+    lib.se2_grid_plan_launches.argtypes = [vp]
+    lib.se2_grid_plan_launches.restype = ctypes.c_ulonglong
+    lib.se2_grid_coeffs.argtypes = [vp, vp, ip, vp, vp]
+    lib.se2_grid_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ip, vp, vp]
     lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
     lib.se2_plan_launches.argtypes = [vp]
     lib.se2_plan_launches.restype = ctypes.c_ulonglong
@@ -77,6 +84,7 @@ def load_library(path: str = LIB_PATH):
                  "se2_convolve_chain", "se2_convolve_chain_all",
                  "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
                  "se2_sample_se2_gaussian", "se2_sample_deformed_gaussian",
+                 "se2_grid_plan_create", "se2_grid_plan_destroy", "se2_grid_coeffs", "se2_grid_convolve_chain",
                  "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -324,6 +332,95 @@ def sample_deformed_gaussian(plan: Plan, H, nu: float, s: float, images: int = 1
     return P
 
 
+class GridPlan:
+    """Odd sampling grid L = (Lx, Ly, Lr) (each 2K+1) with output on the
+    N-grid N = (Nx, Ny, Nr) >= L (se2_grid_plan_create)."""
+
+    def __init__(self, L: Sequence[int], N: Optional[Sequence[int]] = None, batch: int = 1,
+                 precision: str = "f32", flags: int = 0, device: Optional[int] = None):
+        lib = load_library()
+        if precision not in ("f32", "f64"):
+            raise ValueError("precision must be 'f32' or 'f64'")
+        N = tuple(L) if N is None else tuple(N)
+        if len(L) != 3 or len(N) != 3:
+            raise ValueError("L and N need three sizes (x, y, theta)")
+        self.Lx, self.Ly, self.Lr = (int(v) for v in L)
+        self.Nx, self.Ny, self.Nr = (int(v) for v in N)
+        self.Hx = (self.Lx - 1) // 2 + 1
+        self.batch, self.flags, self.precision = batch, flags, precision
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.dtype = torch.float64 if precision == "f64" else torch.float32
+        self.cdtype = torch.complex128 if precision == "f64" else torch.complex64
+        h = ctypes.c_void_p()
+        _check(lib.se2_grid_plan_create(ctypes.byref(h), (ctypes.c_int * 3)(self.Lx, self.Ly, self.Lr),
+                                        (ctypes.c_int * 3)(self.Nx, self.Ny, self.Nr), batch,
+                                        _PRECISIONS[precision], flags, self.device))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def launches(self) -> int:
+        return int(load_library().se2_grid_plan_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().se2_grid_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sample_shape(self, B: int):
+        return (B, self.Lr, self.Ly, self.Lx)
+
+    def out_shape(self, B: int):
+        return (B, self.Nr, self.Ny, self.Nx)
+
+    def spec_shape(self, B: int):
+        return (B, self.Lr, self.Ly, self.Hx)
+
+    def _check(self, t: torch.Tensor, name: str, shape_tail, dtype) -> int:
+        if t.dim() != 4 or tuple(t.shape[1:]) != tuple(shape_tail):
+            raise ValueError(f"{name}: expected [B, {', '.join(map(str, shape_tail))}], got {tuple(t.shape)}")
+        if t.dtype != dtype or not t.is_cuda or t.device.index != self.device or not t.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous {dtype} tensor on cuda:{self.device}")
+        return t.shape[0]
+
+
+def grid_coeffs(plan: GridPlan, samples: torch.Tensor) -> torch.Tensor:
+    """C = DFT(P)/|L| of [n, Lr, Ly, Lx] real samples: [n, Lr, Ly, Kx+1] complex."""
+    n = plan._check(samples, "samples", plan.sample_shape(1)[1:], plan.dtype)
+    C = torch.empty(plan.spec_shape(n), dtype=plan.cdtype, device=samples.device)
+    _check(load_library().se2_grid_coeffs(plan.handle, _ptr(samples), n, _ptr(C), _stream(samples.device)))
+    return C
+
+
+def grid_convolve_chain(plan: GridPlan, f: torch.Tensor, Cs: Sequence[torch.Tensor],
+                        out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Re S_K[f, rho_1..rho_k] on the N-grid ([B, Nr, Ny, Nx]); k = 0 gives the
+    finite Fourier series S_K[f] itself."""
+    B = plan._check(f, "f", plan.sample_shape(1)[1:], plan.dtype)
+    if out is None:
+        out = torch.empty(plan.out_shape(B), dtype=plan.dtype, device=f.device)
+    else:
+        plan._check(out, "out", plan.out_shape(1)[1:], plan.dtype)
+    nb = 1 if plan.flags & SHARED_KERNEL else B
+    for i, C in enumerate(Cs):
+        plan._check(C, f"coeffs[{i}]", plan.spec_shape(1)[1:], plan.cdtype)
+        if C.shape[0] != nb:
+            raise ValueError(f"coeffs[{i}]: expected {nb} arrays, got {C.shape[0]}")
+    k = len(Cs)
+    cp = (ctypes.c_void_p * max(k, 1))(*[C.data_ptr() for C in Cs])
+    _check(load_library().se2_grid_convolve_chain(plan.handle, _ptr(f), B, cp if k else None, k, _ptr(out),
+                                                  _stream(f.device)))
+    return out
+
+
 def table_len(plan: Plan) -> int:
     return plan.N // 2 + 1 + plan.N + plan.M
 
@@ -391,5 +488,6 @@ class SE2Conv(torch.autograd.Function):
 __all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_chain", "convolve_chain_all",
            "backward",
            "sample_radial_gaussian", "sample_se2_gaussian", "sample_deformed_gaussian",
+           "GridPlan", "grid_coeffs", "grid_convolve_chain",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
            "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO"]

@@ -1,0 +1,520 @@
+// Odd sampling grids L = 2K+1 per axis with the output on an N-grid >= L
+// (Section 4.2, Eq. MatSKfonG; Section 6.1, Eqs. Qf, W, MatSKfgonG;
+// Algorithm SKLAlg).  Sizes here are the paper's own experiment shapes
+// (e.g. L = (31, 33, 61) -> N = (36, 38, 76)): a few tens to a few hundred
+// points per axis, anisotropic, not powers of two.  Each axis is a direct DFT
+// (a small dense complex matrix applied to every line), which at these
+// lengths costs a few hundred flops per point and needs no mixed-radix plan.
+//
+// Zero padding (Eq. Qf) never materialises: the inverse passes sum only the
+// 2K+1 stored bins, with the exponentials of the output grid, which is what
+// Proposition LtoN1D states.  The product of coefficient arrays, the sign
+// W^k (Eq. W, signed frequencies) and 1/|L| are applied while the theta
+// inverse pass loads its input.
+//
+// Passes, for a batch of problems (x fastest everywhere):
+//   f [B][Lr][Ly][Lx] real
+//   -> x forward, real to half spectrum  [B][Lr][Ly][Hx]   (Hx = Kx + 1)
+//   -> y forward                          [B][Lr][Ly][Hx]
+//   -> theta forward = DFT(F)             [B][Lr][Ly][Hx]
+//   -> theta inverse onto Nr (x product)  [B][Nr][Ly][Hx]
+//   -> y inverse onto Ny                  [B][Nr][Ny][Hx]
+//   -> x inverse onto Nx, complex to real [B][Nr][Ny][Nx]
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <new>
+
+#include "../../include/se2.h"
+#include "se2_internal.h"
+
+using namespace se2;
+
+struct se2_grid_plan_s {
+    int Lx = 0, Ly = 0, Lr = 0, Nx = 0, Ny = 0, Nr = 0, Hx = 0;
+    int batch = 0, prec = 0, dev = 0;
+    unsigned flags = 0;
+    size_t celem = 0;              // bytes of one complex element
+    void* tab = nullptr;           // the six DFT tables, complex
+    size_t toff[6] = {};           // their offsets, in complex elements
+    void* buf[2] = {nullptr, nullptr};
+    unsigned long long launches = 0;
+};
+
+namespace {
+
+constexpr int kGridMaxK = 32;      // kernels in one chain
+constexpr int kGridMaxL = 255;     // largest sampling size per axis
+constexpr int kGridMaxN = 1024;    // largest output size per axis
+constexpr int kCols = 32;          // columns (or lines) per block
+constexpr int kGridThreads = 256;
+
+se2_status gfail(se2_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_last_error(buf);
+    return st;
+}
+
+se2_status gcuda(cudaError_t e, const char* what) {
+    return gfail(SE2_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+struct GDevice {
+    int prev = -1;
+    explicit GDevice(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~GDevice() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Signed frequency of bin b for an odd length L = 2K+1 (Eq. tauKk inverted).
+__host__ __device__ inline int sfreq(int b, int L) { return b <= (L - 1) / 2 ? b : b - L; }
+
+// ---------------------------------------------------------------------------
+// DFT tables, FP64 (sincospi of the exactly reduced rational angle), rounded
+// to T.  Layouts follow the pass that reads them:
+//   0: x forward  [Lx][Hx]  e^{-2 pi i kx n / Lx}                (row passes: [in][out])
+//   1: y forward  [Ly][Ly]  e^{-2 pi i ky m / Ly}                (column passes: [out][in])
+//   2: theta fwd  [Lr][Lr]  e^{-2 pi i kr l / Lr}
+//   3: theta inv  [Nr][Lr]  e^{+2 pi i s(kr) l' / Nr}
+//   4: y inverse  [Ny][Ly]  e^{+2 pi i s(ky) m' / Ny}
+//   5: x inverse  [Hx][Nx]  w(kx) e^{+2 pi i kx n' / Nx}, w = 1 at kx = 0, else 2
+// ---------------------------------------------------------------------------
+struct TabArgs {
+    int Lx, Ly, Lr, Nx, Ny, Nr, Hx;
+    long long off[6], total;
+};
+
+__device__ inline void cis_frac(long long num, long long den, int sign, double& c, double& s) {
+    long long r = num % den;
+    if (r < 0) r += den;
+    double sp, cp;
+    sincospi(2.0 * (double)r / (double)den, &sp, &cp);
+    c = cp;
+    s = sign * sp;
+}
+
+template <typename T>
+__global__ void k_grid_tables(TabArgs a, c2<T>* tab) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < a.total;
+         e += (long long)gridDim.x * blockDim.x) {
+        double c = 0, s = 0, w = 1;
+        if (e < a.off[1]) {                                  // x forward [n][kx]
+            const long long t = e - a.off[0];
+            const int n = (int)(t / a.Hx), kx = (int)(t % a.Hx);
+            cis_frac((long long)kx * n, a.Lx, -1, c, s);
+        } else if (e < a.off[2]) {                           // y forward [ky][m]
+            const long long t = e - a.off[1];
+            const int ky = (int)(t / a.Ly), m = (int)(t % a.Ly);
+            cis_frac((long long)ky * m, a.Ly, -1, c, s);
+        } else if (e < a.off[3]) {                           // theta forward [kr][l]
+            const long long t = e - a.off[2];
+            const int kr = (int)(t / a.Lr), l = (int)(t % a.Lr);
+            cis_frac((long long)kr * l, a.Lr, -1, c, s);
+        } else if (e < a.off[4]) {                           // theta inverse [l'][kr]
+            const long long t = e - a.off[3];
+            const int l = (int)(t / a.Lr), kb = (int)(t % a.Lr);
+            cis_frac((long long)sfreq(kb, a.Lr) * l, a.Nr, +1, c, s);
+        } else if (e < a.off[5]) {                           // y inverse [m'][ky]
+            const long long t = e - a.off[4];
+            const int m = (int)(t / a.Ly), kb = (int)(t % a.Ly);
+            cis_frac((long long)sfreq(kb, a.Ly) * m, a.Ny, +1, c, s);
+        } else {                                             // x inverse [kx][n']
+            const long long t = e - a.off[5];
+            const int kx = (int)(t / a.Nx), n = (int)(t % a.Nx);
+            cis_frac((long long)kx * n, a.Nx, +1, c, s);
+            w = kx == 0 ? 1.0 : 2.0;
+        }
+        tab[e] = mk<T>((T)(w * c), (T)(w * s));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One axis pass.  Column q of the pass (a line along the axis) has its element
+// i at  (q / inner) * so + (q % inner) + i * si  (input and output alike, with
+// their own strides).  Row passes (x, inner = 1) put the output index on the
+// lanes; column passes (y, theta) put 32 neighbouring columns on the lanes.
+// ---------------------------------------------------------------------------
+enum GridMode { GM_R2C = 0, GM_C2C = 1, GM_MUL = 2, GM_C2R = 3 };
+
+template <typename T>
+struct GridPass {
+    const void* in;
+    void* out;
+    const c2<T>* E;
+    int n_in, n_out, inner;
+    long long Q, in_so, in_si, out_so, out_sj;
+    T out_scale;
+    // GM_MUL: input times scale * W^k * C_1 ... C_k at the same bin
+    const c2<T>* C[kGridMaxK];
+    long long c_bstride;          // per problem (0: one array for the batch)
+    int k, Ly, Hx;
+    T in_scale;
+};
+
+__device__ __forceinline__ long long gaddr(long long q, int inner, long long so) {
+    return (q / inner) * so + (q % inner);
+}
+
+// Row passes: x forward (real input) and x inverse (real output).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kGridThreads) k_grid_rows(GridPass<T> a) {
+    extern __shared__ __align__(16) unsigned char g_smem[];
+    const long long q0 = (long long)blockIdx.x * kCols;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (MODE == GM_R2C) {
+        T* s = reinterpret_cast<T*>(g_smem);                              // [kCols][n_in]
+        const T* in = static_cast<const T*>(a.in);
+        for (int idx = tid; idx < kCols * a.n_in; idx += kGridThreads) {
+            const int r = idx / a.n_in, i = idx % a.n_in;
+            const long long q = q0 + r;
+            s[idx] = q < a.Q ? in[q * a.in_so + i * a.in_si] : T(0);
+        }
+        __syncthreads();
+        c2<T>* out = static_cast<c2<T>*>(a.out);
+        for (int r = warp; r < kCols; r += kGridThreads / 32) {
+            const long long q = q0 + r;
+            if (q >= a.Q) break;
+            const T* sr = s + r * a.n_in;
+            for (int j = lane; j < a.n_out; j += 32) {
+                T ar = 0, ai = 0;
+                for (int i = 0; i < a.n_in; ++i) {
+                    const c2<T> e = a.E[(long long)i * a.n_out + j];
+                    ar += e.x * sr[i];
+                    ai += e.y * sr[i];
+                }
+                out[q * a.out_so + j * a.out_sj] = mk<T>(ar, ai);
+            }
+        }
+    } else {  // GM_C2R
+        c2<T>* s = reinterpret_cast<c2<T>*>(g_smem);                      // [kCols][n_in]
+        const c2<T>* in = static_cast<const c2<T>*>(a.in);
+        for (int idx = tid; idx < kCols * a.n_in; idx += kGridThreads) {
+            const int r = idx / a.n_in, i = idx % a.n_in;
+            const long long q = q0 + r;
+            s[idx] = q < a.Q ? in[q * a.in_so + i * a.in_si] : mk<T>(0, 0);
+        }
+        __syncthreads();
+        T* out = static_cast<T*>(a.out);
+        for (int r = warp; r < kCols; r += kGridThreads / 32) {
+            const long long q = q0 + r;
+            if (q >= a.Q) break;
+            const c2<T>* sr = s + r * a.n_in;
+            for (int j = lane; j < a.n_out; j += 32) {
+                T acc = 0;
+                for (int i = 0; i < a.n_in; ++i) {
+                    const c2<T> e = a.E[(long long)i * a.n_out + j];
+                    const c2<T> v = sr[i];
+                    acc += e.x * v.x - e.y * v.y;                   // Re(e v)
+                }
+                out[q * a.out_so + j * a.out_sj] = acc;
+            }
+        }
+    }
+}
+
+// Column passes: y and theta, forward and inverse; GM_MUL forms the product
+// of the spectra while loading.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kGridThreads) k_grid_cols(GridPass<T> a) {
+    extern __shared__ __align__(16) unsigned char g_smem[];
+    c2<T>* s = reinterpret_cast<c2<T>*>(g_smem);                          // [n_in][kCols]
+    const long long q0 = (long long)blockIdx.x * kCols;
+    const int tid = threadIdx.x;
+    const c2<T>* in = static_cast<const c2<T>*>(a.in);
+    for (int idx = tid; idx < kCols * a.n_in; idx += kGridThreads) {
+        const int c = idx % kCols, i = idx / kCols;
+        const long long q = q0 + c;
+        c2<T> v = mk<T>(0, 0);
+        if (q < a.Q) {
+            const long long off = gaddr(q, a.inner, a.in_so) + i * a.in_si;
+            v = in[off];
+            if (MODE == GM_MUL) {
+                // column q = b * inner + (ky * Hx + kx); the bin index along theta is i
+                const long long b = q / a.inner;
+                const int cc = (int)(q % a.inner), ky = cc / a.Hx, kx = cc % a.Hx;
+                T sr = a.in_scale;
+                if ((a.k & 1) && ((kx + sfreq(ky, a.Ly)) & 1)) sr = -sr;
+                v.x *= sr;
+                v.y *= sr;
+                const long long coff = b * a.c_bstride + (off - b * a.in_so);
+                for (int t = 0; t < a.k; ++t) {
+                    const c2<T> w = a.C[t][coff];
+                    const T xr = v.x * w.x - v.y * w.y, xi = v.x * w.y + v.y * w.x;
+                    v.x = xr;
+                    v.y = xi;
+                }
+            }
+        }
+        s[idx] = v;
+    }
+    __syncthreads();
+    c2<T>* out = static_cast<c2<T>*>(a.out);
+    const int c = tid % kCols, g = tid / kCols;
+    const long long q = q0 + c;
+    if (q >= a.Q) return;
+    const long long obase = gaddr(q, a.inner, a.out_so);
+    for (int j = g; j < a.n_out; j += kGridThreads / kCols) {
+        const c2<T>* e = a.E + (long long)j * a.n_in;
+        T ar = 0, ai = 0;
+        for (int i = 0; i < a.n_in; ++i) {
+            const c2<T> w = e[i];
+            const c2<T> v = s[i * kCols + c];
+            ar += w.x * v.x - w.y * v.y;
+            ai += w.x * v.y + w.y * v.x;
+        }
+        out[obase + j * a.out_sj] = mk<T>(ar * a.out_scale, ai * a.out_scale);
+    }
+}
+
+template <typename T>
+size_t pass_smem(int mode, int n_in) {
+    return (size_t)kCols * n_in * (mode == GM_R2C ? sizeof(T) : sizeof(c2<T>));
+}
+
+template <typename T>
+cudaError_t launch_pass(se2_grid_plan_s* p, int mode, const GridPass<T>& a, cudaStream_t s) {
+    const size_t sm = pass_smem<T>(mode, a.n_in);
+    const unsigned blocks = (unsigned)((a.Q + kCols - 1) / kCols);
+    if (blocks == 0) return cudaSuccess;
+    switch (mode) {
+        case GM_R2C: k_grid_rows<T, GM_R2C><<<blocks, kGridThreads, sm, s>>>(a); break;
+        case GM_C2R: k_grid_rows<T, GM_C2R><<<blocks, kGridThreads, sm, s>>>(a); break;
+        case GM_C2C: k_grid_cols<T, GM_C2C><<<blocks, kGridThreads, sm, s>>>(a); break;
+        default: k_grid_cols<T, GM_MUL><<<blocks, kGridThreads, sm, s>>>(a); break;
+    }
+    ++p->launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t set_smem_attrs() {
+    const int big = (int)(kCols * kGridMaxL * sizeof(c2<T>));
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_grid_rows<T, GM_R2C>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_grid_rows<T, GM_C2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_grid_cols<T, GM_C2C>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    return cudaFuncSetAttribute(k_grid_cols<T, GM_MUL>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+template <typename T>
+const c2<T>* table(const se2_grid_plan_s* p, int i) {
+    return static_cast<const c2<T>*>(p->tab) + p->toff[i];
+}
+
+// The three forward passes of B problems: real [B][Lr][Ly][Lx] -> DFT on
+// [B][Lr][Ly][Hx] in `dst`, times `scale` (the last pass writes dst).
+template <typename T>
+cudaError_t forward(se2_grid_plan_s* p, const T* src, int B, c2<T>* dst, T scale, cudaStream_t s) {
+    const long long slab = (long long)p->Lr * p->Ly * p->Hx;
+    c2<T>* A = static_cast<c2<T>*>(p->buf[0]);
+    c2<T>* Bf = static_cast<c2<T>*>(p->buf[1]);
+    cudaError_t e;
+    GridPass<T> a = {};
+    a.out_scale = T(1);
+    // x: lines (b, l, m), real Lx -> Hx bins
+    a.in = src; a.out = A; a.E = table<T>(p, 0);
+    a.n_in = p->Lx; a.n_out = p->Hx; a.inner = 1;
+    a.Q = (long long)B * p->Lr * p->Ly;
+    a.in_so = p->Lx; a.in_si = 1; a.out_so = p->Hx; a.out_sj = 1;
+    if ((e = launch_pass<T>(p, GM_R2C, a, s))) return e;
+    // y: columns (b, l, kx)
+    a.in = A; a.out = Bf; a.E = table<T>(p, 1);
+    a.n_in = p->Ly; a.n_out = p->Ly; a.inner = p->Hx;
+    a.Q = (long long)B * p->Lr * p->Hx;
+    a.in_so = (long long)p->Ly * p->Hx; a.in_si = p->Hx; a.out_so = a.in_so; a.out_sj = p->Hx;
+    if ((e = launch_pass<T>(p, GM_C2C, a, s))) return e;
+    // theta: columns (b, ky, kx)
+    a.in = Bf; a.out = dst; a.E = table<T>(p, 2);
+    a.n_in = p->Lr; a.n_out = p->Lr; a.inner = p->Ly * p->Hx;
+    a.Q = (long long)B * p->Ly * p->Hx;
+    a.in_so = slab; a.in_si = (long long)p->Ly * p->Hx; a.out_so = slab; a.out_sj = a.in_si;
+    a.out_scale = scale;
+    return launch_pass<T>(p, GM_C2C, a, s);
+}
+
+template <typename T>
+cudaError_t run_chain(se2_grid_plan_s* p, const T* f, int B, const void* const* coeffs, int k, T* out,
+                      cudaStream_t s) {
+    const long long slab = (long long)p->Lr * p->Ly * p->Hx;
+    c2<T>* A = static_cast<c2<T>*>(p->buf[0]);
+    c2<T>* Bf = static_cast<c2<T>*>(p->buf[1]);
+    cudaError_t e;
+    if ((e = forward<T>(p, f, B, A, T(1), s))) return e;
+    GridPass<T> a = {};
+    a.out_scale = T(1);
+    // theta inverse onto Nr, with the product: columns (b, ky, kx)
+    a.in = A; a.out = Bf; a.E = table<T>(p, 3);
+    a.n_in = p->Lr; a.n_out = p->Nr; a.inner = p->Ly * p->Hx;
+    a.Q = (long long)B * p->Ly * p->Hx;
+    a.in_so = slab; a.in_si = (long long)p->Ly * p->Hx;
+    a.out_so = (long long)p->Nr * p->Ly * p->Hx; a.out_sj = a.in_si;
+    for (int t = 0; t < k; ++t) a.C[t] = static_cast<const c2<T>*>(coeffs[t]);
+    a.c_bstride = (p->flags & SE2_SHARED_KERNEL) ? 0 : slab;
+    a.k = k; a.Ly = p->Ly; a.Hx = p->Hx;
+    a.in_scale = (T)(1.0 / ((double)p->Lx * p->Ly * p->Lr));
+    if ((e = launch_pass<T>(p, GM_MUL, a, s))) return e;
+    // y inverse onto Ny: columns (b, l', kx)
+    GridPass<T> y = {};
+    y.out_scale = T(1);
+    y.in = Bf; y.out = A; y.E = table<T>(p, 4);
+    y.n_in = p->Ly; y.n_out = p->Ny; y.inner = p->Hx;
+    y.Q = (long long)B * p->Nr * p->Hx;
+    y.in_so = (long long)p->Ly * p->Hx; y.in_si = p->Hx;
+    y.out_so = (long long)p->Ny * p->Hx; y.out_sj = p->Hx;
+    if ((e = launch_pass<T>(p, GM_C2C, y, s))) return e;
+    // x inverse onto Nx, complex to real: lines (b, l', m')
+    GridPass<T> x = {};
+    x.out_scale = T(1);
+    x.in = A; x.out = out; x.E = table<T>(p, 5);
+    x.n_in = p->Hx; x.n_out = p->Nx; x.inner = 1;
+    x.Q = (long long)B * p->Nr * p->Ny;
+    x.in_so = p->Hx; x.in_si = 1; x.out_so = p->Nx; x.out_sj = 1;
+    return launch_pass<T>(p, GM_C2R, x, s);
+}
+
+bool galigned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+se2_status check_gplan(se2_grid_plan_t p) {
+    if (p == nullptr) return gfail(SE2_ERR_INVALID_ARG, "plan is NULL");
+    return SE2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+se2_status se2_grid_plan_create(se2_grid_plan_t* out, const int* L, const int* N, int batch, int precision,
+                                unsigned flags, int device) {
+    if (out == nullptr) return gfail(SE2_ERR_INVALID_ARG, "plan pointer is NULL");
+    *out = nullptr;
+    if (L == nullptr || N == nullptr) return gfail(SE2_ERR_INVALID_ARG, "L or N is NULL");
+    for (int i = 0; i < 3; ++i) {
+        if (L[i] < 1 || L[i] > kGridMaxL || (L[i] & 1) == 0)
+            return gfail(SE2_ERR_UNSUPPORTED, "L[%d]=%d: sampling sizes must be odd (L = 2K+1) in [1, %d]", i, L[i],
+                         kGridMaxL);
+        if (N[i] < L[i] || N[i] > kGridMaxN)
+            return gfail(SE2_ERR_INVALID_ARG, "N[%d]=%d: output sizes must satisfy L <= N <= %d", i, N[i], kGridMaxN);
+    }
+    if (batch < 1) return gfail(SE2_ERR_INVALID_ARG, "batch=%d must be >= 1", batch);
+    if (precision != SE2_F32 && precision != SE2_F64)
+        return gfail(SE2_ERR_UNSUPPORTED, "precision %d: the grid path runs SE2_F32 or SE2_F64", precision);
+    if (flags & ~(unsigned)SE2_SHARED_KERNEL) return gfail(SE2_ERR_UNSUPPORTED, "flags 0x%x: only SE2_SHARED_KERNEL", flags);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return gfail(SE2_ERR_INVALID_ARG, "device %d not available", device);
+    se2_grid_plan_s* p = new (std::nothrow) se2_grid_plan_s();
+    if (p == nullptr) return gfail(SE2_ERR_OOM, "host allocation failed");
+    p->Lx = L[0]; p->Ly = L[1]; p->Lr = L[2];
+    p->Nx = N[0]; p->Ny = N[1]; p->Nr = N[2];
+    p->Hx = (p->Lx - 1) / 2 + 1;
+    p->batch = batch;
+    p->prec = precision;
+    p->dev = device;
+    p->flags = flags;
+    p->celem = precision == SE2_F64 ? 16 : 8;
+    GDevice guard(device);
+    TabArgs ta;
+    ta.Lx = p->Lx; ta.Ly = p->Ly; ta.Lr = p->Lr; ta.Nx = p->Nx; ta.Ny = p->Ny; ta.Nr = p->Nr; ta.Hx = p->Hx;
+    const long long sz[6] = {(long long)p->Lx * p->Hx, (long long)p->Ly * p->Ly, (long long)p->Lr * p->Lr,
+                             (long long)p->Nr * p->Lr, (long long)p->Ny * p->Ly, (long long)p->Hx * p->Nx};
+    long long acc = 0;
+    for (int i = 0; i < 6; ++i) {
+        ta.off[i] = acc;
+        p->toff[i] = (size_t)acc;
+        acc += sz[i];
+    }
+    ta.total = acc;
+    const size_t ws = (size_t)batch * p->Nr * p->Ny * p->Hx * p->celem;
+    cudaError_t e = cudaMalloc(&p->tab, (size_t)acc * p->celem);
+    if (e == cudaSuccess) e = cudaMalloc(&p->buf[0], ws);
+    if (e == cudaSuccess) e = cudaMalloc(&p->buf[1], ws);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        se2_grid_plan_destroy(p);
+        return gfail(SE2_ERR_OOM, "device allocation of %zu bytes failed", 2 * ws + (size_t)acc * p->celem);
+    }
+    const int blocks = (int)((acc + 255) / 256 < 1024 ? (acc + 255) / 256 : 1024);
+    if (precision == SE2_F64) {
+        e = set_smem_attrs<double>();
+        if (e == cudaSuccess) k_grid_tables<double><<<blocks, 256>>>(ta, static_cast<c2<double>*>(p->tab));
+    } else {
+        e = set_smem_attrs<float>();
+        if (e == cudaSuccess) k_grid_tables<float><<<blocks, 256>>>(ta, static_cast<c2<float>*>(p->tab));
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        se2_grid_plan_destroy(p);
+        return gcuda(e, "grid plan setup");
+    }
+    *out = p;
+    return SE2_OK;
+}
+
+se2_status se2_grid_plan_destroy(se2_grid_plan_t p) {
+    if (p == nullptr) return SE2_OK;
+    {
+        GDevice guard(p->dev);
+        if (p->tab) cudaFree(p->tab);
+        if (p->buf[0]) cudaFree(p->buf[0]);
+        if (p->buf[1]) cudaFree(p->buf[1]);
+    }
+    delete p;
+    return SE2_OK;
+}
+
+unsigned long long se2_grid_plan_launches(se2_grid_plan_t p) { return p ? p->launches : 0ull; }
+
+se2_status se2_grid_coeffs(se2_grid_plan_t p, const void* samples, int n, void* coeffs, void* stream) {
+    se2_status st = check_gplan(p);
+    if (st != SE2_OK) return st;
+    if (samples == nullptr || coeffs == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (n < 1 || n > p->batch) return gfail(SE2_ERR_INVALID_ARG, "n=%d must be in [1, batch=%d]", n, p->batch);
+    if (!galigned(samples, p->celem / 2) || !galigned(coeffs, p->celem))
+        return gfail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    GDevice guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const double inv = 1.0 / ((double)p->Lx * p->Ly * p->Lr);
+    cudaError_t e = p->prec == SE2_F64
+                        ? forward<double>(p, static_cast<const double*>(samples), n, static_cast<c2<double>*>(coeffs),
+                                          inv, s)
+                        : forward<float>(p, static_cast<const float*>(samples), n, static_cast<c2<float>*>(coeffs),
+                                         (float)inv, s);
+    if (e != cudaSuccess) return gcuda(e, "kernel launch");
+    return SE2_OK;
+}
+
+se2_status se2_grid_convolve_chain(se2_grid_plan_t p, const void* f, int B, const void* const* coeffs, int k,
+                                   void* out, void* stream) {
+    se2_status st = check_gplan(p);
+    if (st != SE2_OK) return st;
+    if (f == nullptr || out == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (B < 1 || B > p->batch) return gfail(SE2_ERR_INVALID_ARG, "B=%d must be in [1, batch=%d]", B, p->batch);
+    if (k < 0 || k > kGridMaxK) return gfail(SE2_ERR_INVALID_ARG, "k=%d must be in [0, %d]", k, kGridMaxK);
+    if (k > 0 && coeffs == nullptr) return gfail(SE2_ERR_INVALID_ARG, "coeffs is NULL");
+    if (!galigned(f, p->celem / 2) || !galigned(out, p->celem / 2)) return gfail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    for (int t = 0; t < k; ++t)
+        if (coeffs[t] == nullptr || !galigned(coeffs[t], p->celem))
+            return gfail(SE2_ERR_INVALID_ARG, "coeffs[%d] NULL or misaligned", t);
+    if (f == out) return gfail(SE2_ERR_INVALID_ARG, "out aliases f");
+    GDevice guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = p->prec == SE2_F64
+                        ? run_chain<double>(p, static_cast<const double*>(f), B, coeffs, k, static_cast<double*>(out), s)
+                        : run_chain<float>(p, static_cast<const float*>(f), B, coeffs, k, static_cast<float*>(out), s);
+    if (e != cudaSuccess) return gcuda(e, "kernel launch");
+    return SE2_OK;
+}
+
+}  // extern "C"

@@ -77,3 +77,19 @@ def test_samplers_reject_null_plan_on_host(lib):
     H = (ctypes.c_double * 4)(1, 0, 0, 1)
     assert lib.se2_sample_se2_gaussian(None, beta, S, 1, None, None) == 1
     assert lib.se2_sample_deformed_gaussian(None, H, 0.0, 0.1, 1, None, None) == 1
+
+
+@pytest.mark.parametrize("L,N,status", [
+    ((8, 9, 9), (8, 9, 9), 2),       # even sampling size -> UNSUPPORTED
+    ((9, 9, 257), (9, 9, 257), 2),   # above the largest sampling size
+    ((9, 9, 9), (9, 8, 9), 1),       # N < L -> INVALID_ARG
+    ((9, 9, 9), (9, 9, 2000), 1),    # N too large
+])
+def test_grid_plan_rejects_bad_sizes_on_host(lib, L, N, status):
+    h = ctypes.c_void_p(1)
+    i3 = ctypes.c_int * 3
+    lib.se2_grid_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                         ctypes.c_int]
+    assert lib.se2_grid_plan_create(ctypes.byref(h), i3(*L), i3(*N), 1, 1, 0, 0) == status
+    assert not h.value

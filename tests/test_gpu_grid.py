@@ -1,0 +1,131 @@
+"""Odd sampling grids L = 2K+1 with output on an N-grid >= L
+(se2_grid_plan_*, Eqs. Qf, W, MatSKfgonG) against the FP64 oracle's series
+definition.  Errors are normwise: max|gpu - oracle| / max|oracle|."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import se2_gaussians as G  # noqa: E402
+from oracle import se2_upsample as U  # noqa: E402
+
+TOL = {"f32": 1e-5, "f64": 1e-10}
+NP = {"f32": np.float32, "f64": np.float64}
+
+
+@pytest.fixture(scope="module")
+def se2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_05149_gb300 import build as b
+    b.build()
+    import paper_2504_05149_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _axes(L):
+    Lx, Ly, Lr = L
+    return (-0.5 + np.arange(Lx) / Lx, -0.5 + np.arange(Ly) / Ly, 2 * np.pi * np.arange(Lr) / Lr)
+
+
+def deformed(L, H, nu, s):
+    """f_H^{nu,s} (Eq. fHsnu) on the anisotropic grid Omega_L, [Lr][Ly][Lx]."""
+    x, y, t = _axes(L)
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    sp = np.exp(-(H[0][0] * X * X + (H[0][1] + H[1][0]) * X * Y + H[1][1] * Y * Y))
+    return np.exp(-((t - nu) ** 2) / s)[:, None, None] * sp[None]
+
+
+def se2_gauss(L, sigma2, nu):
+    """rho of Eq. gbS0 shifted by nu, one lattice image, [Lr][Ly][Lx]."""
+    x, y, t = _axes(L)
+    T, Y, X = np.meshgrid(t, y, x, indexing="ij")
+    return G.se2_gaussian_at(X, Y, T, (0.0, 0.0, nu), sigma2 * np.eye(3))
+
+
+def _dev(a, prec):
+    return torch.from_numpy(np.ascontiguousarray(a.astype(NP[prec]))).cuda()
+
+
+def _round(a, prec):
+    return a.astype(NP[prec]).astype(np.float64)
+
+
+CASES = [
+    # (L = (Lx, Ly, Lr), N = (Nx, Ny, Nr), k, B)
+    ((31, 33, 61), (36, 38, 76), 1, 1),     # the paper's single-convolution experiment shape
+    ((7, 5, 9), (7, 5, 9), 2, 2),           # N = L, odd
+    ((15, 17, 21), (32, 32, 32), 3, 3),     # upsampled chain
+    ((9, 11, 13), (20, 21, 22), 0, 2),      # S_K[f] itself (no kernel)
+    ((1, 3, 5), (4, 3, 8), 1, 1),           # K = 0 along x
+    ((41, 43, 151), (41, 43, 151), 3, 1),   # the triple-convolution shape, N = L
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_grid_chain_matches_series(se2, prec, case):
+    L, N, k, B = CASES[case]
+    plan = se2.GridPlan(L, N, batch=B, precision=prec)
+    Fs = [_round(deformed(L, [[1 / 0.03, 0.002], [0.002, 1 / 0.01]], math.pi / 2 + 0.3 * b, 0.05), prec)
+          for b in range(B)]
+    Ps = [[_round(se2_gauss(L, 0.004 + 0.001 * t, 0.2 * t + 0.1 * b), prec) for t in range(k)] for b in range(B)]
+    f = _dev(np.stack(Fs)[:, :, :, :], prec)
+    Cs = [se2.grid_coeffs(plan, _dev(np.stack([Ps[b][t] for b in range(B)]), prec)) for t in range(k)]
+    n0 = plan.launches()
+    out = se2.grid_convolve_chain(plan, f, Cs)
+    torch.cuda.synchronize()
+    assert plan.launches() - n0 == 6
+    got = out.double().cpu().numpy()
+    Nx, Ny, Nr = N
+    for b in range(B):
+        want = U.series(Fs[b], Ps[b], (Nr, Ny, Nx)).real
+        assert _rel(got[b], want) < TOL[prec], b
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_grid_coeffs(se2, prec):
+    L = (9, 7, 11)
+    plan = se2.GridPlan(L, batch=2, precision=prec)
+    rng = np.random.default_rng(3)
+    P = _round(rng.standard_normal((2, 11, 7, 9)), prec)
+    C = se2.grid_coeffs(plan, _dev(P, prec)).cpu().numpy()
+    want = np.fft.fftn(P, axes=(1, 2, 3))[..., :5] / (9 * 7 * 11)
+    assert _rel(C, want) < {"f32": 1e-6, "f64": 1e-13}[prec]
+
+
+def test_grid_shared_kernel_and_paper_e4(se2):
+    """The paper's single-convolution experiment (L = (31, 33, 61), output
+    36 x 38 x 76; f: H = diag(0.03, 0.01)^-1, s = 0.01, nu = pi/2; rho the
+    radial deformed Gaussian U = (1/0.02) I with the same s, nu) on a batch
+    of 4 sharing the kernel."""
+    L, N = (31, 33, 61), (36, 38, 76)
+    plan = se2.GridPlan(L, N, batch=4, precision="f32", flags=se2.SHARED_KERNEL)
+    F = _round(deformed(L, [[1 / 0.03, 0], [0, 1 / 0.01]], math.pi / 2, 0.01), "f32")
+    P = _round(deformed(L, [[1 / 0.02, 0], [0, 1 / 0.02]], math.pi / 2, 0.01), "f32")
+    f = _dev(np.stack([F * (b + 1) for b in range(4)]), "f32")
+    C = se2.grid_coeffs(plan, _dev(P[None], "f32"))
+    out = se2.grid_convolve_chain(plan, f, [C]).double().cpu().numpy()
+    want = U.series(F, [P], (76, 38, 36)).real
+    for b in range(4):
+        assert _rel(out[b], (b + 1) * want) < 1e-5
+
+
+def test_grid_plan_errors(se2):
+    with pytest.raises(se2.SE2Error) as e:
+        se2.GridPlan((8, 9, 9))
+    assert e.value.status == 2
+    with pytest.raises(se2.SE2Error) as e:
+        se2.GridPlan((9, 9, 9), (9, 8, 9))
+    assert e.value.status == 1
+    plan = se2.GridPlan((5, 5, 5), batch=1)
+    f = torch.zeros((2, 5, 5, 5), device="cuda")
+    with pytest.raises(se2.SE2Error):
+        se2.grid_convolve_chain(plan, f, [])          # B above the plan's batch
