@@ -42,10 +42,13 @@ def parse():
     ap.add_argument("--N", type=int, default=N_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c2chain", "c2all", "c3", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c2chain", "c2all", "c3", "c4", "c5", "e4"],
                     help="c2: single convolutions at 256^2x64 (the headline); c2chain: 8-fold chains; "
                          "c2all: 8-fold chains emitting every intermediate (Algorithm 6); "
-                         "c4: 4096 uneven problems with separable chains (CUDA graph); c5: forward+adjoint")
+                         "c4: 4096 uneven problems with separable chains (CUDA graph); c5: forward+adjoint; "
+                         "e4: the paper's single-convolution experiment, L = (31, 33, 61) sampled, "
+                         "output on 36 x 38 x 76 (grid plan, odd sizes, upsampled)")
+    ap.add_argument("--grid-batch", type=int, default=1024, help="e4 batch size")
     ap.add_argument("--problems", type=int, default=4096, help="c4 batch size")
     ap.add_argument("--precision", default="f32", choices=["f32", "split_bf16", "bf16"],
                     help="c2: arithmetic of the angular DFT (tensor cores for split_bf16 / bf16)")
@@ -205,7 +208,7 @@ def main():
     if args.config != "c2":
         from functools import partial
         {"c2chain": run_chain8, "c2all": partial(run_chain8, emit_all=True), "c3": run_precision,
-         "c4": run_batch, "c5": run_adjoint}[args.config](args)
+         "c4": run_batch, "c5": run_adjoint, "e4": run_grid_e4}[args.config](args)
         return
     import torch
     import torch.distributed as dist
@@ -450,6 +453,79 @@ def run_chain8(args, emit_all=False):
           {"roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "traffic": None, "peak_source": src, "alg_bytes_per_chain": alg / B},
            "gpu_launches": launched, "clocks": clocks})
+
+
+def grid_flops(L, N, k=1):
+    """Real flops of the six direct-DFT passes of one grid-plan convolution
+    (a complex multiply-add counts 8, a real-by-complex or real-part one 4)."""
+    (Lx, Ly, Lr), (Nx, Ny, Nr) = L, N
+    Hx = (Lx - 1) // 2 + 1
+    return (4 * Lr * Ly * Hx * Lx + 8 * Lr * Hx * Ly * Ly + 8 * Ly * Hx * Lr * Lr
+            + 8 * Ly * Hx * Nr * Lr + 6 * k * Lr * Ly * Hx + 8 * Nr * Hx * Ny * Ly + 4 * Nr * Ny * Hx * Nx)
+
+
+def alu_peak_f32(sm_mhz):
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops per cycle at the given clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_grid_e4(args):
+    """The paper's single-convolution experiment (Section 6.2): f = f_H^{nu,s}
+    with H = diag(0.03, 0.01)^-1, rho = f_U^{nu,s} with U = (1/0.02) I,
+    s = 0.01, nu = pi/2, sampled on L = (31, 33, 61) and evaluated on a
+    36 x 38 x 76 grid; a batch of such problems (amplitudes vary) through one
+    grid plan, FP32."""
+    import math
+    import torch
+    import paper_2504_05149_gb300 as se2
+    L, N, B = (31, 33, 61), (36, 38, 76), args.grid_batch
+    dev = torch.device("cuda", 0)
+    plan = se2.GridPlan(L, N, batch=B, precision="f32", flags=se2.SHARED_KERNEL)
+
+    def deformed(Hd, nu, s):
+        x = -0.5 + np.arange(L[0]) / L[0]
+        y = -0.5 + np.arange(L[1]) / L[1]
+        t = 2 * np.pi * np.arange(L[2]) / L[2]
+        Y, X = np.meshgrid(y, x, indexing="ij")
+        sp = np.exp(-(Hd[0] * X * X + Hd[1] * Y * Y))
+        return (np.exp(-((t - nu) ** 2) / s)[:, None, None] * sp[None]).astype(np.float32)
+
+    F = torch.from_numpy(deformed((1 / 0.03, 1 / 0.01), math.pi / 2, 0.01))
+    P = torch.from_numpy(deformed((1 / 0.02, 1 / 0.02), math.pi / 2, 0.01))
+    amp = torch.linspace(0.5, 1.5, B).view(B, 1, 1, 1)
+    f = (F[None] * amp).contiguous().to(dev)
+    C = se2.grid_coeffs(plan, P[None].contiguous().to(dev))
+    out = torch.empty(plan.out_shape(B), dtype=torch.float32, device=dev)
+    fn = lambda: se2.grid_convolve_chain(plan, f, [C], out=out)                 # noqa: E731
+    ms, clocks, launched = _clock_and_time(fn, args.steps, args.warmup, dev, plans=(plan,))
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import se2_upsample as U
+        Fd, Pd = F.double().numpy(), P.double().numpy()
+        n, t0 = 0, time.time()
+        while time.time() - t0 < 3.0:
+            U.series(Fd, [Pd], (N[2], N[1], N[0]))
+            n += 1
+        el = time.time() - t0
+        cpu = {"value": n / el, "unit": "conv/s", "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": f"{n} single convolutions over {el:.1f} s, series definition (numpy einsum), FP64"}
+    fl = grid_flops(L, N) * B
+    ach = fl / (ms / args.steps / 1e3) / 1e12
+    mhz = clocks.get("sm_mhz") or 2070
+    peak = alu_peak_f32(mhz)
+    in_bytes = 4 * B * L[0] * L[1] * L[2]
+    out_bytes = 4 * B * N[0] * N[1] * N[2]
+    _line("SE(2) convolutions/s, the paper's single-convolution experiment (L=(31,33,61) -> 36x38x76, FP32)",
+          B * args.steps / (ms / 1e3), "conv/s", args, ms,
+          {"workload": f"grid plan, f_H and radial f_U deformed Gaussians, batch {B}, shared kernel",
+           "L": list(L), "N": list(N), "l2": f"inputs {in_bytes / 1e6:.0f} MB + outputs {out_bytes / 1e6:.0f} MB "
+                                            "per step, larger than L2"},
+          {"roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                        "traffic": None, "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops at {mhz:.0f} MHz",
+                        "flops_per_conv": grid_flops(L, N)},
+           "paper_context": "0.0849 s per convolution for the FFT scheme with upsampling (MATLAB, the paper's "
+                            "hardware, not stated); brute-force quadrature 6.8638e3 s",
+           "cpu_baseline": cpu, "gpu_launches": launched, "clocks": clocks})
 
 
 def run_batch(args):

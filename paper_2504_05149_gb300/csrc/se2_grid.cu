@@ -26,6 +26,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <new>
+#include <type_traits>
 
 #include "../../include/se2.h"
 #include "se2_internal.h"
@@ -48,7 +49,6 @@ namespace {
 constexpr int kGridMaxK = 32;      // kernels in one chain
 constexpr int kGridMaxL = 255;     // largest sampling size per axis
 constexpr int kGridMaxN = 1024;    // largest output size per axis
-constexpr int kCols = 32;          // columns (or lines) per block
 constexpr int kGridThreads = 256;
 
 se2_status gfail(se2_status st, const char* fmt, ...) {
@@ -166,74 +166,108 @@ __device__ __forceinline__ long long gaddr(long long q, int inner, long long so)
     return (q / inner) * so + (q % inner);
 }
 
-// Row passes: x forward (real input) and x inverse (real output).
+// Row passes: x forward (real input) and x inverse (real output).  A block
+// holds kRows lines in shared memory.  Work items are (group of 4 lines,
+// output index) pairs, numbered output-fastest, so that the lanes of a warp
+// read neighbouring table entries and write neighbouring outputs whatever
+// the output length; every item accumulates its 4 lines at once, so one
+// table load feeds 4 multiply-adds.
+constexpr int kRows = 64;
+constexpr int kRowGroup = 4;
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kGridThreads) k_grid_rows(GridPass<T> a) {
     extern __shared__ __align__(16) unsigned char g_smem[];
-    const long long q0 = (long long)blockIdx.x * kCols;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (MODE == GM_R2C) {
-        T* s = reinterpret_cast<T*>(g_smem);                              // [kCols][n_in]
-        const T* in = static_cast<const T*>(a.in);
-        for (int idx = tid; idx < kCols * a.n_in; idx += kGridThreads) {
-            const int r = idx / a.n_in, i = idx % a.n_in;
-            const long long q = q0 + r;
-            s[idx] = q < a.Q ? in[q * a.in_so + i * a.in_si] : T(0);
-        }
-        __syncthreads();
-        c2<T>* out = static_cast<c2<T>*>(a.out);
-        for (int r = warp; r < kCols; r += kGridThreads / 32) {
-            const long long q = q0 + r;
-            if (q >= a.Q) break;
-            const T* sr = s + r * a.n_in;
-            for (int j = lane; j < a.n_out; j += 32) {
-                T ar = 0, ai = 0;
-                for (int i = 0; i < a.n_in; ++i) {
-                    const c2<T> e = a.E[(long long)i * a.n_out + j];
-                    ar += e.x * sr[i];
-                    ai += e.y * sr[i];
+    using In = typename std::conditional<MODE == GM_R2C, T, c2<T>>::type;
+    In* s = reinterpret_cast<In*>(g_smem);                                // [kRows][n_in]
+    const long long q0 = (long long)blockIdx.x * kRows;
+    const int tid = threadIdx.x;
+    const In* in = static_cast<const In*>(a.in);
+    for (int idx = tid; idx < kRows * a.n_in; idx += kGridThreads) {
+        const int r = idx / a.n_in, i = idx % a.n_in;
+        const long long q = q0 + r;
+        In v;
+        if constexpr (MODE == GM_R2C) v = T(0); else v = mk<T>(0, 0);
+        if (q < a.Q) v = in[q * a.in_so + i * a.in_si];
+        s[idx] = v;
+    }
+    __syncthreads();
+    const long long left = a.Q - q0;
+    const int groups = (int)((left < kRows ? left : kRows) + kRowGroup - 1) / kRowGroup;
+    for (int w = tid; w < groups * a.n_out; w += kGridThreads) {
+        const int g = w / a.n_out, j = w % a.n_out;
+        const int r0 = g * kRowGroup;
+        const In* sr = s + r0 * a.n_in;
+        const c2<T>* e = a.E + j;
+        if constexpr (MODE == GM_R2C) {
+            T ar[kRowGroup] = {}, ai[kRowGroup] = {};
+            for (int i = 0; i < a.n_in; ++i) {
+                const c2<T> wv = e[(long long)i * a.n_out];
+#pragma unroll
+                for (int rr = 0; rr < kRowGroup; ++rr) {
+                    const T x = sr[rr * a.n_in + i];
+                    ar[rr] += wv.x * x;
+                    ai[rr] += wv.y * x;
                 }
-                out[q * a.out_so + j * a.out_sj] = mk<T>(ar, ai);
             }
-        }
-    } else {  // GM_C2R
-        c2<T>* s = reinterpret_cast<c2<T>*>(g_smem);                      // [kCols][n_in]
-        const c2<T>* in = static_cast<const c2<T>*>(a.in);
-        for (int idx = tid; idx < kCols * a.n_in; idx += kGridThreads) {
-            const int r = idx / a.n_in, i = idx % a.n_in;
-            const long long q = q0 + r;
-            s[idx] = q < a.Q ? in[q * a.in_so + i * a.in_si] : mk<T>(0, 0);
-        }
-        __syncthreads();
-        T* out = static_cast<T*>(a.out);
-        for (int r = warp; r < kCols; r += kGridThreads / 32) {
-            const long long q = q0 + r;
-            if (q >= a.Q) break;
-            const c2<T>* sr = s + r * a.n_in;
-            for (int j = lane; j < a.n_out; j += 32) {
-                T acc = 0;
-                for (int i = 0; i < a.n_in; ++i) {
-                    const c2<T> e = a.E[(long long)i * a.n_out + j];
-                    const c2<T> v = sr[i];
-                    acc += e.x * v.x - e.y * v.y;                   // Re(e v)
+            c2<T>* out = static_cast<c2<T>*>(a.out);
+#pragma unroll
+            for (int rr = 0; rr < kRowGroup; ++rr) {
+                const long long q = q0 + r0 + rr;
+                if (q < a.Q) out[q * a.out_so + j * a.out_sj] = mk<T>(ar[rr], ai[rr]);
+            }
+        } else {
+            T acc[kRowGroup] = {};
+            for (int i = 0; i < a.n_in; ++i) {
+                const c2<T> wv = e[(long long)i * a.n_out];
+#pragma unroll
+                for (int rr = 0; rr < kRowGroup; ++rr) {
+                    const c2<T> v = sr[rr * a.n_in + i];
+                    acc[rr] += wv.x * v.x - wv.y * v.y;                // Re(e v)
                 }
-                out[q * a.out_so + j * a.out_sj] = acc;
+            }
+            T* out = static_cast<T*>(a.out);
+#pragma unroll
+            for (int rr = 0; rr < kRowGroup; ++rr) {
+                const long long q = q0 + r0 + rr;
+                if (q < a.Q) out[q * a.out_so + j * a.out_sj] = acc[rr];
             }
         }
     }
 }
 
 // Column passes: y and theta, forward and inverse; GM_MUL forms the product
-// of the spectra while loading.
+// of the spectra while loading.  A block holds cols_tile<T>() neighbouring
+// columns; each lane owns 2 (FP32) or 1 (FP64) of them and each warp 4
+// outputs at a time, so per input sample a thread issues 2 shared loads and
+// 4 (warp-uniform) table loads for 32 multiply-adds.
+template <typename T>
+constexpr int cols_tile() { return sizeof(T) == 4 ? 64 : 32; }
+constexpr int kOutGroup = 4;
+constexpr size_t kTableSmem = 48 * 1024;   // column-pass tables up to this size sit in shared memory
+
+template <typename T>
+__host__ __device__ inline bool table_in_smem(int n_in, int n_out) {
+    return (size_t)n_in * n_out * sizeof(c2<T>) <= kTableSmem;
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kGridThreads) k_grid_cols(GridPass<T> a) {
+    constexpr int TC = cols_tile<T>(), CPT = TC / 32;
     extern __shared__ __align__(16) unsigned char g_smem[];
-    c2<T>* s = reinterpret_cast<c2<T>*>(g_smem);                          // [n_in][kCols]
-    const long long q0 = (long long)blockIdx.x * kCols;
-    const int tid = threadIdx.x;
+    c2<T>* s = reinterpret_cast<c2<T>*>(g_smem);                          // [n_in][TC]
+    const long long q0 = (long long)blockIdx.x * TC;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const c2<T>* in = static_cast<const c2<T>*>(a.in);
-    for (int idx = tid; idx < kCols * a.n_in; idx += kGridThreads) {
-        const int c = idx % kCols, i = idx / kCols;
+    // the table follows the tile when it is small enough (table_in_smem)
+    const c2<T>* E = a.E;
+    if (table_in_smem<T>(a.n_in, a.n_out)) {
+        c2<T>* es = s + (size_t)TC * a.n_in;
+        for (int idx = tid; idx < a.n_in * a.n_out; idx += kGridThreads) es[idx] = a.E[idx];
+        E = es;
+    }
+    for (int idx = tid; idx < TC * a.n_in; idx += kGridThreads) {
+        const int c = idx % TC, i = idx / TC;
         const long long q = q0 + c;
         c2<T> v = mk<T>(0, 0);
         if (q < a.Q) {
@@ -260,32 +294,62 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_cols(GridPass<T> a) {
     }
     __syncthreads();
     c2<T>* out = static_cast<c2<T>*>(a.out);
-    const int c = tid % kCols, g = tid / kCols;
-    const long long q = q0 + c;
-    if (q >= a.Q) return;
-    const long long obase = gaddr(q, a.inner, a.out_so);
-    for (int j = g; j < a.n_out; j += kGridThreads / kCols) {
-        const c2<T>* e = a.E + (long long)j * a.n_in;
-        T ar = 0, ai = 0;
+    long long obase[CPT];
+    bool ok[CPT];
+    bool any = false;
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+        const long long q = q0 + lane + 32 * cc;
+        ok[cc] = q < a.Q;
+        obase[cc] = ok[cc] ? gaddr(q, a.inner, a.out_so) : 0;
+        any |= ok[cc];
+    }
+    if (!any) return;
+    for (int j0 = warp * kOutGroup; j0 < a.n_out; j0 += (kGridThreads / 32) * kOutGroup) {
+        const c2<T>* e[kOutGroup];
+#pragma unroll
+        for (int r = 0; r < kOutGroup; ++r) e[r] = E + (long long)min(j0 + r, a.n_out - 1) * a.n_in;
+        T ar[kOutGroup][CPT] = {}, ai[kOutGroup][CPT] = {};
+#pragma unroll 4
         for (int i = 0; i < a.n_in; ++i) {
-            const c2<T> w = e[i];
-            const c2<T> v = s[i * kCols + c];
-            ar += w.x * v.x - w.y * v.y;
-            ai += w.x * v.y + w.y * v.x;
+            c2<T> v[CPT];
+#pragma unroll
+            for (int cc = 0; cc < CPT; ++cc) v[cc] = s[i * TC + lane + 32 * cc];
+#pragma unroll
+            for (int r = 0; r < kOutGroup; ++r) {
+                const c2<T> w = e[r][i];
+#pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) {
+                    ar[r][cc] += w.x * v[cc].x - w.y * v[cc].y;
+                    ai[r][cc] += w.x * v[cc].y + w.y * v[cc].x;
+                }
+            }
         }
-        out[obase + j * a.out_sj] = mk<T>(ar * a.out_scale, ai * a.out_scale);
+#pragma unroll
+        for (int r = 0; r < kOutGroup; ++r) {
+            if (j0 + r >= a.n_out) break;
+#pragma unroll
+            for (int cc = 0; cc < CPT; ++cc)
+                if (ok[cc])
+                    out[obase[cc] + (long long)(j0 + r) * a.out_sj] =
+                        mk<T>(ar[r][cc] * a.out_scale, ai[r][cc] * a.out_scale);
+        }
     }
 }
 
 template <typename T>
-size_t pass_smem(int mode, int n_in) {
-    return (size_t)kCols * n_in * (mode == GM_R2C ? sizeof(T) : sizeof(c2<T>));
+size_t pass_smem(int mode, int n_in, int n_out) {
+    if (mode == GM_R2C) return (size_t)kRows * n_in * sizeof(T);
+    if (mode == GM_C2R) return (size_t)kRows * n_in * sizeof(c2<T>);
+    return ((size_t)cols_tile<T>() * n_in + (table_in_smem<T>(n_in, n_out) ? (size_t)n_in * n_out : 0)) *
+           sizeof(c2<T>);
 }
 
 template <typename T>
 cudaError_t launch_pass(se2_grid_plan_s* p, int mode, const GridPass<T>& a, cudaStream_t s) {
-    const size_t sm = pass_smem<T>(mode, a.n_in);
-    const unsigned blocks = (unsigned)((a.Q + kCols - 1) / kCols);
+    const size_t sm = pass_smem<T>(mode, a.n_in, a.n_out);
+    const int tile = (mode == GM_R2C || mode == GM_C2R) ? kRows : cols_tile<T>();
+    const unsigned blocks = (unsigned)((a.Q + tile - 1) / tile);
     if (blocks == 0) return cudaSuccess;
     switch (mode) {
         case GM_R2C: k_grid_rows<T, GM_R2C><<<blocks, kGridThreads, sm, s>>>(a); break;
@@ -297,9 +361,18 @@ cudaError_t launch_pass(se2_grid_plan_s* p, int mode, const GridPass<T>& a, cuda
     return cudaGetLastError();
 }
 
+// Largest dynamic shared memory any pass asks for: rows of up to 255 real or
+// 128 complex samples, columns of up to 255 samples.
+template <typename T>
+int max_pass_smem() {
+    const size_t a = pass_smem<T>(GM_R2C, kGridMaxL, 1), b = pass_smem<T>(GM_C2R, (kGridMaxL - 1) / 2 + 1, 1),
+                 c = (size_t)cols_tile<T>() * kGridMaxL * sizeof(c2<T>) + kTableSmem;
+    return (int)(a > b ? (a > c ? a : c) : (b > c ? b : c));
+}
+
 template <typename T>
 cudaError_t set_smem_attrs() {
-    const int big = (int)(kCols * kGridMaxL * sizeof(c2<T>));
+    const int big = max_pass_smem<T>();
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_grid_rows<T, GM_R2C>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_grid_rows<T, GM_C2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
