@@ -379,6 +379,20 @@ se2_status se2_grid_coeffs(se2_grid_plan_t plan, const void* samples, int n, voi
 se2_status se2_grid_convolve_chain(se2_grid_plan_t plan, const void* f, int B, const void* const* coeffs, int k,
                                    void* out, void* stream);
 
+/*
+ * se2_accuracy_order -- Algorithm 1 (Section 4.2; Theorem fkLmain and the
+ * remark after it): the smallest K in N with
+ *   K >= max(c ||grad f||_inf / eps, ||k||_inf),
+ * so that the finite Fourier coefficient f^[k; 2K+1] on the odd grid
+ * L = 2K+1 is within eps of the Fourier coefficient f^[k] for f in C^1
+ * supported in Omega.  c = `constant` if > 0, else the theorem's 32 (its
+ * proof through Theorem UkL gives 36).  Host only; writes *K.  Errors:
+ * SE2_ERR_INVALID_ARG (eps <= 0, grad_inf < 0, k_inf < 0, non-finite input,
+ * NULL K), SE2_ERR_UNSUPPORTED (K beyond 4e18).  A K above 127 exceeds the
+ * grid plans' largest L.
+ */
+se2_status se2_accuracy_order(double eps, double grad_inf, int k_inf, double constant, long long* K);
+
 const char* se2_last_error(void);
 
 /* Library version string. */

@@ -75,6 +75,8 @@ def load_library(path: str = LIB_PATH):
     lib.se2_grid_plan_launches.restype = ctypes.c_ulonglong
     lib.se2_grid_coeffs.argtypes = [vp, vp, ip, vp, vp]
     lib.se2_grid_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ip, vp, vp]
+    lib.se2_accuracy_order.argtypes = [ctypes.c_double, ctypes.c_double, ip, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_longlong)]
     lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
     lib.se2_plan_launches.argtypes = [vp]
     lib.se2_plan_launches.restype = ctypes.c_ulonglong
@@ -85,6 +87,7 @@ def load_library(path: str = LIB_PATH):
                  "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
                  "se2_sample_se2_gaussian", "se2_sample_deformed_gaussian",
                  "se2_grid_plan_create", "se2_grid_plan_destroy", "se2_grid_coeffs", "se2_grid_convolve_chain",
+                 "se2_accuracy_order",
                  "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -421,6 +424,49 @@ def grid_convolve_chain(plan: GridPlan, f: torch.Tensor, Cs: Sequence[torch.Tens
     return out
 
 
+def accuracy_order(eps: float, grad_inf: float, k=(0, 0, 0), constant: float = 32.0) -> int:
+    """Algorithm 1: the smallest K with K >= max(constant ||grad f||_inf / eps,
+    ||k||_inf); f^[k; 2K+1] is then within eps of f^[k] (Theorem fkLmain)."""
+    K = ctypes.c_longlong()
+    _check(load_library().se2_accuracy_order(float(eps), float(grad_inf), int(max(abs(int(v)) for v in k)),
+                                             float(constant), ctypes.byref(K)))
+    return int(K.value)
+
+
+def ffc_at(plan: GridPlan, C: torch.Tensor, k, index: int = 0) -> complex:
+    """f^[k; L] = (-1)^(k1+k2) C(tau(k)) (Eq. FkLv) read from grid coefficients
+    C = DFT(P)/|L| ([n, Lr, Ly, Kx+1]) of real samples; k = (k1, k2, k3) with
+    |k_i| <= K_i.  Negative k1 use the Hermitian partner."""
+    k1, k2, k3 = (int(v) for v in k)
+    Kx, Ky, Kr = (plan.Lx - 1) // 2, (plan.Ly - 1) // 2, (plan.Lr - 1) // 2
+    if abs(k1) > Kx or abs(k2) > Ky or abs(k3) > Kr:
+        raise ValueError(f"k = {k} outside |k| <= K = ({Kx}, {Ky}, {Kr})")
+    conj = k1 < 0
+    if conj:
+        k1, k2, k3 = -k1, -k2, -k3
+    v = complex(C[index, k3 % plan.Lr, k2 % plan.Ly, k1].item())
+    if conj:
+        v = v.conjugate()
+    return -v if (k1 + k2) % 2 else v
+
+
+def ffc_convergence(sample, k, Ks, precision: str = "f64", device: Optional[int] = None):
+    """FFC convergence report (Corollary fkOK): f^[k; 2K+1] for each K in Ks,
+    computed on the GPU from `sample(L)` ([Lr, Ly, Lx] samples on Omega_L,
+    L = (2K+1,)*3).  Returns [(K, value, |value - previous value|)]."""
+    out, prev = [], None
+    for K in Ks:
+        L = 2 * int(K) + 1
+        plan = GridPlan((L, L, L), batch=1, precision=precision, device=device)
+        dev = torch.device("cuda", plan.device)
+        P = torch.as_tensor(sample((L, L, L)), dtype=plan.dtype).reshape(1, L, L, L).contiguous().to(dev)
+        v = ffc_at(plan, grid_coeffs(plan, P), k)
+        out.append((int(K), v, None if prev is None else abs(v - prev)))
+        prev = v
+        plan.close()
+    return out
+
+
 def table_len(plan: Plan) -> int:
     return plan.N // 2 + 1 + plan.N + plan.M
 
@@ -488,6 +534,6 @@ class SE2Conv(torch.autograd.Function):
 __all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_chain", "convolve_chain_all",
            "backward",
            "sample_radial_gaussian", "sample_se2_gaussian", "sample_deformed_gaussian",
-           "GridPlan", "grid_coeffs", "grid_convolve_chain",
+           "GridPlan", "grid_coeffs", "grid_convolve_chain", "accuracy_order", "ffc_at", "ffc_convergence",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
            "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO"]

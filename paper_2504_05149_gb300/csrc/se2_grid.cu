@@ -24,6 +24,7 @@
 
 #include <cstdarg>
 #include <cstdint>
+#include <cmath>
 #include <cstdio>
 #include <new>
 #include <type_traits>
@@ -548,6 +549,23 @@ se2_status se2_grid_plan_destroy(se2_grid_plan_t p) {
 }
 
 unsigned long long se2_grid_plan_launches(se2_grid_plan_t p) { return p ? p->launches : 0ull; }
+
+se2_status se2_accuracy_order(double eps, double grad_inf, int k_inf, double constant, long long* K) {
+    if (K == nullptr) return gfail(SE2_ERR_INVALID_ARG, "K is NULL");
+    *K = 0;
+    if (!(eps > 0) || !(eps < 1e300)) return gfail(SE2_ERR_INVALID_ARG, "eps=%g must be finite and > 0", eps);
+    if (!(grad_inf >= 0) || !(grad_inf < 1e300))
+        return gfail(SE2_ERR_INVALID_ARG, "grad_inf=%g must be finite and >= 0", grad_inf);
+    if (k_inf < 0) return gfail(SE2_ERR_INVALID_ARG, "k_inf=%d must be >= 0", k_inf);
+    const double c = constant > 0 ? constant : 32.0;   // Theorem fkLmain's constant
+    const double beta = c * grad_inf / eps;
+    if (!(beta < 4.0e18)) return gfail(SE2_ERR_UNSUPPORTED, "K = %g does not fit", beta);
+    long long k = (long long)ceil(beta);
+    if (k < k_inf) k = k_inf;
+    if (k < 1) k = 1;                                    // K in N
+    *K = k;
+    return SE2_OK;
+}
 
 se2_status se2_grid_coeffs(se2_grid_plan_t p, const void* samples, int n, void* coeffs, void* stream) {
     se2_status st = check_gplan(p);

@@ -93,3 +93,27 @@ def test_grid_plan_rejects_bad_sizes_on_host(lib, L, N, status):
                                          ctypes.c_int]
     assert lib.se2_grid_plan_create(ctypes.byref(h), i3(*L), i3(*N), 1, 1, 0, 0) == status
     assert not h.value
+
+
+@pytest.mark.parametrize("eps,grad,kinf,c,want", [
+    (0.5, 1.0, 0, 0.0, 64),        # 32 * 1 / 0.5
+    (3.0, 1.0, 0, 0.0, 11),        # ceil(10.67)
+    (3.0, 1.0, 40, 0.0, 40),       # ||k||_inf dominates
+    (1.0, 0.0, 0, 0.0, 1),         # K in N
+    (0.5, 1.0, 0, 36.0, 72),       # the proof's constant
+])
+def test_accuracy_order_algorithm1_on_host(lib, eps, grad, kinf, c, want):
+    lib.se2_accuracy_order.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_longlong)]
+    K = ctypes.c_longlong(-1)
+    assert lib.se2_accuracy_order(eps, grad, kinf, c, ctypes.byref(K)) == 0
+    assert K.value == want
+
+
+@pytest.mark.parametrize("eps,grad,kinf", [(0.0, 1.0, 0), (-1.0, 1.0, 0), (1.0, -1.0, 0), (1.0, 1.0, -2),
+                                           (float("nan"), 1.0, 0), (1.0, float("inf"), 0)])
+def test_accuracy_order_rejects_bad_input(lib, eps, grad, kinf):
+    lib.se2_accuracy_order.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_longlong)]
+    K = ctypes.c_longlong(-1)
+    assert lib.se2_accuracy_order(eps, grad, kinf, 0.0, ctypes.byref(K)) == 1
