@@ -349,6 +349,7 @@ typedef struct se2_grid_plan_s* se2_grid_plan_t;
  * precision SE2_F32 or SE2_F64; flags 0 or SE2_SHARED_KERNEL (one coefficient
  * array per kernel for the whole batch).  Allocates the DFT tables (FP64
  * sincospi, rounded) and 2 * batch * Nr * Ny * (Kx+1) complex of workspace.
+ * Calls on one grid plan share that workspace: order them on one stream.
  * Errors: SE2_ERR_UNSUPPORTED (even L, precision, flags), SE2_ERR_INVALID_ARG
  * (N < L, batch, device), SE2_ERR_OOM; *plan is NULL on failure.
  */
