@@ -129,3 +129,33 @@ def test_grid_plan_errors(se2):
     f = torch.zeros((2, 5, 5, 5), device="cuda")
     with pytest.raises(se2.SE2Error):
         se2.grid_convolve_chain(plan, f, [])          # B above the plan's batch
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("L,N", [
+    ((255, 3, 5), (1024, 3, 5)),     # largest sampling and output sizes along x
+    ((3, 255, 5), (3, 1024, 5)),     # along y (FP64 column tile with the table in global memory)
+    ((5, 3, 255), (5, 4, 1024)),     # along theta
+])
+def test_grid_largest_sizes(se2, prec, L, N):
+    plan = se2.GridPlan(L, N, batch=1, precision=prec)
+    rng = np.random.default_rng(sum(L))
+    F = _round(rng.standard_normal(L[::-1]), prec)
+    P = _round(rng.standard_normal(L[::-1]), prec)
+    C = se2.grid_coeffs(plan, _dev(P[None], prec))
+    out = se2.grid_convolve_chain(plan, _dev(F[None], prec), [C])[0].double().cpu().numpy()
+    want = U.series(F, [P], N[::-1]).real
+    assert _rel(out, want) < {"f32": 1e-5, "f64": 1e-10}[prec]
+
+
+def test_grid_longest_chain(se2):
+    """k = 32 kernels (the largest chain), batch 2 with per-problem kernels."""
+    L, N = (5, 7, 9), (6, 8, 10)
+    B, k = 2, 32
+    plan = se2.GridPlan(L, N, batch=B, precision="f64")
+    Fs = [deformed(L, [[30, 0], [0, 60]], 1.0 + b, 0.3) for b in range(B)]
+    Ps = [[1.0 + 0.1 * se2_gauss(L, 0.01 + 0.0005 * t, 0.05 * t + b) for t in range(k)] for b in range(B)]
+    Cs = [se2.grid_coeffs(plan, _dev(np.stack([Ps[b][t] for b in range(B)]), "f64")) for t in range(k)]
+    out = se2.grid_convolve_chain(plan, _dev(np.stack(Fs), "f64"), Cs).cpu().numpy()
+    for b in range(B):
+        assert _rel(out[b], U.series(Fs[b], Ps[b], N[::-1]).real) < 1e-10
