@@ -387,7 +387,7 @@ class GridPlan:
     def spec_shape(self, B: int):
         return (B, self.Lr, self.Ly, self.Hx)
 
-    def _check(self, t: torch.Tensor, name: str, shape_tail, dtype) -> int:
+    def _check_tensor(self, t: torch.Tensor, name: str, shape_tail, dtype) -> int:
         if t.dim() != 4 or tuple(t.shape[1:]) != tuple(shape_tail):
             raise ValueError(f"{name}: expected [B, {', '.join(map(str, shape_tail))}], got {tuple(t.shape)}")
         if t.dtype != dtype or not t.is_cuda or t.device.index != self.device or not t.is_contiguous():
@@ -397,7 +397,7 @@ class GridPlan:
 
 def grid_coeffs(plan: GridPlan, samples: torch.Tensor) -> torch.Tensor:
     """C = DFT(P)/|L| of [n, Lr, Ly, Lx] real samples: [n, Lr, Ly, Kx+1] complex."""
-    n = plan._check(samples, "samples", plan.sample_shape(1)[1:], plan.dtype)
+    n = plan._check_tensor(samples, "samples", plan.sample_shape(1)[1:], plan.dtype)
     C = torch.empty(plan.spec_shape(n), dtype=plan.cdtype, device=samples.device)
     _check(load_library().se2_grid_coeffs(plan.handle, _ptr(samples), n, _ptr(C), _stream(samples.device)))
     return C
@@ -407,14 +407,14 @@ def grid_convolve_chain(plan: GridPlan, f: torch.Tensor, Cs: Sequence[torch.Tens
                         out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Re S_K[f, rho_1..rho_k] on the N-grid ([B, Nr, Ny, Nx]); k = 0 gives the
     finite Fourier series S_K[f] itself."""
-    B = plan._check(f, "f", plan.sample_shape(1)[1:], plan.dtype)
+    B = plan._check_tensor(f, "f", plan.sample_shape(1)[1:], plan.dtype)
     if out is None:
         out = torch.empty(plan.out_shape(B), dtype=plan.dtype, device=f.device)
     else:
-        plan._check(out, "out", plan.out_shape(1)[1:], plan.dtype)
+        plan._check_tensor(out, "out", plan.out_shape(1)[1:], plan.dtype)
     nb = 1 if plan.flags & SHARED_KERNEL else B
     for i, C in enumerate(Cs):
-        plan._check(C, f"coeffs[{i}]", plan.spec_shape(1)[1:], plan.cdtype)
+        plan._check_tensor(C, f"coeffs[{i}]", plan.spec_shape(1)[1:], plan.cdtype)
         if C.shape[0] != nb:
             raise ValueError(f"coeffs[{i}]: expected {nb} arrays, got {C.shape[0]}")
     k = len(Cs)
