@@ -27,7 +27,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-N_DEF, M_DEF, B_DEF = 256, 64, 16
+N_DEF, M_DEF = 256, 64
+B_SINGLE, B_CHAIN = 64, 16   # default batches: single convolutions, 8-fold chains
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 
@@ -38,7 +39,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=B_DEF)
+    ap.add_argument("--batch", type=int, default=None,
+                    help=f"problems per step (default {B_SINGLE} for c2, {B_CHAIN} for c2chain/c2all)")
     ap.add_argument("--N", type=int, default=N_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -202,6 +204,8 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.batch is None:
+        args.batch = B_CHAIN if args.config in ("c2chain", "c2all") else B_SINGLE
     if args.impl == "reference":
         run_reference(args)
         return
