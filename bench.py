@@ -52,8 +52,8 @@ def parse():
                          "output on 36 x 38 x 76 (grid plan, odd sizes, upsampled)")
     ap.add_argument("--grid-batch", type=int, default=1024, help="e4 batch size")
     ap.add_argument("--problems", type=int, default=4096, help="c4 batch size")
-    ap.add_argument("--precision", default="f32", choices=["f32", "split_bf16", "bf16"],
-                    help="c2: arithmetic of the angular DFT (tensor cores for split_bf16 / bf16)")
+    ap.add_argument("--precision", default="f32", choices=["f32", "split_bf16", "split_f16", "bf16"],
+                    help="c2: arithmetic of the angular DFT (tensor cores for split_bf16 / split_f16 / bf16)")
     return ap.parse_args()
 
 
@@ -595,7 +595,7 @@ def run_precision(args):
     params = params.to(dev)
     kk = torch.full((B,), K, dtype=torch.int32, device=dev)
     res = {}
-    for prec in ("split_bf16", "f32"):
+    for prec in ("split_bf16", "split_f16", "f32"):
         plan = se2.Plan(N, M, batch=B, precision=prec)
         tab = se2.separable_tables(plan, params, kk)
         out = torch.empty_like(f)
@@ -615,8 +615,8 @@ def run_precision(args):
           v, "conv/s", args, ms,
           {"workload": "batch 8, 32-bump f1 with amplitudes log-uniform in [1e-6, 1], 32-fold separable chain",
            "grid": [M, N, N]},
-          {"fp32_value": res["f32"][0], "max_rel_err_vs_fp64_oracle": err, "clocks": clocks,
-           "gpu_launches": 5 * args.steps})
+          {"fp32_value": res["f32"][0], "split_f16_value": res["split_f16"][0], "max_rel_err_vs_fp64_oracle": err,
+           "clocks": clocks, "gpu_launches": 5 * args.steps})
 
 
 def run_adjoint(args):

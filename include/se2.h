@@ -62,7 +62,10 @@ typedef enum {
     SE2_SPLIT_BF16 = 2,       /* float storage; the angular DFT (M = 64, 128)
                                  runs on the tensor cores with bf16 hi + lo
                                  operands (3 products), FP32 accumulation      */
-    SE2_BF16 = 3              /* as SE2_SPLIT_BF16 with one bf16 product      */
+    SE2_BF16 = 3,             /* as SE2_SPLIT_BF16 with one bf16 product      */
+    SE2_SPLIT_F16 = 4         /* as SE2_SPLIT_BF16 with fp16 hi + lo operands;
+                                 each line scaled by a power of two into the
+                                 fp16 range first (about 22 bits kept)        */
 } se2_precision;
 
 /* Plan flags */

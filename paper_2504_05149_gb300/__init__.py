@@ -25,7 +25,8 @@ F64 = 0
 F32 = 1
 SPLIT_BF16 = 2
 BF16 = 3
-_PRECISIONS = {"f64": F64, "f32": F32, "split_bf16": SPLIT_BF16, "bf16": BF16}
+SPLIT_F16 = 4
+_PRECISIONS = {"f64": F64, "f32": F32, "split_bf16": SPLIT_BF16, "bf16": BF16, "split_f16": SPLIT_F16}
 SHARED_KERNEL = 0x1
 PERSISTENT = 0x2
 GRID_ORIGIN_ZERO = 0x4        # grids sampled at x_i = i/N: the plain cyclic convolution (no W)

@@ -176,20 +176,22 @@ se2_status plan_init(se2_plan_s* p) {
         p->persist_grid = per_sm * nsm;
     }
     p->elem = sizeof(c2<T>);
-    if (p->prec == SE2_SPLIT_BF16 || p->prec == SE2_BF16) {
-        p->tc = p->prec == SE2_SPLIT_BF16 ? 3 : 1;
+    if (p->prec == SE2_SPLIT_BF16 || p->prec == SE2_BF16 || p->prec == SE2_SPLIT_F16) {
+        p->tc = p->prec == SE2_BF16 ? 1 : 3;
+        const int fmt = p->prec == SE2_SPLIT_F16 ? 1 : 0;
         p->fused = false;                    // x and theta as separate passes
         p->persist = false;
-        if (!tc_kernel(p->M, -1, p->tc, &p->tc_fwd, &p->tc_smem) || !tc_kernel(p->M, +1, p->tc, &p->tc_inv, &p->tc_smem))
+        if (!tc_kernel(p->M, -1, p->tc, fmt, &p->tc_fwd, &p->tc_smem) ||
+            !tc_kernel(p->M, +1, p->tc, fmt, &p->tc_inv, &p->tc_smem))
             return fail(SE2_ERR_UNSUPPORTED, "tensor-core angular DFT needs M = 64 or 128 (M=%d)", p->M);
         cudaError_t r = cudaFuncSetAttribute((const void*)p->tc_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->tc_smem);
         if (r == cudaSuccess)
             r = cudaFuncSetAttribute((const void*)p->tc_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->tc_smem);
         if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
         std::vector<unsigned char> img, all;
-        tc_dft_matrix(-1, img);
+        tc_dft_matrix(-1, fmt, img);
         all.insert(all.end(), img.begin(), img.end());
-        tc_dft_matrix(+1, img);
+        tc_dft_matrix(+1, fmt, img);
         all.insert(all.end(), img.begin(), img.end());
         r = cudaMalloc(&p->tcB, all.size());
         if (r != cudaSuccess) return fail(SE2_ERR_OOM, "tensor-core DFT matrix: %s", cudaGetErrorString(r));
@@ -708,7 +710,8 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (!is_pow2(N) || N < 8 || N > 512) return fail(SE2_ERR_UNSUPPORTED, "N=%d: need a power of two in [8, 512]", N);
     if (!is_pow2(M) || M < 2 || M > 128) return fail(SE2_ERR_UNSUPPORTED, "M=%d: need a power of two in [2, 128]", M);
     if (batch < 1) return fail(SE2_ERR_INVALID_ARG, "batch=%d must be >= 1", batch);
-    if (precision != SE2_F32 && precision != SE2_F64 && precision != SE2_SPLIT_BF16 && precision != SE2_BF16)
+    if (precision != SE2_F32 && precision != SE2_F64 && precision != SE2_SPLIT_BF16 && precision != SE2_BF16 &&
+        precision != SE2_SPLIT_F16)
         return fail(SE2_ERR_UNSUPPORTED, "precision %d not supported", (int)precision);
     if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT | SE2_GRID_ORIGIN_ZERO))
         return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);

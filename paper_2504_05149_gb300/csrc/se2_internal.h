@@ -68,8 +68,8 @@ bool get_fast(int N, int M, FastTable* t);   // se2_capi.cu
 // Tensor-core angular DFT (se2_tc.cu).
 struct TcArgs;
 using TcKernel = void (*)(TcArgs);
-bool tc_kernel(int M, int dir, int split, TcKernel* out, size_t* smem);
-void tc_dft_matrix(int dir, std::vector<unsigned char>& img);
+bool tc_kernel(int M, int dir, int split, int fmt, TcKernel* out, size_t* smem);
+void tc_dft_matrix(int dir, int fmt, std::vector<unsigned char>& img);
 
 // Sets the thread-local text returned by se2_last_error().
 void set_last_error(const char* msg);

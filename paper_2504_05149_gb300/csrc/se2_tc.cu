@@ -8,27 +8,26 @@
 
 namespace se2 {
 
-bool tc_kernel(int M, int dir, int split, TcKernel* out, size_t* smem) {
-    TcKernel k = nullptr;
-    size_t sm = 0;
-    if (M == 64 && dir < 0 && split == 3) { k = k_theta_tc<64, -1, 3>; sm = tc_smem<64, 3>(); }
-    else if (M == 64 && dir > 0 && split == 3) { k = k_theta_tc<64, +1, 3>; sm = tc_smem<64, 3>(); }
-    else if (M == 64 && dir < 0 && split == 1) { k = k_theta_tc<64, -1, 1>; sm = tc_smem<64, 1>(); }
-    else if (M == 64 && dir > 0 && split == 1) { k = k_theta_tc<64, +1, 1>; sm = tc_smem<64, 1>(); }
-    else if (M == 128 && dir < 0 && split == 3) { k = k_theta_tc<128, -1, 3>; sm = tc_smem<128, 3>(); }
-    else if (M == 128 && dir > 0 && split == 3) { k = k_theta_tc<128, +1, 3>; sm = tc_smem<128, 3>(); }
-    else if (M == 128 && dir < 0 && split == 1) { k = k_theta_tc<128, -1, 1>; sm = tc_smem<128, 1>(); }
-    else if (M == 128 && dir > 0 && split == 1) { k = k_theta_tc<128, +1, 1>; sm = tc_smem<128, 1>(); }
-    else return false;
-    *out = k;
-    *smem = sm;
-    return true;
+template <int M, int FMT>
+static bool tc_pick(int dir, int split, TcKernel* k, size_t* sm) {
+    if (dir < 0 && split == 3) { *k = k_theta_tc<M, -1, 3, FMT>; *sm = tc_smem<M, 3>(); return true; }
+    if (dir > 0 && split == 3) { *k = k_theta_tc<M, +1, 3, FMT>; *sm = tc_smem<M, 3>(); return true; }
+    if (FMT == 0 && dir < 0 && split == 1) { *k = k_theta_tc<M, -1, 1, 0>; *sm = tc_smem<M, 1>(); return true; }
+    if (FMT == 0 && dir > 0 && split == 1) { *k = k_theta_tc<M, +1, 1, 0>; *sm = tc_smem<M, 1>(); return true; }
+    return false;
+}
+
+bool tc_kernel(int M, int dir, int split, int fmt, TcKernel* out, size_t* smem) {
+    if (M == 64) return fmt == 0 ? tc_pick<64, 0>(dir, split, out, smem) : tc_pick<64, 1>(dir, split, out, smem);
+    if (M == 128) return fmt == 0 ? tc_pick<128, 0>(dir, split, out, smem) : tc_pick<128, 1>(dir, split, out, smem);
+    return false;
 }
 
 // Host image of the constant operand: the real form of the 64-point DFT
-// matrix in direction `dir`, B[n = 2m + a][k = 2l + b], split into bf16 hi and
-// lo, in the K-major core-matrix layout (hi operand, then lo operand).
-void tc_dft_matrix(int dir, std::vector<unsigned char>& img) {
+// matrix in direction `dir`, B[n = 2m + a][k = 2l + b], split into 16-bit hi
+// and lo (bf16 for fmt 0, fp16 for fmt 1), in the K-major core-matrix layout
+// (hi operand, then lo operand).
+void tc_dft_matrix(int dir, int fmt, std::vector<unsigned char>& img) {
     img.assign(2 * kTcOpBytes, 0);
     const double PI = 3.14159265358979323846;
     for (int m = 0; m < 64; ++m)
@@ -39,11 +38,18 @@ void tc_dft_matrix(int dir, std::vector<unsigned char>& img) {
             for (int aa = 0; aa < 2; ++aa)
                 for (int bb = 0; bb < 2; ++bb) {
                     const float v = (float)vals[aa][bb];
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                    const __nv_bfloat16 lo = __float2bfloat16_rn((float)(vals[aa][bb] - (double)__bfloat162float(hi)));
                     const int off = tc_off(2 * m + aa, 2 * l + bb);
-                    std::memcpy(&img[off], &hi, 2);
-                    std::memcpy(&img[kTcOpBytes + off], &lo, 2);
+                    if (fmt == 0) {
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn((float)(vals[aa][bb] - (double)__bfloat162float(hi)));
+                        std::memcpy(&img[off], &hi, 2);
+                        std::memcpy(&img[kTcOpBytes + off], &lo, 2);
+                    } else {
+                        const __half hi = __float2half_rn(v);
+                        const __half lo = __float2half_rn((float)(vals[aa][bb] - (double)__half2float(hi)));
+                        std::memcpy(&img[off], &hi, 2);
+                        std::memcpy(&img[kTcOpBytes + off], &lo, 2);
+                    }
                 }
         }
 }

@@ -13,11 +13,16 @@
 // Split precision: x = x_hi + x_lo and B = B_hi + B_lo in bf16, and
 // D = A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term is below FP32
 // rounding of the accumulation), which keeps about 16 significant bits.
+// The FP16 variant (FMT = 1) splits into fp16 halves instead (about 22
+// significant bits).  fp16 has a narrow exponent range, so every line is
+// scaled by a power of two that puts its largest sample in [2^13, 2^14)
+// before the split, and its outputs are scaled back (exactly) after.
 // M = 64 is one contraction; M = 128 splits even and odd samples into two
 // 64-point contractions and combines them with the radix-2 butterfly
 // Y[m] = E[m] + w^m O[m], Y[m + 64] = E[m] - w^m O[m] in FP32.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "se2_kernels.cuh"
 
@@ -26,7 +31,7 @@ namespace se2 {
 constexpr int kTcLines = 128;            // lines per tile (tensor-memory lanes)
 constexpr int kTcThreads = 256;          // two threads per line
 constexpr int kTcK = 128;                // K of one contraction (64 complex samples)
-constexpr int kTcOpBytes = kTcLines * kTcK * 2;   // one bf16 operand: 32 KB
+constexpr int kTcOpBytes = kTcLines * kTcK * 2;   // one 16-bit operand: 32 KB
 
 // byte offset of element (row r, k) of a K-major no-swizzle bf16 operand with
 // K = kTcK: 8x8 core matrices (8 rows x 16 bytes), K-adjacent core matrices
@@ -47,15 +52,18 @@ __device__ __forceinline__ uint64_t tc_desc(const void* p) {
     d |= (uint64_t)1 << 46;
     return d;
 }
-// Instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major.
-__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: kind::f16, D = f32, both K-major; A and B share
+// one type: bf16 (fmt 0, type code 1) or fp16 (fmt 1, type code 0).
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N, int fmt) {
+    return (1u << 4) | (fmt == 0 ? ((1u << 7) | (1u << 10)) : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
+template <int FMT>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(tc_idesc(kTcLines, kTcK)), "r"(acc));
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(tc_idesc(kTcLines, kTcK, FMT)), "r"(acc));
 }
 
 // 32 consecutive FP32 columns of this warp's 32 lanes.
@@ -82,13 +90,21 @@ struct TcArgs {
     int* err;                  // set to 2 when a wait for the tensor cores gives up
 };
 
-// Split x into bf16 hi + lo.
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+// Split x into 16-bit hi + lo (bf16 for FMT 0, fp16 for FMT 1), as the raw bits.
+template <int FMT>
+__device__ __forceinline__ void split16(float x, uint32_t& hi, uint32_t& lo) {
+    if constexpr (FMT == 0) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+    } else {
+        const __half h = __float2half_rn(x);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+    }
 }
 
-template <int M, int DIR, int SPLIT>
+template <int M, int DIR, int SPLIT, int FMT>
 __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
     static_assert(M == 64 || M == 128, "tensor-core angular DFT: M = 64 or 128");
     constexpr int NPART = (M == 128) ? 2 : 1;              // even / odd contractions
@@ -98,6 +114,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
     unsigned char* sA = smem + (1 + NLO) * kTcOpBytes;     // per part: A_hi [, A_lo]
     __shared__ uint32_t tmem_base;
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ float lmax[kTcThreads];       // FMT 1: per-thread maxima, then per-line scales
+    __shared__ float lscale[kTcLines];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int row = tid % kTcLines, half = tid / kTcLines;   // line of the tile, which half of it
     const int b = blockIdx.y;
@@ -141,6 +159,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
             unsigned char* Ahi = sA + part * (1 + NLO) * kTcOpBytes;
             unsigned char* Alo = Ahi + kTcOpBytes;
             constexpr int lcount = (NPART == 2) ? 64 : 32;   // samples of this thread
+            float sc = 1.f;
+            if constexpr (FMT == 1) {
+                // the line's largest |re|, |im| over both threads' samples
+                float mx = 0.f;
+#pragma unroll 1
+                for (int l0 = lbeg; l0 < lbeg + lcount; l0 += 16) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int l = (l0 + q) * NPART + part;
+                        const float2 w = act ? __ldcg(base + (size_t)l * ls) : make_float2(0.f, 0.f);
+                        mx = fmaxf(mx, fmaxf(fabsf(w.x), fabsf(w.y)));
+                    }
+                }
+                lmax[tid] = mx;
+                __syncthreads();
+                const float lm = fmaxf(lmax[row], lmax[row + kTcLines]);
+                int ex = 0;
+                if (lm > 0.f && lm <= 3.0e38f) frexpf(lm, &ex);     // lm = f 2^ex, f in [0.5, 1)
+                // 2^e and 2^-e stay finite normal floats (subnormal lines are
+                // scaled by 2^126 only; what stays below fp16's range is lost)
+                const int e = lm > 0.f ? min(max(14 - ex, -126), 126) : 0;
+                sc = ldexpf(1.f, e);
+                if (half == 0) lscale[row] = ldexpf(1.f, -e);
+            }
 #pragma unroll 1
             for (int l0 = lbeg; l0 < lbeg + lcount; l0 += 16) {
                 float2 v[16];
@@ -154,12 +196,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
                     uint32_t h[4], o[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        __nv_bfloat16 hr, lr, hi_, li;
-                        split_bf16(v[4 * g + q].x, hr, lr);
-                        split_bf16(v[4 * g + q].y, hi_, li);
+                        uint32_t hr, lr, hi_, li;
+                        split16<FMT>(v[4 * g + q].x * sc, hr, lr);
+                        split16<FMT>(v[4 * g + q].y * sc, hi_, li);
                         // (re, im) -> one 32-bit word, re in the low half (lower address)
-                        h[q] = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi_) << 16);
-                        o[q] = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
+                        h[q] = hr | (hi_ << 16);
+                        o[q] = lr | (li << 16);
                     }
                     const int off = tc_off(row, 2 * (l0 + 4 * g));
                     *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -180,10 +222,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
 #pragma unroll 1
                 for (int kk = 0; kk < kTcK / 16; ++kk) {
                     const int ko = kk * 256;                     // 16 K elements = 2 core matrices
-                    tc_mma(d, tc_desc(Ahi + ko), tc_desc(sB + ko), kk > 0 ? 1u : 0u);
+                    tc_mma<FMT>(d, tc_desc(Ahi + ko), tc_desc(sB + ko), kk > 0 ? 1u : 0u);
                     if (NLO) {
-                        tc_mma(d, tc_desc(Ahi + ko), tc_desc(sB + kTcOpBytes + ko), 1u);
-                        tc_mma(d, tc_desc(Alo + ko), tc_desc(sB + ko), 1u);
+                        tc_mma<FMT>(d, tc_desc(Ahi + ko), tc_desc(sB + kTcOpBytes + ko), 1u);
+                        tc_mma<FMT>(d, tc_desc(Alo + ko), tc_desc(sB + ko), 1u);
                     }
                 }
             }
@@ -206,6 +248,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
         if (ok) {
             const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
             const int cbeg = 64 * half;
+            // this lane's line (tensor-memory lane) and its scale back
+            const float us = FMT == 1 ? lscale[32 * (warp & 3) + (tid & 31)] : 1.f;
             if constexpr (M == 64) {
 #pragma unroll 1
                 for (int c0 = cbeg; c0 < cbeg + 64; c0 += 32) {
@@ -214,7 +258,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
                     if (act) {
 #pragma unroll
                         for (int q = 0; q < 16; ++q)
-                            base[(size_t)(c0 / 2 + q) * ls] = make_float2(v[2 * q], v[2 * q + 1]);
+                            base[(size_t)(c0 / 2 + q) * ls] = make_float2(v[2 * q] * us, v[2 * q + 1] * us);
                     }
                 }
             } else {
@@ -231,8 +275,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
                             const float wr = w.x, wi = (DIR < 0) ? w.y : -w.y;
                             const float orr = o[2 * q] * wr - o[2 * q + 1] * wi;
                             const float oi = o[2 * q] * wi + o[2 * q + 1] * wr;
-                            base[(size_t)m * ls] = make_float2(e[2 * q] + orr, e[2 * q + 1] + oi);
-                            base[(size_t)(m + 64) * ls] = make_float2(e[2 * q] - orr, e[2 * q + 1] - oi);
+                            base[(size_t)m * ls] = make_float2((e[2 * q] + orr) * us, (e[2 * q + 1] + oi) * us);
+                            base[(size_t)(m + 64) * ls] = make_float2((e[2 * q] - orr) * us, (e[2 * q + 1] - oi) * us);
                         }
                     }
                 }

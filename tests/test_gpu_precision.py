@@ -1,7 +1,8 @@
-"""Mixed precision: the angular DFT on the tensor cores (tcgen05, bf16 hi+lo
-split or one bf16 product, FP32 accumulation) against the FP64 oracle, beside
-the plain FP32 path.  Bars: 1e-3 relative for the split-bf16 mode (its error
-is reported, and in practice near 1e-5), 1e-2 for one bf16 product."""
+"""Mixed precision: the angular DFT on the tensor cores (tcgen05, bf16 or
+fp16 hi+lo split, or one bf16 product, FP32 accumulation) against the FP64
+oracle, beside the plain FP32 path.  Bars: 1e-3 relative for the split-bf16
+mode (its error is reported, and in practice near 1e-5), 1e-5 (the FP32 bar)
+for split fp16, 1e-2 for one bf16 product."""
 import numpy as np
 import pytest
 
@@ -32,7 +33,7 @@ def test_split_bf16_and_bf16_vs_oracle(se2, N, M, B):
     F = rng.standard_normal((B, M, N, N)).astype(np.float32)
     P = rng.random((B, M, N, N)).astype(np.float32)
     errs = {}
-    for prec in ("f32", "split_bf16", "bf16"):
+    for prec in ("f32", "split_bf16", "split_f16", "bf16"):
         plan = se2.Plan(N, M, batch=B, precision=prec)
         C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
         out = se2.convolve(plan, torch.from_numpy(F).cuda(), C).double().cpu().numpy()
@@ -40,8 +41,9 @@ def test_split_bf16_and_bf16_vs_oracle(se2, N, M, B):
         errs[prec] = max(_rel(out[b], O.convolve(F[b].astype(np.float64), P[b].astype(np.float64))) for b in range(B))
     assert errs["f32"] < 3e-6
     assert errs["split_bf16"] < 1e-3
+    assert errs["split_f16"] < 1e-5          # the FP32 bar: about 22 bits kept
     assert errs["bf16"] < 2e-2
-    assert errs["split_bf16"] < errs["bf16"]
+    assert errs["split_f16"] < errs["split_bf16"] < errs["bf16"]
     print("max-rel errors", errs)
 
 
@@ -59,12 +61,29 @@ def test_precision_config_chain_log_amplitudes(se2):
         gx, gy, gt = synth.kernel_factors(N, M, kp)
         coeffs.append(O.coeffs_separable(gx, gy, gt))
     want = O.convolve_chain(F.astype(np.float64), None, coeffs=coeffs)
-    for prec, tol in (("f32", 1e-5), ("split_bf16", 1e-3)):
+    for prec, tol in (("f32", 1e-5), ("split_bf16", 1e-3), ("split_f16", 1e-5)):
         plan = se2.Plan(N, M, batch=1, precision=prec)
         tab = se2.separable_tables(plan, params.cuda(), torch.tensor([32], dtype=torch.int32).cuda())
         out = se2.convolve_separable(plan, torch.from_numpy(F[None]).cuda(), tab)[0].double().cpu().numpy()
         plan.status()
         assert _rel(out, want) < tol, prec
+
+
+def test_split_f16_scales_lines_into_range(se2):
+    """Inputs far outside fp16's range (1e8 and 1e-8 amplitudes) keep FP32
+    accuracy: each line is scaled by a power of two before the split."""
+    N, M, B = 64, 64, 2
+    rng = np.random.default_rng(7)
+    F = rng.standard_normal((B, M, N, N)).astype(np.float32)
+    F[0] *= np.float32(1e8)
+    F[1] *= np.float32(1e-8)
+    P = rng.random((B, M, N, N)).astype(np.float32)
+    plan = se2.Plan(N, M, batch=B, precision="split_f16")
+    C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
+    out = se2.convolve(plan, torch.from_numpy(F).cuda(), C).double().cpu().numpy()
+    plan.status()
+    for b in range(B):
+        assert _rel(out[b], O.convolve(F[b].astype(np.float64), P[b].astype(np.float64))) < 1e-5
 
 
 def test_tc_unsupported_angular_size(se2):
