@@ -30,6 +30,7 @@ _PRECISIONS = {"f64": F64, "f32": F32, "split_bf16": SPLIT_BF16, "bf16": BF16, "
 SHARED_KERNEL = 0x1
 PERSISTENT = 0x2
 GRID_ORIGIN_ZERO = 0x4        # grids sampled at x_i = i/N: the plain cyclic convolution (no W)
+MASS_RENORM = 0x8             # FP64 mass renormalisation of convolve / convolve_chain outputs
 
 _STATUS = {0: "SE2_OK", 1: "SE2_ERR_INVALID_ARG", 2: "SE2_ERR_UNSUPPORTED", 3: "SE2_ERR_OOM",
            4: "SE2_ERR_CUDA", 5: "SE2_ERR_TIMEOUT", 6: "SE2_ERR_NUMERIC"}
@@ -537,4 +538,4 @@ __all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_
            "sample_radial_gaussian", "sample_se2_gaussian", "sample_deformed_gaussian",
            "GridPlan", "grid_coeffs", "grid_convolve_chain", "accuracy_order", "ffc_at", "ffc_convergence",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
-           "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO"]
+           "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO", "MASS_RENORM"]

@@ -72,6 +72,7 @@ struct se2_plan_s {
     void* twN = nullptr;
     void* twM = nullptr;
     double* abs_sum = nullptr;  // [chunk]
+    double* mass = nullptr;     // [2 batch]: sum(f), sum(out) (SE2_MASS_RENORM)
     size_t ws_bytes = 0;
     // persistent path
     bool persist = false;
@@ -264,11 +265,47 @@ void plan_free(se2_plan_s* p) {
     if (p->twN) cudaFree(p->twN);
     if (p->twM) cudaFree(p->twM);
     if (p->abs_sum) cudaFree(p->abs_sum);
+    if (p->mass) cudaFree(p->mass);
     p->scratch = p->twN = p->twM = nullptr;
     p->abs_sum = nullptr;
+    p->mass = nullptr;
 }
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+// SE2_MASS_RENORM: FP64 sums of B problems' samples into sums[0..B).
+template <typename T>
+cudaError_t launch_mass_sum(se2_plan_s* p, const void* x, int B, double* sums, cudaStream_t s) {
+    const long long n = (long long)p->N * p->N * p->M;
+    const int bx = (int)((n + 256 * 8 - 1) / (256 * 8) < 64 ? (n + 256 * 8 - 1) / (256 * 8) : 64);
+    k_mass_sum<T><<<dim3(bx, B), 256, 0, s>>>(static_cast<const T*>(x), n, sums);
+    ++p->launches;
+    return cudaGetLastError();
+}
+
+// Then the outputs' sums into p->mass[B..2B) and the correction.
+template <typename T>
+cudaError_t launch_mass_fix(se2_plan_s* p, void* out, int B, const void* const* coeffs,
+                            const double* const* log_scales, int k, cudaStream_t s) {
+    cudaError_t e = launch_mass_sum<T>(p, out, B, p->mass + B, s);
+    if (e != cudaSuccess) return e;
+    MassArgs<T> a = {};
+    const bool shared = (p->flags & SE2_SHARED_KERNEL) != 0;
+    for (int i = 0; i < k; ++i) {
+        a.C[i] = static_cast<const c2<T>*>(coeffs[i]);
+        a.ls[i] = log_scales ? log_scales[i] : nullptr;
+    }
+    a.k = k;
+    a.B = B;
+    a.c_pstride = shared ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
+    a.ls_pstride = shared ? 0 : 1;
+    const long long n = (long long)p->N * p->N * p->M;
+    const long long per_block = 256LL * kMassRun;    // 8 warps x 32 lanes x kMassRun samples
+    const int bx = (int)((n + per_block - 1) / per_block);
+    k_mass_fix<T><<<dim3(bx, B), 256, 0, s>>>(static_cast<T*>(out), n, p->mass, a);
+    ++p->launches;
+    return cudaGetLastError();
+}
 
 // FP64 plans use double kernels; every other precision keeps float storage.
 bool is_f64(const se2_plan_s* p) { return p->prec == SE2_F64; }
@@ -713,7 +750,7 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (precision != SE2_F32 && precision != SE2_F64 && precision != SE2_SPLIT_BF16 && precision != SE2_BF16 &&
         precision != SE2_SPLIT_F16)
         return fail(SE2_ERR_UNSUPPORTED, "precision %d not supported", (int)precision);
-    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT | SE2_GRID_ORIGIN_ZERO))
+    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT | SE2_GRID_ORIGIN_ZERO | SE2_MASS_RENORM))
         return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -783,6 +820,10 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "tables: %s", cudaGetErrorString(e)); }
     e = cudaMalloc((void**)&p->abs_sum, sizeof(double) * chunk);
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "accumulators: %s", cudaGetErrorString(e)); }
+    if (flags & SE2_MASS_RENORM) {
+        e = cudaMalloc((void**)&p->mass, sizeof(double) * 2 * (size_t)batch);
+        if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "mass sums: %s", cudaGetErrorString(e)); }
+    }
     e = cudaMalloc((void**)&p->ctr, sizeof(unsigned) * (1 + 3 * (size_t)batch));
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "counters: %s", cudaGetErrorString(e)); }
     e = cudaMalloc((void**)&p->err, sizeof(int));
@@ -838,8 +879,20 @@ se2_status se2_convolve_chain(se2_plan_t p, const void* f, int B, const void* co
     if (f == out) return fail(SE2_ERR_INVALID_ARG, "out aliases f");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
-    return !is_f64(p) ? run_chain<float>(p, f, B, coeffs, log_scales, k, out, s)
-                              : run_chain<double>(p, f, B, coeffs, log_scales, k, out, s);
+    const bool renorm = (p->flags & SE2_MASS_RENORM) != 0;
+    if (renorm) {
+        cudaError_t e = cudaMemsetAsync(p->mass, 0, sizeof(double) * 2 * (size_t)B, s);
+        if (e == cudaSuccess) e = !is_f64(p) ? launch_mass_sum<float>(p, f, B, p->mass, s)
+                                             : launch_mass_sum<double>(p, f, B, p->mass, s);
+        if (e != cudaSuccess) return cuda_fail(e, "mass sums");
+    }
+    st = !is_f64(p) ? run_chain<float>(p, f, B, coeffs, log_scales, k, out, s)
+                    : run_chain<double>(p, f, B, coeffs, log_scales, k, out, s);
+    if (st != SE2_OK || !renorm) return st;
+    cudaError_t e = !is_f64(p) ? launch_mass_fix<float>(p, out, B, coeffs, log_scales, k, s)
+                               : launch_mass_fix<double>(p, out, B, coeffs, log_scales, k, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mass renormalisation");
+    return SE2_OK;
 }
 
 se2_status se2_convolve_host(se2_plan_t p, const void* f, int B, const void* coeffs, const double* log_scale,

@@ -824,6 +824,65 @@ __global__ void k_gauss_fill(const double* tab, int N, int M, T* P, T* dPs, T* d
 }
 
 // ---------------------------------------------------------------------------
+// Mass renormalisation (FP64).  k_mass_sum adds each problem's samples into
+// sums[b] (grid: (blocks, B)); k_mass_fix adds (target - sum(out)) / n to
+// every sample of problem b, target = sum(f) C_1[0] ... C_k[0] exp(sum ls).
+// Adding one constant to samples already on the T grid would round the same
+// way within a binade, so the total would drift by up to n/2 ulp; each lane
+// therefore carries its rounding residual along its kMassRun samples (error
+// feedback), which leaves at most half an ulp per lane.
+// ---------------------------------------------------------------------------
+constexpr int kMassRun = 256;   // samples per lane in k_mass_fix
+template <typename T>
+__global__ void k_mass_sum(const T* x, long long n, double* sums) {
+    __shared__ double red[32];
+    const T* xb = x + (size_t)blockIdx.y * n;
+    double acc = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        acc += (double)xb[e];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(sums + blockIdx.y, t);
+    }
+}
+
+template <typename T>
+struct MassArgs {
+    const c2<T>* C[32];
+    const double* ls[32];
+    int k, B;
+    long long c_pstride, ls_pstride;
+};
+
+template <typename T>
+__global__ void k_mass_fix(T* out, long long n, const double* sums, MassArgs<T> a) {
+    const int b = blockIdx.y;
+    double prod = 1.0, lsum = 0.0;
+    for (int i = 0; i < a.k; ++i) {
+        prod *= (double)a.C[i][(size_t)b * a.c_pstride].x;
+        if (a.ls[i] != nullptr) lsum += a.ls[i][(size_t)b * a.ls_pstride];
+    }
+    const double delta = (sums[b] * prod * exp(lsum) - sums[a.B + b]) / (double)n;
+    T* ob = out + (size_t)b * n;
+    // warp w of the grid row owns the segment [w * 32 * kMassRun, +32 * kMassRun)
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long seg = w * 32 * kMassRun + (threadIdx.x & 31);
+    double carry = 0.0;
+    for (int i = 0; i < kMassRun; ++i) {
+        const long long e = seg + 32LL * i;
+        if (e >= n) break;
+        const double v = (double)ob[e] + delta + carry;
+        const T r = (T)v;
+        carry = v - (double)r;
+        ob[e] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Analytic inputs of the paper's experiments, sampled in FP64 on the plan's
 // grid: the Gaussian on SE(2) (Section 5, Eq. fbS; Eq. gbS0 is the case
 // beta = (0, R_nu), Sigma = sigma^2 I) and the 3D deformed Gaussian (Eq. fHsnu).

@@ -90,3 +90,36 @@ def test_tc_unsupported_angular_size(se2):
     with pytest.raises(se2.SE2Error) as ei:
         se2.Plan(64, 32, batch=1, precision="split_bf16")
     assert ei.value.status == 2
+
+
+@pytest.mark.parametrize("prec,k,shared", [("split_bf16", 1, False), ("bf16", 1, True), ("f32", 8, False)])
+def test_mass_renormalisation(se2, prec, k, shared):
+    """SE2_MASS_RENORM: sum(out) equals sum(f) * prod C_i[0] * exp(sum ls) to
+    FP64 rounding (the exact DC of the product), while the samples stay
+    within the mode's error bar."""
+    N, M, B = 64, 64, 2
+    rng = np.random.default_rng(11 + k)
+    F = (rng.random((B, M, N, N)) + 0.5).astype(np.float32)
+    Ps = [(rng.random((1 if shared else B, M, N, N)) * (10.0 ** i)).astype(np.float32) for i in range(k)]
+    flags = se2.MASS_RENORM | (se2.SHARED_KERNEL if shared else 0)
+    outs = {}
+    for fl in (0, flags):
+        plan = se2.Plan(N, M, batch=B, precision=prec, flags=fl | (se2.SHARED_KERNEL if shared else 0))
+        Cs, Ls = [], []
+        for P in Ps:
+            C, ls = se2.coeffs(plan, torch.from_numpy(P).cuda(), normalize=True)
+            Cs.append(C)
+            Ls.append(ls)
+        outs[fl] = se2.convolve_chain(plan, torch.from_numpy(F).cuda(), Cs, Ls).double().cpu().numpy()
+        plan.status()
+        cdc = [C[:, 0, 0, 0].real.double().cpu().numpy() * np.exp(l.cpu().numpy()) for C, l in zip(Cs, Ls)]
+    tol = {"split_bf16": 1e-3, "bf16": 2e-2, "f32": 1e-5}[prec]
+    for b in range(B):
+        bb = 0 if shared else b
+        target = F[b].astype(np.float64).sum() * np.prod([c[bb] for c in cdc])
+        got = outs[flags][b].sum()
+        assert abs(got - target) <= 1e-9 * abs(target)   # FP32 rounding of the stored samples
+        want = O.convolve_chain(F[b].astype(np.float64), [P[bb].astype(np.float64) for P in Ps])
+        assert _rel(outs[flags][b], want) < tol
+        # without the flag the mass carries the mode's rounding
+        assert abs(outs[0][b].sum() - target) >= abs(got - target)
