@@ -391,6 +391,18 @@ se2_status se2_grid_convolve_chain(se2_grid_plan_t plan, const void* f, int B, c
                                    void* out, void* stream);
 
 /*
+ * se2_grid_sample_se2_gaussian / se2_grid_sample_deformed_gaussian -- the
+ * samplers of se2_sample_se2_gaussian (Eq. fbS) and
+ * se2_sample_deformed_gaussian (Eq. fHsnu) on a grid plan's sampling grid
+ * Omega_L: P is [Lr][Ly][Lx] of the plan's real type (device).  Arguments
+ * and errors as for the square-grid samplers.
+ */
+se2_status se2_grid_sample_se2_gaussian(se2_grid_plan_t plan, const double* beta, const double* Sigma, int images,
+                                        void* P, void* stream);
+se2_status se2_grid_sample_deformed_gaussian(se2_grid_plan_t plan, const double* H, double nu, double s, int images,
+                                             void* P, void* stream);
+
+/*
  * se2_accuracy_order -- Algorithm 1 (Section 4.2; Theorem fkLmain and the
  * remark after it): the smallest K in N with
  *   K >= max(c ||grad f||_inf / eps, ||k||_inf),

@@ -77,6 +77,8 @@ def load_library(path: str = LIB_PATH):
     lib.se2_grid_plan_launches.restype = ctypes.c_ulonglong
     lib.se2_grid_coeffs.argtypes = [vp, vp, ip, vp, vp]
     lib.se2_grid_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ip, vp, vp]
+    lib.se2_grid_sample_se2_gaussian.argtypes = [vp, dptr, dptr, ctypes.c_int, vp, vp]
+    lib.se2_grid_sample_deformed_gaussian.argtypes = [vp, dptr, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
     lib.se2_accuracy_order.argtypes = [ctypes.c_double, ctypes.c_double, ip, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_longlong)]
     lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
@@ -89,7 +91,7 @@ def load_library(path: str = LIB_PATH):
                  "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
                  "se2_sample_se2_gaussian", "se2_sample_deformed_gaussian",
                  "se2_grid_plan_create", "se2_grid_plan_destroy", "se2_grid_coeffs", "se2_grid_convolve_chain",
-                 "se2_accuracy_order",
+                 "se2_accuracy_order", "se2_grid_sample_se2_gaussian", "se2_grid_sample_deformed_gaussian",
                  "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -307,33 +309,41 @@ def _host_doubles(vals, n: int, name: str):
     return (ctypes.c_double * n)(*[float(v) for v in vals])
 
 
-def sample_se2_gaussian(plan: Plan, beta=(0.0, 0.0, 0.0), Sigma=None, sigma2: float | None = None,
-                        images: int = 1):
-    """The Gaussian on SE(2) (Eq. fbS) with mean beta = (b1, b2, nu) and
-    covariance Sigma (3x3), or Sigma = sigma2 * I (the kernel of Eq. gbS0
-    shifted by nu), sampled on the plan's grid ([1, M, N, N])."""
+def _sigma_list(Sigma, sigma2):
     if (Sigma is None) == (sigma2 is None):
         raise ValueError("give exactly one of Sigma and sigma2")
     if Sigma is None:
-        S = [float(sigma2) if r == c else 0.0 for r in range(3) for c in range(3)]
-    else:
-        S = [float(v) for row in Sigma for v in row]
+        return [float(sigma2) if r == c else 0.0 for r in range(3) for c in range(3)]
+    return [float(v) for row in Sigma for v in row]
+
+
+def sample_se2_gaussian(plan, beta=(0.0, 0.0, 0.0), Sigma=None, sigma2: float | None = None, images: int = 1):
+    """The Gaussian on SE(2) (Eq. fbS) with mean beta = (b1, b2, nu) and
+    covariance Sigma (3x3), or Sigma = sigma2 * I (the kernel of Eq. gbS0
+    shifted by nu), sampled on the plan's grid: [1, M, N, N] for a Plan,
+    [1, Lr, Ly, Lx] (Omega_L) for a GridPlan."""
+    S = _sigma_list(Sigma, sigma2)
     dev = torch.device("cuda", plan.device)
-    P = torch.empty(plan.grid_shape(1), dtype=plan.dtype, device=dev)
-    _check(load_library().se2_sample_se2_gaussian(plan.handle, _host_doubles(list(beta), 3, "beta"),
-                                                  _host_doubles(S, 9, "Sigma"), int(images), _ptr(P),
-                                                  _stream(dev)))
+    grid = isinstance(plan, GridPlan)
+    P = torch.empty(plan.sample_shape(1) if grid else plan.grid_shape(1), dtype=plan.dtype, device=dev)
+    lib = load_library()
+    fn = lib.se2_grid_sample_se2_gaussian if grid else lib.se2_sample_se2_gaussian
+    _check(fn(plan.handle, _host_doubles(list(beta), 3, "beta"), _host_doubles(S, 9, "Sigma"), int(images), _ptr(P),
+              _stream(dev)))
     return P
 
 
-def sample_deformed_gaussian(plan: Plan, H, nu: float, s: float, images: int = 1):
+def sample_deformed_gaussian(plan, H, nu: float, s: float, images: int = 1):
     """The 3D deformed Gaussian exp(-x^T H x) exp(-(theta - nu)^2 / s)
-    (Eq. fHsnu) on the plan's grid ([1, M, N, N])."""
+    (Eq. fHsnu) on the plan's grid ([1, M, N, N], or [1, Lr, Ly, Lx] for a
+    GridPlan)."""
     Hs = [float(v) for row in H for v in row]
     dev = torch.device("cuda", plan.device)
-    P = torch.empty(plan.grid_shape(1), dtype=plan.dtype, device=dev)
-    _check(load_library().se2_sample_deformed_gaussian(plan.handle, _host_doubles(Hs, 4, "H"), float(nu), float(s),
-                                                       int(images), _ptr(P), _stream(dev)))
+    grid = isinstance(plan, GridPlan)
+    P = torch.empty(plan.sample_shape(1) if grid else plan.grid_shape(1), dtype=plan.dtype, device=dev)
+    lib = load_library()
+    fn = lib.se2_grid_sample_deformed_gaussian if grid else lib.se2_sample_deformed_gaussian
+    _check(fn(plan.handle, _host_doubles(Hs, 4, "H"), float(nu), float(s), int(images), _ptr(P), _stream(dev)))
     return P
 
 

@@ -1094,38 +1094,12 @@ se2_status se2_sample_se2_gaussian(se2_plan_t p, const double* beta, const doubl
     if (beta == nullptr || Sigma == nullptr || P == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
     if (images < 0 || images > 8) return fail(SE2_ERR_INVALID_ARG, "images=%d must be in [0, 8]", images);
     if (!aligned(P, p->elem / 2)) return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
-    for (int i = 0; i < 3; ++i)
-        if (!(fabs(beta[i]) < 1e300)) return fail(SE2_ERR_INVALID_ARG, "beta is not finite");
-    double S[9], amax = 0.0;
-    for (int i = 0; i < 9; ++i) {
-        S[i] = Sigma[i];
-        if (!(S[i] == S[i]) || S[i] > 1e300 || S[i] < -1e300) return fail(SE2_ERR_INVALID_ARG, "Sigma is not finite");
-        amax = fabs(S[i]) > amax ? fabs(S[i]) : amax;
-    }
-    for (int r = 0; r < 3; ++r)
-        for (int c = r + 1; c < 3; ++c)
-            if (fabs(S[3 * r + c] - S[3 * c + r]) > 1e-12 * amax) return fail(SE2_ERR_INVALID_ARG, "Sigma is not symmetric");
-    // positive definite by the leading principal minors; inverse by the adjugate
-    const double m1 = S[0], m2 = S[0] * S[4] - S[1] * S[3];
-    const double c00 = S[4] * S[8] - S[5] * S[7], c01 = -(S[3] * S[8] - S[5] * S[6]), c02 = S[3] * S[7] - S[4] * S[6];
-    const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
-    if (!(m1 > 0) || !(m2 > 0) || !(det > 0)) return fail(SE2_ERR_INVALID_ARG, "Sigma is not positive definite");
-    const double c11 = S[0] * S[8] - S[2] * S[6], c12 = -(S[0] * S[7] - S[1] * S[6]);
-    const double c22 = S[0] * S[4] - S[1] * S[3];
     GaussSE2Args a;
-    a.N = p->N;
+    if (const char* why = make_gauss_args(beta, Sigma, &a)) return fail(SE2_ERR_INVALID_ARG, "%s", why);
+    a.Nx = a.Ny = p->N;
     a.M = p->M;
     a.images = images;
     a.x0 = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0.0 : -0.5;
-    a.b1 = beta[0];
-    a.b2 = beta[1];
-    a.nu_turns = beta[2] / (2.0 * 3.14159265358979323846);
-    a.q11 = c00 / det;
-    a.q12 = c01 / det;
-    a.q13 = c02 / det;
-    a.q22 = c11 / det;
-    a.q23 = c12 / det;
-    a.q33 = c22 / det;
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
     if (!is_f64(p))
@@ -1144,21 +1118,13 @@ se2_status se2_sample_deformed_gaussian(se2_plan_t p, const double* H, double nu
     if (st != SE2_OK) return st;
     if (H == nullptr || P == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
     if (images < 0 || images > 8) return fail(SE2_ERR_INVALID_ARG, "images=%d must be in [0, 8]", images);
-    if (!(s_theta > 0) || !(fabs(nu) < 1e300)) return fail(SE2_ERR_INVALID_ARG, "s must be > 0 and nu finite");
     if (!aligned(P, p->elem / 2)) return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
-    const double h11 = H[0], h12 = 0.5 * (H[1] + H[2]), h22 = H[3];
-    if (!(h11 > 0) || !(h11 * h22 - h12 * h12 > 0) || !(h22 < 1e300) || !(fabs(h12) < 1e300))
-        return fail(SE2_ERR_INVALID_ARG, "H is not positive definite");
     DeformedArgs a;
-    a.N = p->N;
+    if (const char* why = make_deformed_args(H, nu, s_theta, &a)) return fail(SE2_ERR_INVALID_ARG, "%s", why);
+    a.Nx = a.Ny = p->N;
     a.M = p->M;
     a.images = images;
     a.x0 = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0.0 : -0.5;
-    a.nu = nu;
-    a.s = s_theta;
-    a.h11 = h11;
-    a.h12 = h12;
-    a.h22 = h22;
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
     if (!is_f64(p))

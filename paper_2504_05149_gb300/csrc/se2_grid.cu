@@ -31,6 +31,7 @@
 
 #include "../../include/se2.h"
 #include "se2_internal.h"
+#include "se2_kernels.cuh"
 
 using namespace se2;
 
@@ -549,6 +550,61 @@ se2_status se2_grid_plan_destroy(se2_grid_plan_t p) {
 }
 
 unsigned long long se2_grid_plan_launches(se2_grid_plan_t p) { return p ? p->launches : 0ull; }
+
+static int grid_sampler_blocks(const se2_grid_plan_s* p) {
+    const long long total = (long long)p->Lx * p->Ly * p->Lr;
+    return (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+}
+
+se2_status se2_grid_sample_se2_gaussian(se2_grid_plan_t p, const double* beta, const double* Sigma, int images,
+                                        void* P, void* stream) {
+    se2_status st = check_gplan(p);
+    if (st != SE2_OK) return st;
+    if (beta == nullptr || Sigma == nullptr || P == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (images < 0 || images > 8) return gfail(SE2_ERR_INVALID_ARG, "images=%d must be in [0, 8]", images);
+    if (!galigned(P, p->celem / 2)) return gfail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    GaussSE2Args a;
+    if (const char* why = make_gauss_args(beta, Sigma, &a)) return gfail(SE2_ERR_INVALID_ARG, "%s", why);
+    a.Nx = p->Lx;
+    a.Ny = p->Ly;
+    a.M = p->Lr;
+    a.images = images;
+    a.x0 = -0.5;
+    GDevice guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->prec == SE2_F64)
+        k_se2_gauss_fill<double><<<grid_sampler_blocks(p), 256, 0, s>>>(a, static_cast<double*>(P));
+    else
+        k_se2_gauss_fill<float><<<grid_sampler_blocks(p), 256, 0, s>>>(a, static_cast<float*>(P));
+    ++p->launches;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SE2_OK : gcuda(e, "kernel launch");
+}
+
+se2_status se2_grid_sample_deformed_gaussian(se2_grid_plan_t p, const double* H, double nu, double s_theta,
+                                             int images, void* P, void* stream) {
+    se2_status st = check_gplan(p);
+    if (st != SE2_OK) return st;
+    if (H == nullptr || P == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (images < 0 || images > 8) return gfail(SE2_ERR_INVALID_ARG, "images=%d must be in [0, 8]", images);
+    if (!galigned(P, p->celem / 2)) return gfail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    DeformedArgs a;
+    if (const char* why = make_deformed_args(H, nu, s_theta, &a)) return gfail(SE2_ERR_INVALID_ARG, "%s", why);
+    a.Nx = p->Lx;
+    a.Ny = p->Ly;
+    a.M = p->Lr;
+    a.images = images;
+    a.x0 = -0.5;
+    GDevice guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->prec == SE2_F64)
+        k_deformed_fill<double><<<grid_sampler_blocks(p), 256, 0, s>>>(a, static_cast<double*>(P));
+    else
+        k_deformed_fill<float><<<grid_sampler_blocks(p), 256, 0, s>>>(a, static_cast<float*>(P));
+    ++p->launches;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SE2_OK : gcuda(e, "kernel launch");
+}
 
 se2_status se2_accuracy_order(double eps, double grad_inf, int k_inf, double constant, long long* K) {
     if (K == nullptr) return gfail(SE2_ERR_INVALID_ARG, "K is NULL");

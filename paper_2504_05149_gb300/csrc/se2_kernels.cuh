@@ -890,7 +890,7 @@ __global__ void k_mass_fix(T* out, long long n, const double* sums, MassArgs<T> 
 // makes them functions on Z^2\SE(2).
 // ---------------------------------------------------------------------------
 struct GaussSE2Args {
-    int N, M, images;
+    int Nx, Ny, M, images;   // grid x_i = x0 + i / Nx, y_j = x0 + j / Ny, theta_l = 2 pi l / M
     double x0;          // first grid coordinate: -1/2 on Omega_L, 0 at x_i = i/N
     double b1, b2;      // translation of the mean beta
     double nu_turns;    // rotation of the mean beta, in turns (nu / 2 pi)
@@ -904,11 +904,11 @@ struct GaussSE2Args {
 // = ((phi/2) / sin(phi/2)) R_-(nu + phi/2) (x - b).
 template <typename T>
 __global__ void k_se2_gauss_fill(GaussSE2Args a, T* P) {
-    const long long total = (long long)a.M * a.N * a.N;
-    const double inv_n = 1.0 / a.N;
+    const long long total = (long long)a.M * a.Ny * a.Nx;
+    const double inv_nx = 1.0 / a.Nx, inv_ny = 1.0 / a.Ny;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % a.N), j = (int)((e / a.N) % a.N), l = (int)(e / ((long long)a.N * a.N));
+        const int i = (int)(e % a.Nx), j = (int)((e / a.Nx) % a.Ny), l = (int)(e / ((long long)a.Nx * a.Ny));
         // angle of theta_l - nu in turns, reduced to (-1/2, 1/2]
         double t = (double)l / a.M - a.nu_turns;
         t -= rint(t);
@@ -918,7 +918,7 @@ __global__ void k_se2_gauss_fill(GaussSE2Args a, T* P) {
         const double ah = (t == 0.0) ? 1.0 : (PI * t) / sinpi(t);  // (phi/2)/sin(phi/2)
         double sr, cr;
         sincospi(2.0 * a.nu_turns + t, &sr, &cr);  // rotation by nu + phi/2
-        const double px = a.x0 + i * inv_n - a.b1, py = a.x0 + j * inv_n - a.b2;
+        const double px = a.x0 + i * inv_nx - a.b1, py = a.x0 + j * inv_ny - a.b2;
         double acc = 0.0;
         for (int n2 = -a.images; n2 <= a.images; ++n2) {
             for (int n1 = -a.images; n1 <= a.images; ++n1) {
@@ -934,25 +934,73 @@ __global__ void k_se2_gauss_fill(GaussSE2Args a, T* P) {
     }
 }
 
+// Host-side preparation of GaussSE2Args from beta = {b1, b2, nu} and a
+// row-major 3x3 Sigma: checks symmetry and positive definiteness (leading
+// minors) and inverts by the adjugate.  Returns nullptr or why it refused.
+inline const char* make_gauss_args(const double* beta, const double* Sigma, GaussSE2Args* a) {
+    for (int i = 0; i < 3; ++i)
+        if (!(fabs(beta[i]) < 1e300)) return "beta is not finite";
+    double S[9], amax = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        S[i] = Sigma[i];
+        if (!(fabs(S[i]) < 1e300)) return "Sigma is not finite";
+        amax = fabs(S[i]) > amax ? fabs(S[i]) : amax;
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int c = r + 1; c < 3; ++c)
+            if (fabs(S[3 * r + c] - S[3 * c + r]) > 1e-12 * amax) return "Sigma is not symmetric";
+    const double m1 = S[0], m2 = S[0] * S[4] - S[1] * S[3];
+    const double c00 = S[4] * S[8] - S[5] * S[7], c01 = -(S[3] * S[8] - S[5] * S[6]), c02 = S[3] * S[7] - S[4] * S[6];
+    const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+    if (!(m1 > 0) || !(m2 > 0) || !(det > 0)) return "Sigma is not positive definite";
+    const double c11 = S[0] * S[8] - S[2] * S[6], c12 = -(S[0] * S[7] - S[1] * S[6]);
+    const double c22 = S[0] * S[4] - S[1] * S[3];
+    a->b1 = beta[0];
+    a->b2 = beta[1];
+    a->nu_turns = beta[2] / (2.0 * 3.14159265358979323846);
+    a->q11 = c00 / det;
+    a->q12 = c01 / det;
+    a->q13 = c02 / det;
+    a->q22 = c11 / det;
+    a->q23 = c12 / det;
+    a->q33 = c22 / det;
+    return nullptr;
+}
+
 struct DeformedArgs {
-    int N, M, images;
+    int Nx, Ny, M, images;
     double x0, nu, s;
     double h11, h12, h22;  // symmetric part of H
 };
+
+// Host-side preparation of DeformedArgs from a row-major 2x2 H (its
+// symmetric part must be positive definite), nu and s > 0.
+inline const char* make_deformed_args(const double* H, double nu, double s_theta, DeformedArgs* a) {
+    if (!(s_theta > 0) || !(s_theta < 1e300) || !(fabs(nu) < 1e300)) return "s must be finite and > 0, nu finite";
+    const double h11 = H[0], h12 = 0.5 * (H[1] + H[2]), h22 = H[3];
+    if (!(h11 > 0) || !(h11 * h22 - h12 * h12 > 0) || !(h22 < 1e300) || !(fabs(h12) < 1e300))
+        return "H is not positive definite";
+    a->nu = nu;
+    a->s = s_theta;
+    a->h11 = h11;
+    a->h12 = h12;
+    a->h22 = h22;
+    return nullptr;
+}
 
 // f(x, R_theta) = exp(-x^T H x) exp(-(theta - nu)^2 / s), theta = 2 pi l / M
 // taken as it is (no wrapping), as Eq. fHsnu is printed.
 template <typename T>
 __global__ void k_deformed_fill(DeformedArgs a, T* P) {
-    const long long total = (long long)a.M * a.N * a.N;
-    const double inv_n = 1.0 / a.N;
+    const long long total = (long long)a.M * a.Ny * a.Nx;
+    const double inv_nx = 1.0 / a.Nx, inv_ny = 1.0 / a.Ny;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % a.N), j = (int)((e / a.N) % a.N), l = (int)(e / ((long long)a.N * a.N));
+        const int i = (int)(e % a.Nx), j = (int)((e / a.Nx) % a.Ny), l = (int)(e / ((long long)a.Nx * a.Ny));
         const double PI = 3.14159265358979323846;
         const double dt = 2.0 * PI * l / a.M - a.nu;
         const double ang = exp(-dt * dt / a.s);
-        const double px = a.x0 + i * inv_n, py = a.x0 + j * inv_n;
+        const double px = a.x0 + i * inv_nx, py = a.x0 + j * inv_ny;
         double acc = 0.0;
         for (int n2 = -a.images; n2 <= a.images; ++n2) {
             for (int n1 = -a.images; n1 <= a.images; ++n1) {

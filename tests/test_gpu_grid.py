@@ -159,3 +159,34 @@ def test_grid_longest_chain(se2):
     out = se2.grid_convolve_chain(plan, _dev(np.stack(Fs), "f64"), Cs).cpu().numpy()
     for b in range(B):
         assert _rel(out[b], U.series(Fs[b], Ps[b], N[::-1]).real) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_grid_samplers(se2, prec):
+    """The samplers on a grid plan's odd, anisotropic Omega_L (one lattice
+    image) against the oracle's pointwise functions."""
+    L = (31, 33, 61)
+    plan = se2.GridPlan(L, (36, 38, 76), batch=1, precision=prec)
+    tol = {"f32": 1e-6, "f64": 1e-13}[prec]
+    beta, Sig = (0.05, -0.1, math.pi / 4), np.array([[0.02, 0.004, 0.001], [0.004, 0.03, -0.002], [0.001, -0.002, 0.5]])
+    got = se2.sample_se2_gaussian(plan, beta, Sigma=Sig, images=0)[0].double().cpu().numpy()
+    x, y, t = _axes(L)
+    T, Y, X = np.meshgrid(t, y, x, indexing="ij")
+    assert _rel(got, G.se2_gaussian_at(X, Y, T, beta, Sig)) < tol
+    H = [[1 / 0.03, 0.0], [0.0, 1 / 0.01]]
+    got = se2.sample_deformed_gaussian(plan, H, math.pi / 2, 0.01, images=0)[0].double().cpu().numpy()
+    assert _rel(got, deformed(L, H, math.pi / 2, 0.01)) < tol
+
+
+def test_paper_e4_sampled_on_the_gpu(se2):
+    """The paper's single-convolution experiment with both inputs sampled by
+    the grid plan's samplers (f: H = diag(0.03, 0.01)^-1; rho: U = (1/0.02) I;
+    s = 0.01, nu = pi/2), against the oracle's series."""
+    L, N = (31, 33, 61), (36, 38, 76)
+    plan = se2.GridPlan(L, N, batch=1, precision="f32")
+    H, U_ = [[1 / 0.03, 0.0], [0.0, 1 / 0.01]], [[1 / 0.02, 0.0], [0.0, 1 / 0.02]]
+    f = se2.sample_deformed_gaussian(plan, H, math.pi / 2, 0.01, images=0)
+    rho = se2.sample_deformed_gaussian(plan, U_, math.pi / 2, 0.01, images=0)
+    out = se2.grid_convolve_chain(plan, f, [se2.grid_coeffs(plan, rho)])[0].double().cpu().numpy()
+    want = U.series(deformed(L, H, math.pi / 2, 0.01), [deformed(L, U_, math.pi / 2, 0.01)], N[::-1]).real
+    assert _rel(out, want) < 1e-5
