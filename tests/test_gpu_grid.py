@@ -190,3 +190,48 @@ def test_paper_e4_sampled_on_the_gpu(se2):
     out = se2.grid_convolve_chain(plan, f, [se2.grid_coeffs(plan, rho)])[0].double().cpu().numpy()
     want = U.series(deformed(L, H, math.pi / 2, 0.01), [deformed(L, U_, math.pi / 2, 0.01)], N[::-1]).real
     assert _rel(out, want) < 1e-5
+
+
+def _peak_theta(V, Nr):
+    """Angle (in units of pi) of the theta slice holding the largest value."""
+    l = np.unravel_index(np.argmax(V), V.shape)[0]
+    return 2.0 * l / Nr
+
+
+def test_paper_triple_convolution_e5(se2):
+    """The paper's triple convolution: K = (20, 21, 50), L = (41, 43, 101),
+    output 41 x 43 x 151; f = f_H^{pi/4, 0.0125}, H = diag(0.025, 0.0025)^-1,
+    rho of Eq. gbS0 with sigma^2 = 0.005 shifted by pi/4.  Against the
+    oracle's series, and the mass of f * rho^(3) sits at theta = pi, where
+    the paper slices it (each factor adds pi/4)."""
+    L, N = (41, 43, 101), (41, 43, 151)
+    plan = se2.GridPlan(L, N, batch=1, precision="f32")
+    H = [[1 / 0.025, 0.0], [0.0, 1 / 0.0025]]
+    f = se2.sample_deformed_gaussian(plan, H, math.pi / 4, 0.0125, images=0)
+    rho = se2.sample_se2_gaussian(plan, (0.0, 0.0, math.pi / 4), sigma2=0.005, images=0)
+    C = se2.grid_coeffs(plan, rho)
+    out = se2.grid_convolve_chain(plan, f, [C, C, C])[0].double().cpu().numpy()
+    F = f[0].double().cpu().numpy()
+    P = rho[0].double().cpu().numpy()
+    want = U.series(F, [P, P, P], N[::-1]).real
+    assert _rel(out, want) < 1e-5
+    assert abs(_peak_theta(out, N[2]) - 1.0) <= 2.0 / N[2] + 1e-12
+
+
+def test_paper_six_powers_e6(se2):
+    """The paper's Algorithm 6 experiment: K = (15, 16, 30), grid 31 x 33 x 61;
+    f = f_H^{pi/7, 0.0071}, H = diag(0.0143, 0.0014)^-1, rho of Eq. gbS0 with
+    sigma^2 = 0.0029 shifted by pi/7.  V_p = f * rho^(p), p = 1..6, against the
+    oracle's series; V_p peaks at theta = (p+1) pi/7, where the paper slices it."""
+    L = (31, 33, 61)
+    plan = se2.GridPlan(L, batch=1, precision="f32")
+    H = [[1 / 0.0143, 0.0], [0.0, 1 / 0.0014]]
+    f = se2.sample_deformed_gaussian(plan, H, math.pi / 7, 0.0071, images=0)
+    rho = se2.sample_se2_gaussian(plan, (0.0, 0.0, math.pi / 7), sigma2=0.0029, images=0)
+    C = se2.grid_coeffs(plan, rho)
+    F = f[0].double().cpu().numpy()
+    P = rho[0].double().cpu().numpy()
+    for p in range(1, 7):
+        out = se2.grid_convolve_chain(plan, f, [C] * p)[0].double().cpu().numpy()
+        assert _rel(out, U.series(F, [P] * p, L[::-1]).real) < 1e-5, p
+        assert abs(_peak_theta(out, L[2]) - (p + 1) / 7.0) <= 2.0 / L[2] + 1e-12, p
