@@ -358,7 +358,8 @@ typedef struct se2_grid_plan_s* se2_grid_plan_t;
  * N: host int[3] {Nx, Ny, Nr} with L <= N <= 1024 per axis; batch >= 1;
  * precision SE2_F32 or SE2_F64; flags 0 or SE2_SHARED_KERNEL (one coefficient
  * array per kernel for the whole batch).  Allocates the DFT tables (FP64
- * sincospi, rounded) and 2 * batch * Nr * Ny * (Kx+1) complex of workspace.
+ * sincospi, rounded) and 2 * batch * Nr * Ny * (Kx+1) + batch * Lr * Ly * (Kx+1)
+ * complex of workspace.
  * Calls on one grid plan share that workspace: order them on one stream.
  * Errors: SE2_ERR_UNSUPPORTED (even L, precision, flags), SE2_ERR_INVALID_ARG
  * (N < L, batch, device), SE2_ERR_OOM; *plan is NULL on failure.
@@ -389,6 +390,16 @@ se2_status se2_grid_coeffs(se2_grid_plan_t plan, const void* samples, int n, voi
  */
 se2_status se2_grid_convolve_chain(se2_grid_plan_t plan, const void* f, int B, const void* const* coeffs, int k,
                                    void* out, void* stream);
+
+/*
+ * se2_grid_convolve_chain_all -- every intermediate V_p = Re S_K[f, rho_1..rho_p],
+ * p = 1..k, on the N-grid from one forward transform (Algorithm 6, the fast
+ * recursion): out is [k][B][Nr][Ny][Nx] (it must not overlap f); coeffs and
+ * the other arguments as se2_grid_convolve_chain, 1 <= k <= 32.  The running
+ * product is kept unscaled in the plan's workspace.
+ */
+se2_status se2_grid_convolve_chain_all(se2_grid_plan_t plan, const void* f, int B, const void* const* coeffs, int k,
+                                       void* out, void* stream);
 
 /*
  * se2_grid_sample_se2_gaussian / se2_grid_sample_deformed_gaussian -- the

@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
     lib.se2_grid_plan_launches.restype = ctypes.c_ulonglong
     lib.se2_grid_coeffs.argtypes = [vp, vp, ip, vp, vp]
     lib.se2_grid_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ip, vp, vp]
+    lib.se2_grid_convolve_chain_all.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ip, vp, vp]
     lib.se2_grid_sample_se2_gaussian.argtypes = [vp, dptr, dptr, ctypes.c_int, vp, vp]
     lib.se2_grid_sample_deformed_gaussian.argtypes = [vp, dptr, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
     lib.se2_accuracy_order.argtypes = [ctypes.c_double, ctypes.c_double, ip, ctypes.c_double,
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH):
                  "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
                  "se2_sample_se2_gaussian", "se2_sample_deformed_gaussian",
                  "se2_grid_plan_create", "se2_grid_plan_destroy", "se2_grid_coeffs", "se2_grid_convolve_chain",
+                 "se2_grid_convolve_chain_all",
                  "se2_accuracy_order", "se2_grid_sample_se2_gaussian", "se2_grid_sample_deformed_gaussian",
                  "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
@@ -436,6 +438,29 @@ def grid_convolve_chain(plan: GridPlan, f: torch.Tensor, Cs: Sequence[torch.Tens
     return out
 
 
+def grid_convolve_chain_all(plan: GridPlan, f: torch.Tensor, Cs: Sequence[torch.Tensor],
+                            out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Every V_p = Re S_K[f, rho_1..rho_p], p = 1..k, on the N-grid from one
+    forward transform (Algorithm 6): returns [k, B, Nr, Ny, Nx]."""
+    B = plan._check_tensor(f, "f", plan.sample_shape(1)[1:], plan.dtype)
+    k = len(Cs)
+    if k < 1:
+        raise ValueError("need at least one kernel")
+    shape = (k,) + plan.out_shape(B)
+    if out is None:
+        out = torch.empty(shape, dtype=plan.dtype, device=f.device)
+    elif tuple(out.shape) != shape or out.dtype != plan.dtype or not out.is_contiguous():
+        raise ValueError(f"out: need a contiguous {plan.dtype} tensor {shape}")
+    nb = 1 if plan.flags & SHARED_KERNEL else B
+    for i, C in enumerate(Cs):
+        plan._check_tensor(C, f"coeffs[{i}]", plan.spec_shape(1)[1:], plan.cdtype)
+        if C.shape[0] != nb:
+            raise ValueError(f"coeffs[{i}]: expected {nb} arrays, got {C.shape[0]}")
+    cp = (ctypes.c_void_p * k)(*[C.data_ptr() for C in Cs])
+    _check(load_library().se2_grid_convolve_chain_all(plan.handle, _ptr(f), B, cp, k, _ptr(out), _stream(f.device)))
+    return out
+
+
 def accuracy_order(eps: float, grad_inf: float, k=(0, 0, 0), constant: float = 32.0) -> int:
     """Algorithm 1: the smallest K with K >= max(constant ||grad f||_inf / eps,
     ||k||_inf); f^[k; 2K+1] is then within eps of f^[k] (Theorem fkLmain)."""
@@ -546,6 +571,6 @@ class SE2Conv(torch.autograd.Function):
 __all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_chain", "convolve_chain_all",
            "backward",
            "sample_radial_gaussian", "sample_se2_gaussian", "sample_deformed_gaussian",
-           "GridPlan", "grid_coeffs", "grid_convolve_chain", "accuracy_order", "ffc_at", "ffc_convergence",
+           "GridPlan", "grid_coeffs", "grid_convolve_chain", "grid_convolve_chain_all", "accuracy_order", "ffc_at", "ffc_convergence",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
            "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO", "MASS_RENORM"]

@@ -42,7 +42,7 @@ struct se2_grid_plan_s {
     size_t celem = 0;              // bytes of one complex element
     void* tab = nullptr;           // the six DFT tables, complex
     size_t toff[6] = {};           // their offsets, in complex elements
-    void* buf[2] = {nullptr, nullptr};
+    void* buf[3] = {nullptr, nullptr, nullptr};   // ping-pong workspace; running product of Algorithm 6
     unsigned long long launches = 0;
 };
 
@@ -161,7 +161,9 @@ struct GridPass {
     const c2<T>* C[kGridMaxK];
     long long c_bstride;          // per problem (0: one array for the batch)
     int k, Ly, Hx;
+    int wpow;                     // W^wpow (k for a chain, p for step p of Algorithm 6)
     T in_scale;
+    c2<T>* acc;                   // when set: the unscaled product is stored back here (running product)
 };
 
 __device__ __forceinline__ long long gaddr(long long q, int inner, long long so) {
@@ -279,10 +281,6 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_cols(GridPass<T> a) {
                 // column q = b * inner + (ky * Hx + kx); the bin index along theta is i
                 const long long b = q / a.inner;
                 const int cc = (int)(q % a.inner), ky = cc / a.Hx, kx = cc % a.Hx;
-                T sr = a.in_scale;
-                if ((a.k & 1) && ((kx + sfreq(ky, a.Ly)) & 1)) sr = -sr;
-                v.x *= sr;
-                v.y *= sr;
                 const long long coff = b * a.c_bstride + (off - b * a.in_so);
                 for (int t = 0; t < a.k; ++t) {
                     const c2<T> w = a.C[t][coff];
@@ -290,6 +288,11 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_cols(GridPass<T> a) {
                     v.x = xr;
                     v.y = xi;
                 }
+                if (a.acc != nullptr) a.acc[off] = v;   // each bin is loaded by one thread only
+                T sr = a.in_scale;
+                if ((a.wpow & 1) && ((kx + sfreq(ky, a.Ly)) & 1)) sr = -sr;
+                v.x *= sr;
+                v.y *= sr;
             }
         }
         s[idx] = v;
@@ -418,18 +421,21 @@ cudaError_t forward(se2_grid_plan_s* p, const T* src, int B, c2<T>* dst, T scale
     return launch_pass<T>(p, GM_C2C, a, s);
 }
 
+// The three inverse passes from the spectrum `spec` ([B][Lr][Ly][Hx]) to
+// out ([B][Nr][Ny][Nx]): theta inverse with the product of the k coefficient
+// arrays, W^wpow and 1/|L| formed while loading (and the unscaled product
+// stored back into `acc` when given), then y and x.
 template <typename T>
-cudaError_t run_chain(se2_grid_plan_s* p, const T* f, int B, const void* const* coeffs, int k, T* out,
-                      cudaStream_t s) {
+cudaError_t inverse_from(se2_grid_plan_s* p, c2<T>* spec, int B, const void* const* coeffs, int k, int wpow,
+                         c2<T>* acc, T* out, cudaStream_t s) {
     const long long slab = (long long)p->Lr * p->Ly * p->Hx;
     c2<T>* A = static_cast<c2<T>*>(p->buf[0]);
     c2<T>* Bf = static_cast<c2<T>*>(p->buf[1]);
     cudaError_t e;
-    if ((e = forward<T>(p, f, B, A, T(1), s))) return e;
     GridPass<T> a = {};
     a.out_scale = T(1);
     // theta inverse onto Nr, with the product: columns (b, ky, kx)
-    a.in = A; a.out = Bf; a.E = table<T>(p, 3);
+    a.in = spec; a.out = Bf; a.E = table<T>(p, 3);
     a.n_in = p->Lr; a.n_out = p->Nr; a.inner = p->Ly * p->Hx;
     a.Q = (long long)B * p->Ly * p->Hx;
     a.in_so = slab; a.in_si = (long long)p->Ly * p->Hx;
@@ -437,6 +443,8 @@ cudaError_t run_chain(se2_grid_plan_s* p, const T* f, int B, const void* const* 
     for (int t = 0; t < k; ++t) a.C[t] = static_cast<const c2<T>*>(coeffs[t]);
     a.c_bstride = (p->flags & SE2_SHARED_KERNEL) ? 0 : slab;
     a.k = k; a.Ly = p->Ly; a.Hx = p->Hx;
+    a.wpow = wpow;
+    a.acc = acc;
     a.in_scale = (T)(1.0 / ((double)p->Lx * p->Ly * p->Lr));
     if ((e = launch_pass<T>(p, GM_MUL, a, s))) return e;
     // y inverse onto Ny: columns (b, l', kx)
@@ -456,6 +464,33 @@ cudaError_t run_chain(se2_grid_plan_s* p, const T* f, int B, const void* const* 
     x.Q = (long long)B * p->Nr * p->Ny;
     x.in_so = p->Hx; x.in_si = 1; x.out_so = p->Nx; x.out_sj = 1;
     return launch_pass<T>(p, GM_C2R, x, s);
+}
+
+template <typename T>
+cudaError_t run_chain(se2_grid_plan_s* p, const T* f, int B, const void* const* coeffs, int k, T* out,
+                      cudaStream_t s) {
+    c2<T>* A = static_cast<c2<T>*>(p->buf[0]);
+    cudaError_t e = forward<T>(p, f, B, A, T(1), s);
+    if (e != cudaSuccess) return e;
+    // the theta inverse reads A; the y inverse then overwrites it
+    return inverse_from<T>(p, A, B, coeffs, k, k, nullptr, out, s);
+}
+
+// Algorithm 6 on the grid: one forward transform into the running product
+// R (buf[2]), then per step p: R <- R C_p (stored back) and out_p from
+// W^p R / |L|.
+template <typename T>
+cudaError_t run_chain_all(se2_grid_plan_s* p, const T* f, int B, const void* const* coeffs, int k, T* out,
+                          cudaStream_t s) {
+    c2<T>* R = static_cast<c2<T>*>(p->buf[2]);
+    cudaError_t e = forward<T>(p, f, B, R, T(1), s);
+    if (e != cudaSuccess) return e;
+    const size_t per = (size_t)B * p->Nr * p->Ny * p->Nx;
+    for (int q = 0; q < k; ++q) {
+        const void* cq[1] = {coeffs[q]};
+        if ((e = inverse_from<T>(p, R, B, cq, 1, q + 1, R, out + (size_t)q * per, s))) return e;
+    }
+    return cudaSuccess;
 }
 
 bool galigned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
@@ -514,10 +549,12 @@ se2_status se2_grid_plan_create(se2_grid_plan_t* out, const int* L, const int* N
     cudaError_t e = cudaMalloc(&p->tab, (size_t)acc * p->celem);
     if (e == cudaSuccess) e = cudaMalloc(&p->buf[0], ws);
     if (e == cudaSuccess) e = cudaMalloc(&p->buf[1], ws);
+    if (e == cudaSuccess) e = cudaMalloc(&p->buf[2], (size_t)batch * p->Lr * p->Ly * p->Hx * p->celem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         se2_grid_plan_destroy(p);
-        return gfail(SE2_ERR_OOM, "device allocation of %zu bytes failed", 2 * ws + (size_t)acc * p->celem);
+        return gfail(SE2_ERR_OOM, "device allocation of %zu bytes failed",
+                     2 * ws + (size_t)acc * p->celem + (size_t)batch * p->Lr * p->Ly * p->Hx * p->celem);
     }
     const int blocks = (int)((acc + 255) / 256 < 1024 ? (acc + 255) / 256 : 1024);
     if (precision == SE2_F64) {
@@ -544,6 +581,7 @@ se2_status se2_grid_plan_destroy(se2_grid_plan_t p) {
         if (p->tab) cudaFree(p->tab);
         if (p->buf[0]) cudaFree(p->buf[0]);
         if (p->buf[1]) cudaFree(p->buf[1]);
+        if (p->buf[2]) cudaFree(p->buf[2]);
     }
     delete p;
     return SE2_OK;
@@ -660,6 +698,30 @@ se2_status se2_grid_convolve_chain(se2_grid_plan_t p, const void* f, int B, cons
     cudaError_t e = p->prec == SE2_F64
                         ? run_chain<double>(p, static_cast<const double*>(f), B, coeffs, k, static_cast<double*>(out), s)
                         : run_chain<float>(p, static_cast<const float*>(f), B, coeffs, k, static_cast<float*>(out), s);
+    if (e != cudaSuccess) return gcuda(e, "kernel launch");
+    return SE2_OK;
+}
+
+se2_status se2_grid_convolve_chain_all(se2_grid_plan_t p, const void* f, int B, const void* const* coeffs, int k,
+                                       void* out, void* stream) {
+    se2_status st = check_gplan(p);
+    if (st != SE2_OK) return st;
+    if (f == nullptr || out == nullptr || coeffs == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (B < 1 || B > p->batch) return gfail(SE2_ERR_INVALID_ARG, "B=%d must be in [1, batch=%d]", B, p->batch);
+    if (k < 1 || k > kGridMaxK) return gfail(SE2_ERR_INVALID_ARG, "k=%d must be in [1, %d]", k, kGridMaxK);
+    if (!galigned(f, p->celem / 2) || !galigned(out, p->celem / 2)) return gfail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    for (int t = 0; t < k; ++t)
+        if (coeffs[t] == nullptr || !galigned(coeffs[t], p->celem))
+            return gfail(SE2_ERR_INVALID_ARG, "coeffs[%d] NULL or misaligned", t);
+    const size_t re = p->celem / 2;
+    const uintptr_t fa = (uintptr_t)f, oa = (uintptr_t)out;
+    const size_t flen = (size_t)B * p->Lr * p->Ly * p->Lx * re, olen = (size_t)k * B * p->Nr * p->Ny * p->Nx * re;
+    if (fa < oa + olen && oa < fa + flen) return gfail(SE2_ERR_INVALID_ARG, "out overlaps f");
+    GDevice guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = p->prec == SE2_F64
+                        ? run_chain_all<double>(p, static_cast<const double*>(f), B, coeffs, k, static_cast<double*>(out), s)
+                        : run_chain_all<float>(p, static_cast<const float*>(f), B, coeffs, k, static_cast<float*>(out), s);
     if (e != cudaSuccess) return gcuda(e, "kernel launch");
     return SE2_OK;
 }

@@ -235,3 +235,35 @@ def test_paper_six_powers_e6(se2):
         out = se2.grid_convolve_chain(plan, f, [C] * p)[0].double().cpu().numpy()
         assert _rel(out, U.series(F, [P] * p, L[::-1]).real) < 1e-5, p
         assert abs(_peak_theta(out, L[2]) - (p + 1) / 7.0) <= 2.0 / L[2] + 1e-12, p
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_grid_chain_all_algorithm6(se2, prec):
+    """se2_grid_convolve_chain_all: V_1..V_k from one forward transform
+    (Algorithm 6) on an odd upsampled grid, per-problem kernels, against the
+    oracle's series for every p; and the paper's six-power experiment."""
+    L, N, B, k = (9, 11, 13), (12, 14, 20), 2, 4
+    plan = se2.GridPlan(L, N, batch=B, precision=prec)
+    Fs = [_round(deformed(L, [[30, 0], [0, 60]], 1.0 + b, 0.3), prec) for b in range(B)]
+    Ps = [[_round(se2_gauss(L, 0.008 + 0.001 * t, 0.1 * t + 0.2 * b), prec) for t in range(k)] for b in range(B)]
+    Cs = [se2.grid_coeffs(plan, _dev(np.stack([Ps[b][t] for b in range(B)]), prec)) for t in range(k)]
+    n0 = plan.launches()
+    V = se2.grid_convolve_chain_all(plan, _dev(np.stack(Fs), prec), Cs)
+    torch.cuda.synchronize()
+    assert plan.launches() - n0 == 3 + 3 * k
+    V = V.double().cpu().numpy()
+    for b in range(B):
+        for p in range(1, k + 1):
+            assert _rel(V[p - 1, b], U.series(Fs[b], Ps[b][:p], N[::-1]).real) < TOL[prec], (b, p)
+
+    # the paper's six powers (K = (15, 16, 30), grid 31 x 33 x 61), all at once
+    L6 = (31, 33, 61)
+    plan6 = se2.GridPlan(L6, batch=1, precision="f32")
+    f = se2.sample_deformed_gaussian(plan6, [[1 / 0.0143, 0.0], [0.0, 1 / 0.0014]], math.pi / 7, 0.0071, images=0)
+    rho = se2.sample_se2_gaussian(plan6, (0.0, 0.0, math.pi / 7), sigma2=0.0029, images=0)
+    C = se2.grid_coeffs(plan6, rho)
+    V6 = se2.grid_convolve_chain_all(plan6, f, [C] * 6)[:, 0].double().cpu().numpy()
+    F = f[0].double().cpu().numpy()
+    P = rho[0].double().cpu().numpy()
+    for p in range(1, 7):
+        assert _rel(V6[p - 1], U.series(F, [P] * p, L6[::-1]).real) < 1e-5, p
