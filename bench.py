@@ -277,6 +277,16 @@ def main():
     ms, value = aggregate(ms, B * args.steps, world, reduce_max)
     ms_step = ms / args.steps
 
+    # per-kernel launch durations, live: a second pass of the same steps with
+    # CUDA events around every unit launch, recorded by the library on the
+    # stream each launch runs on (FP32 fast path only)
+    plan.timing(True)
+    for _ in range(args.steps):
+        se2.convolve(plan, f, C, out=out)
+    torch.cuda.synchronize(dev)
+    unit_stats = plan.timing_read()
+    plan.timing(False)
+
     # end to end through the public API with host buffers (se2_convolve_host):
     # pinned host f -> device, convolve, device -> host out, overlapped by groups
     hf = torch.from_numpy(F).pin_memory()
@@ -344,11 +354,8 @@ def main():
             "data": "synthetic",
             "config": {**c2_config(N, M, B, world),
                        "l2": f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB moved per step)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_source": src,
-                         "scope": "whole se2_convolve step (all kernels)",
-                         "alg_bytes_per_conv": alg_bytes / B,
-                         **traffic_fields(N, M, args.precision)},
+            "roofline": kernel_roofline(unit_stats, N, M, B, args.steps, hbm, src, achieved, alg_bytes,
+                                        args.precision),
             "cpu_baseline": base,
             "e2e": {"value": e2e_val, "unit": "conv/s", "h2d_bytes_per_step": int(F.nbytes),
                     "d2h_bytes_per_step": int(F.nbytes)},
@@ -370,6 +377,47 @@ def main():
 # caches before each kernel, so the scratch that the live run keeps in L2 is
 # counted as DRAM traffic: an upper bound.
 NCU_TRAFFIC_PER_CONV = {(256, 64, "f32"): (33.602304 + 0.463360 + 71.602688 + 1.382656 + 37.777408 + 1.117184) * 1e6 / 2}
+
+
+# The same capture per launch (2 problems): kf_fwd_xt, kf_lines, kf_inv_tx.
+NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.602304 + 0.463360) * 1e6, (71.602688 + 1.382656) * 1e6,
+                                             (37.777408 + 1.117184) * 1e6)}
+UNIT_NAMES = ("kf_fwd_xt", "kf_lines", "kf_inv_tx")
+
+
+def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_bytes, precision):
+    """Roofline of the dominant kernel from live per-launch durations.
+    Algorithmic bytes per problem: kf_fwd_xt reads f (4|L|), kf_lines reads
+    the kernel spectrum (8 M N (N/2+1)), kf_inv_tx writes out (4|L|); the
+    scratch between them is not algorithmic."""
+    L = N * N * M
+    step = {"scope": "whole se2_convolve step (all kernels)", "achieved": step_achieved,
+            "frac": step_achieved / hbm, "alg_bytes_per_conv": step_bytes / B, **traffic_fields(N, M, precision)}
+    per_problem = (4 * L, 8 * M * N * (N // 2 + 1), 4 * L)
+    kern = []
+    for name, bpp, (tms, cnt) in zip(UNIT_NAMES, per_problem, unit_stats):
+        if cnt == 0:
+            continue
+        ppl = B * steps / cnt
+        avg = tms / cnt
+        ach = bpp * ppl / (avg / 1e3) / 1e9
+        kern.append({"kernel": name, "launches": cnt, "avg_launch_ms": avg, "total_ms": tms,
+                     "problems_per_launch": ppl, "alg_bytes_per_launch": bpp * ppl, "achieved": ach,
+                     "frac": ach / hbm})
+    if not kern:   # not the FP32 fast path: the whole step only
+        return {"bound": "hbm", "achieved": step_achieved, "peak": hbm, "unit": "GB/s",
+                "frac": step_achieved / hbm, "peak_source": src, **step}
+    dom = max(kern, key=lambda d: d["total_ms"])
+    tr = NCU_TRAFFIC_PER_LAUNCH.get((N, M, precision))
+    ti = UNIT_NAMES.index(dom["kernel"])
+    traffic = tr[ti] if (tr is not None and abs(dom["problems_per_launch"] - 2) < 1e-9) else None
+    return {"bound": "hbm", "achieved": dom["achieved"], "peak": hbm, "unit": "GB/s", "frac": dom["frac"],
+            "peak_source": src, "kernel": dom["kernel"], "avg_launch_ms": dom["avg_launch_ms"],
+            "alg_bytes_per_launch": dom["alg_bytes_per_launch"], "traffic": traffic,
+            "traffic_source": "ncu --set full, caches flushed (upper bound), per launch of 2 problems; "
+                              "profiles/kf_units_f32_256x256x64_b4_full.md",
+            "timing": "CUDA events around each launch on its own stream, a second pass of the same steps",
+            "kernels": kern, "step": step}
 
 
 def traffic_fields(N, M, precision):

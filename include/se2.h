@@ -263,6 +263,20 @@ se2_status se2_convolve_separable(se2_plan_t plan, const void* f, int B, const v
 unsigned long long se2_plan_launches(se2_plan_t plan);
 
 /*
+ * se2_plan_timing / se2_plan_timing_read -- per-launch durations of the FP32
+ * fast path's three units (0: forward x and theta transforms, kf_fwd_xt;
+ * 1: y pass with the product, kf_lines; 2: inverse theta and x transforms,
+ * kf_inv_tx).  With timing on, each unit launch is bracketed by CUDA events
+ * recorded on the stream it runs on (the pipeline's own streams included);
+ * se2_plan_timing(plan, 1) also clears what was recorded.  _read waits for
+ * the recorded events and returns, per unit, the summed milliseconds ms[3]
+ * and the launch counts count[3] (host arrays).  Not for use while a stream
+ * is being captured into a CUDA graph.  Up to 32768 launches are recorded.
+ */
+se2_status se2_plan_timing(se2_plan_t plan, int on);
+se2_status se2_plan_timing_read(se2_plan_t plan, double* ms, long long* count);
+
+/*
  * se2_plan_status -- synchronise `stream`, then report and clear the plan's
  * device error word.  The persistent convolution kernel waits on counters
  * that other blocks of the same launch update and the tensor-core DFT on

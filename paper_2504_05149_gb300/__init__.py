@@ -83,6 +83,8 @@ def load_library(path: str = LIB_PATH):
     lib.se2_accuracy_order.argtypes = [ctypes.c_double, ctypes.c_double, ip, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_longlong)]
     lib.se2_debug_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
+    lib.se2_plan_timing.argtypes = [vp, ip]
+    lib.se2_plan_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     lib.se2_plan_launches.argtypes = [vp]
     lib.se2_plan_launches.restype = ctypes.c_ulonglong
     lib.se2_last_error.restype = ctypes.c_char_p
@@ -93,7 +95,7 @@ def load_library(path: str = LIB_PATH):
                  "se2_sample_se2_gaussian", "se2_sample_deformed_gaussian",
                  "se2_grid_plan_create", "se2_grid_plan_destroy", "se2_grid_coeffs", "se2_grid_convolve_chain",
                  "se2_grid_convolve_chain_all",
-                 "se2_accuracy_order", "se2_grid_sample_se2_gaussian", "se2_grid_sample_deformed_gaussian",
+                 "se2_accuracy_order", "se2_plan_timing", "se2_plan_timing_read", "se2_grid_sample_se2_gaussian", "se2_grid_sample_deformed_gaussian",
                  "se2_separable_tables", "se2_convolve_separable"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -137,6 +139,19 @@ class Plan:
     def launches(self) -> int:
         """Kernels launched through this plan so far (se2_plan_launches)."""
         return int(load_library().se2_plan_launches(self._h))
+
+    def timing(self, on: bool = True):
+        """Record per-launch durations of the FP32 fast path's units (and clear
+        earlier records); see timing_read."""
+        _check(load_library().se2_plan_timing(self._h, 1 if on else 0))
+
+    def timing_read(self):
+        """[(summed ms, launches)] for units 0 (kf_fwd_xt), 1 (kf_lines),
+        2 (kf_inv_tx) since timing was switched on."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_longlong * 3)()
+        _check(load_library().se2_plan_timing_read(self._h, ms, n))
+        return [(float(ms[i]), int(n[i])) for i in range(3)]
 
     def workspace_bytes(self) -> int:
         return int(load_library().se2_plan_workspace_bytes(self._h))

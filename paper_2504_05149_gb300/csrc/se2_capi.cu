@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/se2.h"
 #include "se2_internal.h"
@@ -92,6 +93,11 @@ struct se2_plan_s {
     KTable<double> kd;
     bool fused = false;
     unsigned long long launches = 0;   // kernels launched by this plan so far
+    // per-launch timing of the FP32 fast path's units (se2_plan_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;       // event pool, 2 per timed launch
+    std::vector<int> tkind;             // unit of each timed launch (0 A, 1 B, 2 C)
+    size_t tused = 0;                   // timed launches recorded
     // FP32 paired-FFT kernels for the convolution and chain (null: generic ones)
     bool fast = false;
     FastTable ft;
@@ -232,6 +238,9 @@ se2_status plan_init(se2_plan_s* p) {
 }
 
 void plan_free(se2_plan_s* p) {
+    for (cudaEvent_t ev : p->tev) cudaEventDestroy(ev);
+    p->tev.clear();
+    p->tkind.clear();
     for (int k = 0; k < kHostBufs; ++k) {
         if (p->hev_in[k]) cudaEventDestroy(p->hev_in[k]);
         if (p->hev_done[k]) cudaEventDestroy(p->hev_done[k]);
@@ -483,6 +492,27 @@ se2_status run_persist(se2_plan_s* p, const void* f, int B, const void* const* c
 // round-robin over pipe_depth streams forked from (and joined back into) st,
 // each stream with its own scratch slots; a group's three kernels stay in
 // order on its stream while groups on other streams overlap them.
+// Unit timing (se2_plan_timing): an event before and after a launch, on the
+// stream the launch runs on.  Returns the slot, or SIZE_MAX when not timing.
+constexpr size_t kMaxTimed = 32768;
+size_t time_begin(se2_plan_s* p, int kind, cudaStream_t s) {
+    if (!p->timing || p->tused >= kMaxTimed) return SIZE_MAX;
+    const size_t i = p->tused;
+    while (p->tev.size() < 2 * (i + 1)) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreate(&ev) != cudaSuccess) return SIZE_MAX;
+        p->tev.push_back(ev);
+    }
+    if (p->tkind.size() < i + 1) p->tkind.resize(i + 1);
+    p->tkind[i] = kind;
+    if (cudaEventRecord(p->tev[2 * i], s) != cudaSuccess) return SIZE_MAX;
+    p->tused = i + 1;
+    return i;
+}
+void time_end(se2_plan_s* p, size_t i, cudaStream_t s) {
+    if (i != SIZE_MAX) cudaEventRecord(p->tev[2 * i + 1], s);
+}
+
 se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* const* coeffs,
                           const double* const* log_scales, int k, float* out, cudaStream_t st,
                           const float2* sep_tables = nullptr) {
@@ -528,12 +558,18 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
                 a.ls[q] = (log_scales && log_scales[q]) ? log_scales[q] + c0 * lps : nullptr;
             }
         }
+        const size_t t0 = time_begin(p, 0, s);
         ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);
         ++p->launches;
+        time_end(p, t0, s);
+        const size_t t1 = time_begin(p, 1, s);
         (sep_tables != nullptr ? ft.lines_sep : ft.lines)<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);
         ++p->launches;
+        time_end(p, t1, s);
+        const size_t t2 = time_begin(p, 2, s);
         ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);
         ++p->launches;
+        time_end(p, t2, s);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -1203,6 +1239,34 @@ se2_status se2_debug_wait_timeout(se2_plan_t p, const void* f, const void* coeff
 }
 
 unsigned long long se2_plan_launches(se2_plan_t p) { return p == nullptr ? 0ull : p->launches; }
+
+se2_status se2_plan_timing(se2_plan_t p, int on) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    p->timing = on != 0;
+    p->tused = 0;
+    return SE2_OK;
+}
+
+se2_status se2_plan_timing_read(se2_plan_t p, double* ms, long long* count) {
+    se2_status st = check_plan(p);
+    if (st != SE2_OK) return st;
+    if (ms == nullptr || count == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    for (int u = 0; u < 3; ++u) {
+        ms[u] = 0.0;
+        count[u] = 0;
+    }
+    DeviceGuard guard(p->dev);
+    for (size_t i = 0; i < p->tused; ++i) {
+        cudaError_t e = cudaEventSynchronize(p->tev[2 * i + 1]);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p->tev[2 * i], p->tev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "timing events");
+        ms[p->tkind[i]] += t;
+        ++count[p->tkind[i]];
+    }
+    return SE2_OK;
+}
 
 se2_status se2_convolve(se2_plan_t p, const void* f, int B, const void* coeffs, const double* log_scale,
                         void* out, void* stream) {

@@ -465,3 +465,27 @@ def test_bounded_wait_times_out_and_plan_recovers(se2):
     plan.status()
     want = O.convolve(F[0].astype(np.float64), P[0].astype(np.float64))
     assert _rel(out[0].double().cpu().numpy(), want) < 1e-5
+
+
+def test_unit_timing_counts_launches(se2):
+    """se2_plan_timing: every unit launch of the FP32 fast path is timed on
+    its own stream; counts match the launches and durations are positive."""
+    N, M, B = 64, 32, 6
+    plan = se2.Plan(N, M, batch=B)
+    f = torch.rand((B, M, N, N), device="cuda")
+    C, _ = se2.coeffs(plan, torch.rand((B, M, N, N), device="cuda"))
+    out = torch.empty_like(f)
+    plan.timing(True)
+    n0 = plan.launches()
+    for _ in range(3):
+        se2.convolve(plan, f, C, out=out)
+    torch.cuda.synchronize()
+    stats = plan.timing_read()
+    plan.timing(False)
+    launched = plan.launches() - n0
+    assert sum(c for _, c in stats) == launched
+    assert stats[0][1] == stats[1][1] == stats[2][1] > 0
+    assert all(ms > 0 for ms, _ in stats)
+    plan.timing(True)           # switching on again clears the records
+    assert plan.timing_read() == [(0.0, 0), (0.0, 0), (0.0, 0)]
+    plan.timing(False)
