@@ -70,13 +70,6 @@ typedef enum {
 
 /* Plan flags */
 #define SE2_SHARED_KERNEL 0x1u  /* one coefficient array serves the whole batch */
-/* Mass renormalisation in FP64 (se2_convolve and se2_convolve_chain): the
- * total mass of each output, sum(out), is set to its exact value
- * sum(f) * C_1[0] ... C_k[0] * exp(sum of the log-scales) (the DC bin of the
- * product, Eq. MatSqKfgG; W = 1 there) by adding the difference, spread
- * evenly, to every sample.  Both sums are taken in FP64 on the device.  Costs
- * one extra read of f and a read-modify-write of out. */
-#define SE2_MASS_RENORM   0x8u
 #define SE2_PERSISTENT    0x2u  /* FP32: run se2_convolve(_chain) as one persistent dataflow kernel */
 /* Grids (f, kernel samples, output) sampled at x_i = i/N instead of on
  * Omega_L (x_i = -1/2 + i/N, Eq. OmL), theta unchanged.  The rectangle rule of
@@ -87,6 +80,15 @@ typedef enum {
  * the kernel samplers (se2_sample_radial_gaussian, se2_separable_tables)
  * sample at x_i = i/N.  se2_coeffs is unaffected (C = DFT(P)/|L| either way). */
 #define SE2_GRID_ORIGIN_ZERO 0x4u
+/* Mass renormalisation in FP64 (se2_convolve and se2_convolve_chain): the
+ * total mass of each output, sum(out), is set to its exact value
+ * sum(f) * C_1[0] ... C_k[0] * exp(sum of the log-scales) (the DC bin of the
+ * product, Eq. MatSqKfgG; W = 1 there) by adding the difference, spread
+ * evenly, to every sample; the rounding residual of each stored sample is
+ * carried to the next one, so the stored samples keep the mass to about
+ * 1e-10 relative.  Both sums are taken in FP64 on the device.  Costs one
+ * extra read of f and a read-modify-write of out. */
+#define SE2_MASS_RENORM   0x8u
 
 /*
  * se2_plan_create -- validate sizes, build FP64-accurate twiddle tables and
