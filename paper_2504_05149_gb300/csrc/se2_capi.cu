@@ -826,8 +826,9 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (p->persist && p->slots > (int)chunk) p->slots = (int)chunk;
     // at least two slots: the adjoint transforms grad_out and f side by side
     p->nslots = chunk < 2 ? 2 : (int)chunk;
-    e = cudaMalloc(&p->scratch, per * p->nslots);
-    if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "scratch (%zu bytes): %s", per * p->nslots, cudaGetErrorString(e)); }
+    const size_t scratch_bytes = per * p->nslots;
+    e = cudaMalloc(&p->scratch, scratch_bytes);
+    if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "scratch (%zu bytes): %s", scratch_bytes, cudaGetErrorString(e)); }
     if (p->fast) {
         // pipelined groups (SE2_PIPE_DEPTH / SE2_PIPE_GROUP in the environment
         // override the defaults); depth * group scratch slots must exist
