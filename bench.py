@@ -51,6 +51,8 @@ def parse():
                          "e4: the paper's single-convolution experiment, L = (31, 33, 61) sampled, "
                          "output on 36 x 38 x 76 (grid plan, odd sizes, upsampled)")
     ap.add_argument("--grid-batch", type=int, default=1024, help="e4 batch size")
+    ap.add_argument("--ysym", action="store_true",
+                    help="c2: declare the (radial) kernel spectra mirror-symmetric in y (SE2_KERNEL_YSYM)")
     ap.add_argument("--problems", type=int, default=4096, help="c4 batch size")
     ap.add_argument("--precision", default="f32", choices=["f32", "split_bf16", "split_f16", "bf16"],
                     help="c2: arithmetic of the angular DFT (tensor cores for split_bf16 / split_f16 / bf16)")
@@ -229,7 +231,8 @@ def main():
     L = N * N * M
 
     F, P = workload_inputs(N, M, B, rank)
-    plan = se2.Plan(N, M, batch=B, precision=args.precision, device=local)
+    plan = se2.Plan(N, M, batch=B, precision=args.precision, device=local,
+                    flags=se2.KERNEL_YSYM if args.ysym else 0)
     f = torch.from_numpy(F).to(dev)
     C, _ = se2.coeffs(plan, torch.from_numpy(P).to(dev))
     out = torch.empty_like(f)
@@ -340,7 +343,8 @@ def main():
                               "max_rel_diff_vs_se2": agree}}
 
     hbm, src = peaks()
-    alg_bytes = B * (4 * L + 4 * L + 8 * M * N * (N // 2 + 1))   # read f, write out, read half spectrum
+    c_rows = N // 2 + 1 if args.ysym else N                        # kernel-spectrum rows read per problem
+    alg_bytes = B * (4 * L + 4 * L + 8 * M * c_rows * (N // 2 + 1))   # read f, write out, read the spectrum
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
 
     line = None
@@ -355,7 +359,7 @@ def main():
             "config": {**c2_config(N, M, B, world),
                        "l2": f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB moved per step)"},
             "roofline": kernel_roofline(unit_stats, N, M, B, args.steps, hbm, src, achieved, alg_bytes,
-                                        args.precision),
+                                        args.precision, c_rows),
             "cpu_baseline": base,
             "e2e": {"value": e2e_val, "unit": "conv/s", "h2d_bytes_per_step": int(F.nbytes),
                     "d2h_bytes_per_step": int(F.nbytes)},
@@ -385,7 +389,7 @@ NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.602304 + 0.463360) * 1e6, (71.6
 UNIT_NAMES = ("kf_fwd_xt", "kf_lines", "kf_inv_tx")
 
 
-def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_bytes, precision):
+def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_bytes, precision, c_rows=None):
     """Roofline of the dominant kernel from live per-launch durations.
     Algorithmic bytes per problem: kf_fwd_xt reads f (4|L|), kf_lines reads
     the kernel spectrum (8 M N (N/2+1)), kf_inv_tx writes out (4|L|); the
@@ -393,7 +397,7 @@ def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_by
     L = N * N * M
     step = {"scope": "whole se2_convolve step (all kernels)", "achieved": step_achieved,
             "frac": step_achieved / hbm, "alg_bytes_per_conv": step_bytes / B, **traffic_fields(N, M, precision)}
-    per_problem = (4 * L, 8 * M * N * (N // 2 + 1), 4 * L)
+    per_problem = (4 * L, 8 * M * (N if c_rows is None else c_rows) * (N // 2 + 1), 4 * L)
     kern = []
     for name, bpp, (tms, cnt) in zip(UNIT_NAMES, per_problem, unit_stats):
         if cnt == 0:
@@ -410,7 +414,7 @@ def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_by
     dom = max(kern, key=lambda d: d["total_ms"])
     tr = NCU_TRAFFIC_PER_LAUNCH.get((N, M, precision))
     ti = UNIT_NAMES.index(dom["kernel"])
-    traffic = tr[ti] if (tr is not None and abs(dom["problems_per_launch"] - 2) < 1e-9) else None
+    traffic = tr[ti] if (tr is not None and abs(dom["problems_per_launch"] - 2) < 1e-9 and c_rows in (None, N)) else None
     return {"bound": "hbm", "achieved": dom["achieved"], "peak": hbm, "unit": "GB/s", "frac": dom["frac"],
             "peak_source": src, "kernel": dom["kernel"], "avg_launch_ms": dom["avg_launch_ms"],
             "alg_bytes_per_launch": dom["alg_bytes_per_launch"], "traffic": traffic,

@@ -89,6 +89,13 @@ typedef enum {
  * 1e-10 relative.  Both sums are taken in FP64 on the device.  Costs one
  * extra read of f and a read-modify-write of out. */
 #define SE2_MASS_RENORM   0x8u
+/* The kernel spectra are mirror-symmetric in y, C(kt, ky, kx) = C(kt, N - ky, kx),
+ * as for every kernel radial in translations sampled on Omega_L (or at
+ * x_i = i/N): y_j -> -y_j maps the grid to itself.  The FP32 fast path of
+ * se2_convolve and se2_convolve_chain then reads only the rows ky <= N/2 of
+ * each coefficient array, about half of its bytes; the other paths read all
+ * rows.  Results for kernels without the symmetry are undefined. */
+#define SE2_KERNEL_YSYM   0x10u
 
 /*
  * se2_plan_create -- validate sizes, build FP64-accurate twiddle tables and

@@ -31,6 +31,7 @@ SHARED_KERNEL = 0x1
 PERSISTENT = 0x2
 GRID_ORIGIN_ZERO = 0x4        # grids sampled at x_i = i/N: the plain cyclic convolution (no W)
 MASS_RENORM = 0x8             # FP64 mass renormalisation of convolve / convolve_chain outputs
+KERNEL_YSYM = 0x10            # kernel spectra mirror-symmetric in y (radial kernels): half the C rows read
 
 _STATUS = {0: "SE2_OK", 1: "SE2_ERR_INVALID_ARG", 2: "SE2_ERR_UNSUPPORTED", 3: "SE2_ERR_OOM",
            4: "SE2_ERR_CUDA", 5: "SE2_ERR_TIMEOUT", 6: "SE2_ERR_NUMERIC"}
@@ -588,4 +589,5 @@ __all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_
            "sample_radial_gaussian", "sample_se2_gaussian", "sample_deformed_gaussian",
            "GridPlan", "grid_coeffs", "grid_convolve_chain", "grid_convolve_chain_all", "accuracy_order", "ffc_at", "ffc_convergence",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
-           "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO", "MASS_RENORM"]
+           "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO", "MASS_RENORM",
+           "KERNEL_YSYM"]

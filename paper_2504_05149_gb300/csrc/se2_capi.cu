@@ -548,6 +548,7 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
         a.ls_pstride = lps;
         a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
         a.wsign = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0 : 1;
+        a.ymirror = (p->flags & SE2_KERNEL_YSYM) ? 1 : 0;
         if (sep_tables != nullptr) {
             const long long tps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)(p->N / 2 + 1 + p->N + p->M);
             a.sep = sep_tables + c0 * tps;
@@ -786,7 +787,7 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (precision != SE2_F32 && precision != SE2_F64 && precision != SE2_SPLIT_BF16 && precision != SE2_BF16 &&
         precision != SE2_SPLIT_F16)
         return fail(SE2_ERR_UNSUPPORTED, "precision %d not supported", (int)precision);
-    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT | SE2_GRID_ORIGIN_ZERO | SE2_MASS_RENORM))
+    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT | SE2_GRID_ORIGIN_ZERO | SE2_MASS_RENORM | SE2_KERNEL_YSYM))
         return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);

@@ -252,6 +252,7 @@ struct FArgs {
     double* grad_params;
     int want_grad;
     int wsign;                   // 1: apply W (grids on Omega_L); 0: grids at x_i = i/N
+    int ymirror;                 // 1: C(ky) = C(N - ky) is promised; rows ky > N/2 are not read
     // running-product y pass (kf_lines<.., FL_ACC>): s holds the full spectrum
     // product R_{p-1} in ky order; R_p = R_{p-1} C_p is stored back and the
     // inverse y FFT of W^p R_p exp(sum_{i<=p} ls_i) / |L| goes to sout
@@ -589,15 +590,19 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
         // coefficient loads in chunks of CK bins (the adjoint keeps fewer in flight)
         constexpr int CK = MODE == FL_ADJ ? R2 / 2 : R2;
         const int i0 = MODE == FL_ACC ? a.p - 1 : 0, i1 = SEP ? 0 : (MODE == FL_ACC ? a.p : a.k);
+        const bool ym = a.ymirror != 0;
         for (int i = i0; i < i1; ++i) {
-            const float2* cb = a.C[i] + (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa + (size_t)t * CP;
+            const float2* cb = a.C[i] + (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa;
 #pragma unroll
             for (int k0 = 0; k0 < R2; k0 += CK) {
                 float2 ca[CK], cq[CK];
 #pragma unroll
                 for (int kk = 0; kk < CK; ++kk) {
-                    ca[kk] = __ldcs(cb + (size_t)(R1 * (k0 + kk)) * CP);
-                    cq[kk] = hasb ? __ldcs(cb + (size_t)(R1 * (k0 + kk)) * CP + Q) : pf(0.f, 0.f);
+                    // row ky of this lane's bin, folded to N - ky for mirror-symmetric kernels
+                    int row = t + R1 * (k0 + kk);
+                    if (ym && row > N / 2) row = N - row;
+                    ca[kk] = __ldcs(cb + (size_t)row * CP);
+                    cq[kk] = hasb ? __ldcs(cb + (size_t)row * CP + Q) : pf(0.f, 0.f);
                 }
 #pragma unroll
                 for (int kk = 0; kk < CK; ++kk) {

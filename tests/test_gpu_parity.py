@@ -489,3 +489,25 @@ def test_unit_timing_counts_launches(se2):
     plan.timing(True)           # switching on again clears the records
     assert plan.timing_read() == [(0.0, 0), (0.0, 0), (0.0, 0)]
     plan.timing(False)
+
+
+@pytest.mark.parametrize("N,M,k", [(256, 64, 1), (64, 32, 3), (32, 16, 2)])
+def test_kernel_ysym_flag_reads_half_the_rows(se2, N, M, k):
+    """SE2_KERNEL_YSYM with radial kernels (mirror-symmetric in y on Omega_L):
+    the same result as the full read, against the oracle; the rows ky > N/2
+    are not read (they are overwritten with NaN here)."""
+    B = 2
+    kps = [synth.KernelParams(0.02 + 0.01 * i, 0.2 + 0.1 * i, 0.3 * i) for i in range(k)]
+    Fs = [synth.sample_bumps(N, M, synth.make_problem(9, b, N, M, n_bumps=4).bumps).astype(np.float32)
+          for b in range(B)]
+    Ps = [synth.sample_kernel(N, M, kp).astype(np.float32) for kp in kps]
+    plan = se2.Plan(N, M, batch=B, flags=se2.KERNEL_YSYM)
+    Cs = []
+    for P in Ps:
+        C, _ = se2.coeffs(plan, _dev(np.stack([P] * B), "f32"))
+        C[:, :, N // 2 + 1:, :] = float("nan")
+        Cs.append(C)
+    out = se2.convolve_chain(plan, _dev(np.stack(Fs), "f32"), Cs).double().cpu().numpy()
+    for b in range(B):
+        want = O.convolve_chain(Fs[b].astype(np.float64), [P.astype(np.float64) for P in Ps])
+        assert _rel(out[b], want) < 1e-5
