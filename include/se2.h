@@ -163,9 +163,10 @@ se2_status se2_convolve_chain(se2_plan_t plan, const void* f, int B,
  * the fast recursion): V_p = f * rho_1 * ... * rho_p for p = 1..k from one
  * forward transform, V_p = iDFT(W^p . DFT(f) . C_1 ... C_p) exp(ls_1 + ... + ls_p).
  * Arguments as se2_convolve_chain; out is [k][B][M][N][N] (V_p at p - 1).
- * FP32 plans with N in {32, 64, 128, 256} only (SE2_ERR_UNSUPPORTED
- * otherwise); B must fit half the plan's scratch slots (the running product
- * and its inverse y transform live side by side), larger B runs in groups.
+ * On the FP32 fast path (N in {32, 64, 128, 256}) B runs in groups of half
+ * the plan's scratch slots (the running product and its inverse y transform
+ * live side by side).  Other plans (FP64, N = 512, tensor-core precisions)
+ * compute each V_p as its own chain of the first p kernels.
  */
 se2_status se2_convolve_chain_all(se2_plan_t plan, const void* f, int B, const void* const* coeffs,
                                   const double* const* log_scales, int k, void* out, void* stream);

@@ -1011,8 +1011,8 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
     if (f == nullptr || out == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
     if (B < 1 || B > p->batch) return fail(SE2_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, p->batch);
     if (k < 1 || k > kMaxChain) return fail(SE2_ERR_INVALID_ARG, "chain length k=%d outside [1, %d]", k, kMaxChain);
-    if (!p->fast) return fail(SE2_ERR_UNSUPPORTED, "the emit-all chain needs an FP32 plan with N in {32..256}");
-    if (!aligned(f, 4) || !aligned(out, 4)) return fail(SE2_ERR_INVALID_ARG, "misaligned f/out");
+    const size_t re = p->elem / 2;
+    if (!aligned(f, re) || !aligned(out, re)) return fail(SE2_ERR_INVALID_ARG, "misaligned f/out");
     for (int i = 0; i < k; ++i) {
         if (coeffs[i] == nullptr) return fail(SE2_ERR_INVALID_ARG, "coeffs[%d] is NULL", i);
         if (!aligned(coeffs[i], p->elem)) return fail(SE2_ERR_INVALID_ARG, "coeffs[%d] misaligned", i);
@@ -1020,9 +1020,20 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
     }
     const size_t gs = (size_t)p->N * p->N * p->M;
     const uintptr_t fa = (uintptr_t)f, oa = (uintptr_t)out;
-    if (fa < oa + gs * 4 * (size_t)k * B && oa < fa + gs * 4 * (size_t)B) return fail(SE2_ERR_INVALID_ARG, "out overlaps f");
+    if (fa < oa + gs * re * (size_t)k * B && oa < fa + gs * re * (size_t)B) return fail(SE2_ERR_INVALID_ARG, "out overlaps f");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
+    if (!p->fast) {
+        // without the FP32 fast path (FP64, N = 512, the tensor-core modes):
+        // each V_p as its own chain of the first p kernels
+        for (int q = 1; q <= k; ++q) {
+            unsigned char* op = static_cast<unsigned char*>(out) + (size_t)(q - 1) * B * gs * re;
+            st = !is_f64(p) ? run_chain<float>(p, f, B, coeffs, log_scales, q, op, s)
+                            : run_chain<double>(p, f, B, coeffs, log_scales, q, op, s);
+            if (st != SE2_OK) return st;
+        }
+        return SE2_OK;
+    }
     const FastTable& ft = p->ft;
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
     const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;

@@ -105,11 +105,8 @@ def test_all_six_powers_with_gbs0_kernel(se2, prec):
     H = [[1 / 0.0143, 0.0], [0.0, 1 / 0.0014]]
     f, rho, F, P = _inputs(se2, plan, H, 0.0071, math.pi / 7, 0.0029)
     C, ls = se2.coeffs(plan, rho, normalize=(prec == "f32"))
-    if prec == "f32":
-        out = se2.convolve_chain_all(plan, f, [C] * 6, [ls] * 6)
-        out = out[:, 0].double().cpu().numpy()
-    else:  # the emit-all entry point is FP32 only: one chain per power
-        out = [se2.convolve_chain(plan, f, [C] * p)[0].double().cpu().numpy() for p in range(1, 7)]
+    out = se2.convolve_chain_all(plan, f, [C] * 6, None if ls is None else [ls] * 6)
+    out = out[:, 0].double().cpu().numpy()
     want = O.convolve_all(F, [P] * 6)
     for p in range(6):
         assert _rel(out[p], want[p]) < TOL[prec], p
