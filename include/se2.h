@@ -274,14 +274,16 @@ unsigned long long se2_plan_launches(se2_plan_t plan);
 
 /*
  * se2_plan_timing / se2_plan_timing_read -- per-launch durations of the FP32
- * fast path's three units (0: forward x and theta transforms, kf_fwd_xt;
- * 1: y pass with the product, kf_lines; 2: inverse theta and x transforms,
- * kf_inv_tx).  With timing on, each unit launch is bracketed by CUDA events
- * recorded on the stream it runs on (the pipeline's own streams included);
- * se2_plan_timing(plan, 1) also clears what was recorded.  _read waits for
- * the recorded events and returns, per unit, the summed milliseconds ms[3]
- * and the launch counts count[3] (host arrays).  Not for use while a stream
- * is being captured into a CUDA graph.  Up to 32768 launches are recorded.
+ * fast path's kernels (0: forward x and theta transforms, kf_fwd_xt /
+ * kf2_fwd_xt; 1: y pass with the product, kf_lines; 2: inverse theta and x
+ * transforms, kf_inv_tx / kf2_inv_tx; 3: the whole-batch dataflow kernel
+ * kflow_conv, which runs all three units).  With timing on, each launch is
+ * bracketed by CUDA events recorded on the stream it runs on (the pipeline's
+ * own streams included); se2_plan_timing(plan, 1) also clears what was
+ * recorded.  _read waits for the recorded events and returns, per kind, the
+ * summed milliseconds ms[4] and the launch counts count[4] (host arrays).
+ * Not for use while a stream is being captured into a CUDA graph.  Up to
+ * 32768 launches are recorded.
  */
 se2_status se2_plan_timing(se2_plan_t plan, int on);
 se2_status se2_plan_timing_read(se2_plan_t plan, double* ms, long long* count);

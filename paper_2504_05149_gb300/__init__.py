@@ -149,10 +149,10 @@ class Plan:
     def timing_read(self):
         """[(summed ms, launches)] for units 0 (kf_fwd_xt), 1 (kf_lines),
         2 (kf_inv_tx) since timing was switched on."""
-        ms = (ctypes.c_double * 3)()
-        n = (ctypes.c_longlong * 3)()
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_longlong * 4)()
         _check(load_library().se2_plan_timing_read(self._h, ms, n))
-        return [(float(ms[i]), int(n[i])) for i in range(3)]
+        return [(float(ms[i]), int(n[i])) for i in range(4)]
 
     def workspace_bytes(self) -> int:
         return int(load_library().se2_plan_workspace_bytes(self._h))

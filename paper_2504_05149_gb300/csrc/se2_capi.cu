@@ -3,6 +3,7 @@
 // Host side: argument validation, plan (twiddle tables, scratch), and the
 // launch sequences of Algorithm 3 (se2_convolve), Algorithms 4/6
 // (se2_convolve_chain) and the coefficient transform (se2_coeffs, Eq. FkLv).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -113,6 +114,8 @@ struct se2_plan_s {
     void* hstage = nullptr;
     cudaStream_t hin = nullptr, hout = nullptr;
     cudaEvent_t hev_start = nullptr, hev_in[kHostBufs] = {}, hev_done[kHostBufs] = {}, hev_out[kHostBufs] = {};
+    // tensor maps of the dataflow kernel's B items over the scratch
+    CUtensorMap tm_blk{}, tm_nyq{};
 };
 
 bool se2::get_fast(int N, int M, FastTable* t) {
@@ -225,6 +228,21 @@ se2_status plan_init(se2_plan_s* p) {
                 r = cudaFuncSetAttribute((const void*)p->ft.lines_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
             if (r == cudaSuccess)
                 r = cudaFuncSetAttribute((const void*)p->ft.lines_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_y);
+            // The bulk-copy units A and C are opt-in (SE2_FAST2=1, or "a" / "c"
+            // for one of them): measured inside the two-stream pipeline they are
+            // 1-4% slower than the original units.
+            const char* f2 = getenv("SE2_FAST2");
+            if (!(f2 && (f2[0] == '1' || f2[0] == 'a'))) p->ft.fwd2 = nullptr;
+            if (!(f2 && (f2[0] == '1' || f2[0] == 'c'))) p->ft.inv2 = nullptr;
+            const char* fl = getenv("SE2_FLOW");   // the whole-batch dataflow kernel is opt-in
+            if (!(fl && fl[0] == '1')) p->ft.flow = nullptr;
+            if (r == cudaSuccess && p->ft.flow != nullptr)
+                r = cudaFuncSetAttribute((const void*)p->ft.flow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_flow);
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev);
+            if (r == cudaSuccess && p->ft.fwd2 != nullptr)
+                r = cudaFuncSetAttribute((const void*)p->ft.fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_xt2);
+            if (r == cudaSuccess && p->ft.inv2 != nullptr)
+                r = cudaFuncSetAttribute((const void*)p->ft.inv2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->ft.smem_xt2);
             if (r != cudaSuccess) return cuda_fail(r, "cudaFuncSetAttribute");
             p->fast = true;
         }
@@ -513,9 +531,101 @@ void time_end(se2_plan_s* p, size_t i, cudaStream_t s) {
     if (i != SIZE_MAX) cudaEventRecord(p->tev[2 * i + 1], s);
 }
 
+// Units A and C of the FP32 fast path: the bulk-copy kernels where they
+// exist and the grid is 16-byte aligned, the original ones otherwise.
+void launch_unit_a(const FastTable& ft, int N, int nb, cudaStream_t s, const FArgs& a) {
+    if (ft.fwd2 != nullptr && aligned(a.f, 16))
+        ft.fwd2<<<dim3(N, nb), kThreads, ft.smem_xt2, s>>>(a);
+    else
+        ft.fwd<<<dim3(N, nb), kThreads, ft.smem_xt, s>>>(a);
+}
+void launch_unit_c(const FastTable& ft, int N, int nb, cudaStream_t s, const FArgs& a) {
+    if (ft.inv2 != nullptr && aligned(a.out, 16))
+        ft.inv2<<<dim3(N, nb), kThreads, ft.smem_xt2, s>>>(a);
+    else
+        ft.inv<<<dim3(N, nb), kThreads, ft.smem_xt, s>>>(a);
+}
+
+// Tensor maps of the dataflow kernel over the scratch [nslots M][N][4 tp/2
+// floats]: boxes of 16 entries x N rows x 1 theta bin (B items of entry
+// blocks) and 1 entry x N rows x 16 bins (Nyquist items).  The encoder is
+// the driver's, reached through the runtime (no link to the driver library).
+bool encode_flow_maps(se2_plan_s* p) {
+    using Enc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                             const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                             CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr)
+        return false;
+    const Enc enc = (Enc)fn;
+    const cuuint64_t row4 = (cuuint64_t)p->tp / 2;   // float4 entries per scratch row
+    const cuuint64_t dims[3] = {row4 * 4, (cuuint64_t)p->N, (cuuint64_t)p->nslots * p->M};
+    const cuuint64_t strides[2] = {row4 * 16, (cuuint64_t)p->N * row4 * 16};
+    const cuuint32_t box_blk[3] = {4 * kFlowLines, (cuuint32_t)p->N, 1}, box_nyq[3] = {4, (cuuint32_t)p->N, kFlowLines};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r1 = enc(&p->tm_blk, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->scratch, dims, strides, box_blk, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUresult r2 = enc(&p->tm_nyq, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->scratch, dims, strides, box_nyq, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
+}
+
+// The convolution (or chain) of B problems as one persistent dataflow launch
+// (se2_flow.cuh): units A, B, C of every problem in one kernel, problems in
+// flight in the plan's scratch slots.
+bool flow_usable(const se2_plan_s* p, int B, const float* f, const float* out) {
+    const int slots = p->nslots < kFlowSlots ? p->nslots : kFlowSlots;
+    return p->ft.flow != nullptr && aligned(f, 16) && aligned(out, 16) && (slots >= 3 || B <= slots);
+}
+se2_status run_flow(se2_plan_s* p, const float* f, int B, const void* const* coeffs, const double* const* log_scales,
+                    int k, float* out, cudaStream_t st) {
+    const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
+    const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
+    FlowArgs fa{};
+    FArgs& a = fa.a;
+    a.err = p->err;
+    a.f = f;
+    a.out = out;
+    a.s = (float4*)p->scratch;
+    a.s_pstride = (long long)(p->s_pstride / 2);
+    a.twN = (const float2*)p->twN;
+    a.twM = (const float2*)p->twM;
+    a.k = k;
+    a.c_pstride = cps;
+    a.ls_pstride = lps;
+    a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
+    a.wsign = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0 : 1;
+    a.ymirror = (p->flags & SE2_KERNEL_YSYM) ? 1 : 0;
+    for (int q = 0; q < k; ++q) {
+        a.C[q] = (const float2*)coeffs[q];
+        a.ls[q] = (log_scales && log_scales[q]) ? log_scales[q] : nullptr;
+    }
+    fa.tm_blk = p->tm_blk;
+    fa.tm_nyq = p->tm_nyq;
+    fa.work = p->ctr;
+    fa.cnt = (int*)(p->ctr + 1);
+    fa.P = B;
+    fa.slots = p->nslots < kFlowSlots ? p->nslots : kFlowSlots;
+    cudaError_t e = cudaMemsetAsync(p->ctr, 0, sizeof(unsigned) * (1 + 3 * (size_t)B), st);
+    if (e != cudaSuccess) return cuda_fail(e, "counter reset");
+    int grid = p->nsm > 0 ? p->nsm : 1;
+    const size_t t = time_begin(p, 3, st);
+    p->ft.flow<<<grid, kFlowThreads, p->ft.smem_flow, st>>>(fa);
+    ++p->launches;
+    time_end(p, t, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
+}
+
 se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* const* coeffs,
                           const double* const* log_scales, int k, float* out, cudaStream_t st,
                           const float2* sep_tables = nullptr) {
+    if (sep_tables == nullptr && flow_usable(p, B, f, out)) return run_flow(p, f, B, coeffs, log_scales, k, out, st);
     const FastTable& ft = p->ft;
     const size_t g = (size_t)p->N * p->N * p->M;
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
@@ -537,6 +647,7 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
         const int d = i % depth;
         cudaStream_t s = d == 0 ? st : p->aux[d];
         FArgs a{};
+        a.err = p->err;
         a.f = f + c0 * g;
         a.out = out + c0 * g;
         a.s = (float4*)p->scratch + (size_t)d * group * (p->s_pstride / 2);
@@ -560,7 +671,7 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
             }
         }
         const size_t t0 = time_begin(p, 0, s);
-        ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);
+        launch_unit_a(ft, p->N, nb, s, a);
         ++p->launches;
         time_end(p, t0, s);
         const size_t t1 = time_begin(p, 1, s);
@@ -568,7 +679,7 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
         ++p->launches;
         time_end(p, t1, s);
         const size_t t2 = time_begin(p, 2, s);
-        ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);
+        launch_unit_c(ft, p->N, nb, s, a);
         ++p->launches;
         time_end(p, t2, s);
     }
@@ -658,6 +769,7 @@ se2_status run_backward_fast(se2_plan_s* p, const float* g, const float* f, int 
     for (int c0 = 0; c0 < B; c0 += per_pass) {
         const int nb = (B - c0 < per_pass) ? (B - c0) : per_pass;
         FArgs a{};
+        a.err = p->err;
         a.s_pstride = (long long)(p->s_pstride / 2);
         a.twN = (const float2*)p->twN;
         a.twM = (const float2*)p->twM;
@@ -667,12 +779,12 @@ se2_status run_backward_fast(se2_plan_s* p, const float* g, const float* f, int 
         float4* s1 = s0 + (size_t)nb * (p->s_pstride / 2);
         a.f = g + c0 * gs;
         a.s = s0;
-        ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+        launch_unit_a(ft, p->N, nb, st, a);
         ++p->launches;
         if (n_params > 0) {
             a.f = f + c0 * gs;
             a.s = s1;
-            ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+            launch_unit_a(ft, p->N, nb, st, a);
             ++p->launches;
             ft.lines_fwd<<<dim3(yb, nb), kThreads, ft.smem_y, st>>>(a);
             ++p->launches;
@@ -692,7 +804,7 @@ se2_status run_backward_fast(se2_plan_s* p, const float* g, const float* f, int 
         ++p->launches;
         if (grad_f) {
             a.out = grad_f + c0 * gs;
-            ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, st>>>(a);
+            launch_unit_c(ft, p->N, nb, st, a);
             ++p->launches;
         }
     }
@@ -830,6 +942,7 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     const size_t scratch_bytes = per * p->nslots;
     e = cudaMalloc(&p->scratch, scratch_bytes);
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "scratch (%zu bytes): %s", scratch_bytes, cudaGetErrorString(e)); }
+    if (p->fast && p->ft.flow != nullptr && !encode_flow_maps(p)) p->ft.flow = nullptr;   // keep the pipelined units
     if (p->fast) {
         // pipelined groups (SE2_PIPE_DEPTH / SE2_PIPE_GROUP in the environment
         // override the defaults); depth * group scratch slots must exist
@@ -1043,6 +1156,7 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
     for (int c0 = 0; c0 < B; c0 += per_pass) {
         const int nb = (B - c0 < per_pass) ? (B - c0) : per_pass;
         FArgs a{};
+        a.err = p->err;
         a.s_pstride = (long long)(p->s_pstride / 2);
         a.twN = (const float2*)p->twN;
         a.twM = (const float2*)p->twM;
@@ -1060,7 +1174,7 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
         a.f = (const float*)f + c0 * gs;
         a.s = s0;
         a.sout = s1;
-        ft.fwd<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(a);       // x, theta
+        launch_unit_a(ft, p->N, nb, s, a);       // x, theta
         ++p->launches;
         ft.lines_fwd<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);     // y: the full spectrum of f
         ++p->launches;
@@ -1071,7 +1185,7 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
             FArgs c = a;
             c.s = s1;
             c.out = (float*)out + ((size_t)(q - 1) * B + c0) * gs;
-            ft.inv<<<dim3(p->N, nb), kThreads, ft.smem_xt, s>>>(c);
+            launch_unit_c(ft, p->N, nb, s, c);
             ++p->launches;
         }
     }
@@ -1265,7 +1379,7 @@ se2_status se2_plan_timing_read(se2_plan_t p, double* ms, long long* count) {
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (ms == nullptr || count == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
-    for (int u = 0; u < 3; ++u) {
+    for (int u = 0; u < 4; ++u) {
         ms[u] = 0.0;
         count[u] = 0;
     }

@@ -23,6 +23,18 @@ bool fill_fast_nm(FastTable* t) {
         t->smem_xt = sx;
         t->smem_y = sy;
         t->lines_per_block = fast_lines<N>();
+        if constexpr (fast2_ok<N>()) {
+            constexpr size_t s2 = fast2_smem<N, M>();
+            if constexpr (s2 <= kMaxDynSmem) {
+                t->fwd2 = kf2_fwd_xt<N, M>;
+                t->inv2 = kf2_inv_tx<N, M>;
+                t->smem_xt2 = s2;
+            }
+        }
+        if constexpr (flow_ok<N, M>()) {
+            t->flow = kflow_conv<N, M>;
+            t->smem_flow = FlowGeom<N, M>::SMEM;
+        }
         return true;
     }
     return false;

@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "se2_fast.cuh"
+#include "se2_flow.cuh"
 
 namespace se2 {
 
@@ -60,6 +60,15 @@ struct FastTable {
        inv = nullptr;
     size_t smem_xt = 0, smem_y = 0;
     int lines_per_block = 0;
+    // units A and C with bulk row copies and the real-FFT split in registers
+    // (se2_fast2.cuh, N = 64, 256); they copy rows of f and out, so a call
+    // whose f (or out) is not 16-byte aligned runs fwd (or inv) instead
+    FK fwd2 = nullptr, inv2 = nullptr;
+    size_t smem_xt2 = 0;
+    // the whole convolution of a batch as one persistent dataflow launch
+    // (se2_flow.cuh); null where (N, M) has none
+    void (*flow)(FlowArgs) = nullptr;
+    size_t smem_flow = 0;
 };
 template <int N>
 bool get_fast_n(int M, FastTable* t);
