@@ -147,9 +147,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def cpu_baseline(N, M, seconds=12.0):
-    """The FP64 oracle (numpy FFT route, as it stands) on host cores: single
-    convolutions of the same workload with precomputed kernel spectra."""
+def _oracle_worker(args):
+    """Single convolutions of the oracle for `seconds` (one process)."""
+    N, M, seconds = args
     from oracle import se2_oracle as O
     import synth
     prob = synth.make_problem(2, 0, N, M, n_bumps=16, n_kernels=1)
@@ -162,9 +162,37 @@ def cpu_baseline(N, M, seconds=12.0):
         n += 1
         el = time.perf_counter() - t0
         if el >= seconds or n >= 64:
-            break
-    return {"value": n / el, "unit": "conv/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} single convolutions N={N} M={M} (numpy FFT route, FP64, precomputed kernel spectrum), {el:.1f} s"}
+            return n, el
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(N, M, seconds=10.0):
+    """The FP64 oracle (numpy FFT route, as it stands) on host cores: single
+    convolutions of the same workload with precomputed kernel spectra, on one
+    core, then one process per core (spawned) for the same time."""
+    import multiprocessing as mp
+    n1, el1 = _oracle_worker((N, M, seconds))
+    ncores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        res = pool.map(_oracle_worker, [(N, M, seconds)] * ncores)
+    total = sum(n / el for n, el in res)
+    return {"value": total, "unit": "conv/s", "cores": ncores, "kind": "oracle", "nproc": ncores,
+            "cpu_model": cpu_model(),
+            "single_core": {"value": n1 / el1, "unit": "conv/s", "cores": 1},
+            "sample": f"numpy FFT route, FP64, precomputed kernel spectrum: {n1} single convolutions N={N} M={M} "
+                      f"on one core in {el1:.1f} s; then {ncores} spawned processes, one per core, "
+                      f"{sum(n for n, _ in res)} convolutions in about {seconds:.0f} s"}
 
 
 METRIC_C2 = "SE(2) convolutions/s at N=256, M=64 (FP32) and fraction of HBM roofline"
@@ -232,7 +260,7 @@ def main():
 
     F, P = workload_inputs(N, M, B, rank)
     plan = se2.Plan(N, M, batch=B, precision=args.precision, device=local,
-                    flags=se2.KERNEL_YSYM if args.ysym else 0)
+                    flags=se2.HOST_STAGING | (se2.KERNEL_YSYM if args.ysym else 0))
     f = torch.from_numpy(F).to(dev)
     C, _ = se2.coeffs(plan, torch.from_numpy(P).to(dev))
     out = torch.empty_like(f)
@@ -282,13 +310,30 @@ def main():
 
     # per-kernel launch durations, live: a second pass of the same steps with
     # CUDA events around every unit launch, recorded by the library on the
-    # stream each launch runs on (FP32 fast path only)
+    # stream each launch runs on (FP32 fast path only).  In the pipeline two
+    # streams overlap, so these durations include the neighbour's contention.
     plan.timing(True)
     for _ in range(args.steps):
         se2.convolve(plan, f, C, out=out)
     torch.cuda.synchronize(dev)
     unit_stats = plan.timing_read()
     plan.timing(False)
+    # the same launches serialised (one stream, groups of 2 problems as in the
+    # pipeline): each kernel's own duration, the per-kernel roofline
+    splan = plan_with_env(se2, {"SE2_PIPE_DEPTH": "1", "SE2_MAX_CHUNK": "2"}, N, M, B, args.precision, local,
+                          se2.KERNEL_YSYM if args.ysym else 0)
+    for _ in range(2):
+        se2.convolve(splan, f, C, out=out)
+    ns = max(3, min(args.steps, 10))
+    splan.timing(True)
+    for _ in range(ns):
+        se2.convolve(splan, f, C, out=out)
+    torch.cuda.synchronize(dev)
+    unit_stats_serial = splan.timing_read()
+    splan.timing(False)
+    splan.close()
+    se2.convolve(plan, f, C, out=out)
+    out0 = out[0].double().cpu().numpy()
 
     # end to end through the public API with host buffers (se2_convolve_host):
     # pinned host f -> device, convolve, device -> host out, overlapped by groups
@@ -342,6 +387,12 @@ def main():
                                       "a comparator for context, not the product",
                               "max_rel_diff_vs_se2": agree}}
 
+    # mixed precision against plain FP32 on the same batch: conv/s and max-rel
+    # error against the FP64 oracle on problem 0
+    mixed = None
+    if args.precision == "f32" and rank == 0 and world == 1:
+        mixed = mixed_vs_fp32(se2, torch, dev, stream, N, M, B, F, P, f, value, out0, args)
+
     hbm, src = peaks()
     c_rows = N // 2 + 1 if args.ysym else N                        # kernel-spectrum rows read per problem
     alg_bytes = B * (4 * L + 4 * L + 8 * M * c_rows * (N // 2 + 1))   # read f, write out, read the spectrum
@@ -358,8 +409,9 @@ def main():
             "data": "synthetic",
             "config": {**c2_config(N, M, B, world),
                        "l2": f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB moved per step)"},
-            "roofline": kernel_roofline(unit_stats, N, M, B, args.steps, hbm, src, achieved, alg_bytes,
-                                        args.precision, c_rows),
+            "roofline": kernel_roofline(unit_stats_serial, N, M, B, ns, hbm, src, achieved, alg_bytes,
+                                        args.precision, c_rows, overlapped=(unit_stats, args.steps)),
+            "mixed_vs_fp32": mixed,
             "cpu_baseline": base,
             "e2e": {"value": e2e_val, "unit": "conv/s", "h2d_bytes_per_step": int(F.nbytes),
                     "d2h_bytes_per_step": int(F.nbytes)},
@@ -374,26 +426,79 @@ def main():
         dist.destroy_process_group()
 
 
-# DRAM bytes per convolution of the FP32 paired kernels at 256^2 x 64: the sum
-# of dram__bytes_read.sum + dram__bytes_write.sum of kf_fwd_xt, kf_lines and
-# kf_inv_tx from one `ncu --set full` capture (one launch each, 2 problems
-# per launch), profiles/kf_units_f32_256x256x64_b4_full.md.  ncu flushes the
-# caches before each kernel, so the scratch that the live run keeps in L2 is
-# counted as DRAM traffic: an upper bound.
-NCU_TRAFFIC_PER_CONV = {(256, 64, "f32"): (33.602304 + 0.463360 + 71.602688 + 1.382656 + 37.777408 + 1.117184) * 1e6 / 2}
+def plan_with_env(se2, env, N, M, B, precision, device, flags):
+    """A plan created with the given environment settings (read at creation)."""
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return se2.Plan(N, M, batch=B, precision=precision, device=device, flags=flags)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
-# The same capture per launch (2 problems): kf_fwd_xt, kf_lines, kf_inv_tx.
-NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.602304 + 0.463360) * 1e6, (71.602688 + 1.382656) * 1e6,
-                                             (37.777408 + 1.117184) * 1e6)}
+MIXED_BAR = 1e-5   # the accuracy at which mixed precision is compared with FP32
+
+
+def mixed_vs_fp32(se2, torch, dev, stream, N, M, B, F, P, f, f32_value, f32_out0, args):
+    """The tensor-core angular DFT modes (split fp16, split bf16: FP32 storage,
+    hi + lo operands, FP32 accumulation) against the plain FP32 path on the
+    same batch: conv/s, and max-rel error of problem 0 against the FP64
+    oracle; the fastest mode within MIXED_BAR is compared with FP32."""
+    from oracle import se2_oracle as O
+    want = O.convolve_chain(F[0].astype(np.float64), None, coeffs=[O.coeffs_full(P[0].astype(np.float64))])
+
+    def err(o):
+        return float(np.max(np.abs(o - want)) / np.max(np.abs(want)))
+
+    modes = {"f32": {"value": f32_value, "unit": "conv/s", "max_rel_err": err(f32_out0)}}
+    km = max(3, min(args.steps, 5))
+    for prec in ("split_f16", "split_bf16"):
+        plan = se2.Plan(N, M, batch=B, precision=prec, device=dev.index or 0)
+        Cm, _ = se2.coeffs(plan, torch.from_numpy(P).to(dev))
+        outm = torch.empty_like(f)
+        for _ in range(2):
+            se2.convolve(plan, f, Cm, out=outm)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(km):
+            se2.convolve(plan, f, Cm, out=outm)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        plan.status()
+        modes[prec] = {"value": B * km / (e0.elapsed_time(e1) / 1e3), "unit": "conv/s",
+                       "max_rel_err": err(outm[0].double().cpu().numpy())}
+        plan.close()
+    within = [m for m in modes if m != "f32" and modes[m]["max_rel_err"] <= MIXED_BAR]
+    best = max(within, key=lambda m: modes[m]["value"]) if within else None
+    return {**modes, "accuracy_bar": MIXED_BAR, "fastest_mixed_within_bar": best,
+            "mixed_beats_fp32": bool(best is not None and modes[best]["value"] > f32_value),
+            "what": f"split_f16 / split_bf16: tensor-core (tcgen05) angular DFT with hi + lo operands; "
+                    f"{km} timed steps of the same batch; errors of problem 0 against the FP64 oracle"}
+
+
+# DRAM bytes of the FP32 paired kernels at 256^2 x 64 per launch (2 problems):
+# dram__bytes_read.sum + dram__bytes_write.sum of kf_fwd_xt, kf_lines and
+# kf_inv_tx from one `ncu --set full` capture (profiles/kf_units_*).  ncu
+# flushes the caches before each kernel, so the scratch that the live run keeps
+# in L2 is counted as DRAM traffic: an upper bound.  None where the kernel has
+# changed since the capture.
+NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.602304 + 0.463360) * 1e6, None, (37.777408 + 1.117184) * 1e6)}
+NCU_TRAFFIC_PER_CONV = {k: (None if any(x is None for x in v) else sum(v) / 2) for k, v in NCU_TRAFFIC_PER_LAUNCH.items()}
 UNIT_NAMES = ("kf_fwd_xt", "kf_lines", "kf_inv_tx")
 
 
-def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_bytes, precision, c_rows=None):
-    """Roofline of the dominant kernel from live per-launch durations.
-    Algorithmic bytes per problem: kf_fwd_xt reads f (4|L|), kf_lines reads
-    the kernel spectrum (8 M N (N/2+1)), kf_inv_tx writes out (4|L|); the
-    scratch between them is not algorithmic."""
+def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_bytes, precision, c_rows=None,
+                    overlapped=None):
+    """Roofline of the dominant kernel from per-launch durations of a
+    serialised pass (each kernel alone on the GPU); `overlapped` = (stats,
+    steps) of the pipelined pass, reported beside them.  Algorithmic bytes
+    per problem: kf_fwd_xt reads f (4|L|), kf_lines reads the kernel spectrum
+    (8 M N (N/2+1)), kf_inv_tx writes out (4|L|); the scratch between them is
+    not algorithmic."""
     L = N * N * M
     step = {"scope": "whole se2_convolve step (all kernels)", "achieved": step_achieved,
             "frac": step_achieved / hbm, "alg_bytes_per_conv": step_bytes / B, **traffic_fields(N, M, precision)}
@@ -408,6 +513,14 @@ def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_by
         kern.append({"kernel": name, "launches": cnt, "avg_launch_ms": avg, "total_ms": tms,
                      "problems_per_launch": ppl, "alg_bytes_per_launch": bpp * ppl, "achieved": ach,
                      "frac": ach / hbm})
+    over = []
+    if overlapped is not None:
+        ostats, osteps = overlapped
+        for name, bpp, (tms, cnt) in zip(UNIT_NAMES, per_problem, ostats):
+            if cnt:
+                ppl = B * osteps / cnt
+                over.append({"kernel": name, "launches": cnt, "avg_launch_ms": tms / cnt,
+                             "frac": bpp * ppl / (tms / cnt / 1e3) / 1e9 / hbm})
     if not kern:   # not the FP32 fast path: the whole step only
         return {"bound": "hbm", "achieved": step_achieved, "peak": hbm, "unit": "GB/s",
                 "frac": step_achieved / hbm, "peak_source": src, **step}
@@ -420,8 +533,9 @@ def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_by
             "alg_bytes_per_launch": dom["alg_bytes_per_launch"], "traffic": traffic,
             "traffic_source": "ncu --set full, caches flushed (upper bound), per launch of 2 problems; "
                               "profiles/kf_units_f32_256x256x64_b4_full.md",
-            "timing": "CUDA events around each launch on its own stream, a second pass of the same steps",
-            "kernels": kern, "step": step}
+            "timing": "CUDA events around each launch, serialised pass (one stream, 2 problems per launch, "
+                      "no other kernel running); the pipelined step is roofline.step",
+            "kernels": kern, "kernels_overlapped": over, "step": step}
 
 
 def traffic_fields(N, M, precision):

@@ -26,10 +26,12 @@
  * Sizes: N in {8, 16, ..., 512}, M in {2, 4, ..., 128} (powers of two), B >= 1.
  *
  * Ownership and streams.  The caller owns every data buffer (device memory,
- * e.g. from PyTorch).  A plan owns only its twiddle tables and a scratch
- * workspace, allocated in se2_plan_create; no call below allocates.  Every
- * compute call is asynchronous on the caller's CUDA stream (`stream` is a
- * cudaStream_t; NULL = legacy default stream).
+ * e.g. from PyTorch).  A plan owns only its twiddle tables, its scratch
+ * workspace and (with SE2_HOST_STAGING) the staging of se2_convolve_host, all
+ * allocated in se2_plan_create; no call below allocates (grid plans: likewise
+ * in se2_grid_plan_create).  Every compute call is asynchronous on the
+ * caller's CUDA stream (`stream` is a cudaStream_t; NULL = legacy default
+ * stream).
  *
  * Errors.  Every call returns an se2_status and never aborts or traps.
  * Argument errors are found on the host before anything is launched.
@@ -92,10 +94,20 @@ typedef enum {
 /* The kernel spectra are mirror-symmetric in y, C(kt, ky, kx) = C(kt, N - ky, kx),
  * as for every kernel radial in translations sampled on Omega_L (or at
  * x_i = i/N): y_j -> -y_j maps the grid to itself.  The FP32 fast path of
- * se2_convolve and se2_convolve_chain then reads only the rows ky <= N/2 of
- * each coefficient array, about half of its bytes; the other paths read all
- * rows.  Results for kernels without the symmetry are undefined. */
+ * se2_convolve, se2_convolve_chain and se2_convolve_chain_all then reads only
+ * the rows ky <= N/2 of each coefficient array, about half of its bytes; the
+ * other paths read all rows.  Results for kernels without the symmetry are
+ * undefined. */
 #define SE2_KERNEL_YSYM   0x10u
+/* se2_convolve_host staging: three groups of f and out in device memory and
+ * two copy streams, allocated by se2_plan_create; se2_convolve_host needs a
+ * plan with this flag. */
+#define SE2_HOST_STAGING  0x20u
+/* Output check: after each se2_convolve / se2_convolve_chain /
+ * se2_convolve_chain_all / se2_convolve_separable / se2_backward call, one
+ * extra read of the output looks for NaN or infinity; if it finds one, the
+ * plan's error word records it and se2_plan_status returns SE2_ERR_NUMERIC. */
+#define SE2_CHECK_FINITE  0x40u
 
 /*
  * se2_plan_create -- validate sizes, build FP64-accurate twiddle tables and
@@ -264,6 +276,60 @@ se2_status se2_convolve_separable(se2_plan_t plan, const void* f, int B, const v
                                   void* stream);
 
 /*
+ * Batch plans: many independent problems of uneven sizes (Algorithm 3 for
+ * each problem, or Algorithm 4 / Eq. MatSqKfgG with a chain of separable
+ * radial kernels in factored form, as se2_convolve_separable).
+ *
+ * se2_batch_plan_create -- a plan over n_problems problems, problem i on an
+ * N x N x M grid given by shapes[i] (host array; each N, M as for
+ * se2_plan_create).  Problems are grouped into size classes (equal (N, M)),
+ * ordered by total work, largest first; each class gets its own plan, whose
+ * scratch holds at most 512 MiB of problems at a time.  flags: 0,
+ * SE2_GRID_ORIGIN_ZERO, SE2_CHECK_FINITE.  Synchronous.  Errors: as
+ * se2_plan_create.
+ *
+ * Packed layout.  All grids of the batch live in one array and all tables in
+ * another, class by class in class order and, inside a class, in the order of
+ * `shapes`.  se2_batch_plan_layout returns, per problem (host arrays of
+ * n_problems, each may be NULL): its position in that order, the offset of
+ * its grid ([M][N][N] real elements) and of its tables (N/2+1+N+M complex
+ * elements), and the two totals.  params and k of se2_batch_separable_tables
+ * are indexed by position.
+ *
+ * se2_batch_separable_tables -- se2_separable_tables for every class:
+ *   params  device, [n][kmax][3] double (sigma, sigma_theta, nu), by position
+ *   k       device, [n] int, chain lengths 1..kmax, by position
+ *   tables  device, the packed tables (written)
+ * se2_batch_convolve_separable -- the convolution of every problem: f and out
+ * the packed grids (device, must not overlap), tables the packed tables.
+ * The classes run concurrently on streams forked from `stream` and joined back
+ * into it (events only), so the call can be captured in a CUDA graph.
+ *
+ * se2_batch_tune -- the autotuner: for each class, time the candidate
+ * schedules (`reps` calls each, on the given data, on `stream`) and keep the
+ * fastest: FP32 fast path with pipeline depth 1 or depth 2 with groups of
+ * 1, 2, 4, .. 64 problems, or the persistent dataflow kernel.  Synchronous;
+ * not for stream capture.  se2_batch_plan_config reports per class (host
+ * arrays of n_classes, each may be NULL): shape, count, pipeline depth (0 for
+ * the persistent kernel), group, persistent (0/1) and the tuned ms per call.
+ * se2_batch_plan_launches: kernels launched through the plan so far.
+ */
+typedef struct { int N, M; } se2_shape;
+typedef struct se2_batch_plan_s* se2_batch_plan_t;
+se2_status se2_batch_plan_create(se2_batch_plan_t* plan, const se2_shape* shapes, int n_problems,
+                                 se2_precision precision, unsigned flags, int device);
+se2_status se2_batch_plan_destroy(se2_batch_plan_t plan);
+se2_status se2_batch_plan_layout(se2_batch_plan_t plan, int* position, long long* grid_offset, long long* table_offset,
+                                 long long* grid_total, long long* table_total);
+se2_status se2_batch_separable_tables(se2_batch_plan_t plan, const double* params, const int* k, int kmax, void* tables,
+                                      void* stream);
+se2_status se2_batch_convolve_separable(se2_batch_plan_t plan, const void* f, const void* tables, void* out, void* stream);
+se2_status se2_batch_tune(se2_batch_plan_t plan, const void* f, const void* tables, void* out, int reps, void* stream);
+se2_status se2_batch_plan_config(se2_batch_plan_t plan, int* n_classes, se2_shape* shape, int* count, int* depth,
+                                 int* group, int* persistent, double* tuned_ms);
+unsigned long long se2_batch_plan_launches(se2_batch_plan_t plan);
+
+/*
  * se2_plan_launches -- the number of kernels the plan's entry points have
  * launched so far (host-side count, updated as launches are enqueued; plan
  * creation's own set-up launches are not counted).  0 for a NULL plan.
@@ -327,9 +393,10 @@ se2_status se2_debug_wait_timeout(se2_plan_t plan, const void* f, const void* co
  *   stream     the call is ordered after earlier work on `stream`; on
  *              return all of its work is enqueued and `stream` waits for it,
  *              so synchronise `stream` before reading out
- * The first call allocates the staging buffers (three groups of f and out)
- * and two copy streams; later calls reuse them.  Not for stream capture.
- * Errors: as se2_convolve.
+ * The plan must have been created with SE2_HOST_STAGING (SE2_ERR_INVALID_ARG
+ * otherwise): its staging buffers (three groups of f and out) and copy
+ * streams come from se2_plan_create, and this call allocates nothing.
+ * Not for stream capture.  Errors: as se2_convolve.
  */
 se2_status se2_convolve_host(se2_plan_t plan, const void* f, int B, const void* coeffs, const double* log_scale,
                              void* out, void* stream);
@@ -340,8 +407,7 @@ se2_status se2_convolve_host(se2_plan_t plan, const void* f, int B, const void* 
  * because creating one allocates device memory: for instance code running
  * inside a host framework's execution step where device allocation is not
  * allowed, or code that must not risk the implicit synchronisation that
- * cudaMalloc / cudaFree may cause.  The paper has no counterpart; this is a
- * deployment variant of Algorithm 3 at N = L.
+ * cudaMalloc / cudaFree may cause.  The paper has no counterpart.
  *   f, coeffs, out  as in se2_convolve (float / complex float, caller-owned)
  *   N, M, B         sizes; the batch is processed in chunks that fit
  * Memory: the call uses a fixed 64 MiB device array defined in the library
@@ -358,6 +424,20 @@ se2_status se2_convolve_host(se2_plan_t plan, const void* f, int B, const void* 
  */
 se2_status se2_convolve_noalloc(const void* f, const void* coeffs, void* out, int N, int M, int B,
                                 void* stream);
+
+/*
+ * Allocation accounting (tests and diagnostics).  Every device allocation the
+ * library makes (plans, grid plans, host-call staging) goes through one
+ * counter:
+ *   se2_debug_alloc_stats -- live: allocations not yet freed; total: all made.
+ *   se2_debug_fail_alloc  -- make the n-th next allocation fail as if device
+ *                            memory had run out (n = 0: off).  The call that
+ *                            meets it returns SE2_ERR_OOM and frees what it had
+ *                            allocated.  Process-wide.
+ * Host arrays; never fail except on NULL / negative arguments.
+ */
+se2_status se2_debug_alloc_stats(long long* live, long long* total);
+se2_status se2_debug_fail_alloc(long long n);
 
 /* Thread-local text of the last error (never NULL). */
 /*
@@ -438,6 +518,23 @@ se2_status se2_grid_sample_se2_gaussian(se2_grid_plan_t plan, const double* beta
                                         void* P, void* stream);
 se2_status se2_grid_sample_deformed_gaussian(se2_grid_plan_t plan, const double* H, double nu, double s, int images,
                                              void* P, void* stream);
+
+/*
+ * se2_grid_ffc_at -- one finite Fourier coefficient f^[k; L] (Eq. FkLv,
+ * Section 4.1) read from grid coefficients C = DFT(P) / |L| of real samples:
+ * (-1)^(k1 + k2) C(tau(k)), where tau maps the signed frequency to its DFT bin
+ * (k mod L); C holds x bins 0 .. Kx only, so a negative k1 reads the
+ * Hermitian partner -k and conjugates it.  The step of Algorithm 1 that reads
+ * one entry of the transform.
+ *   coeffs  device, [batch][Lr][Ly][Kx+1] complex as written by se2_grid_coeffs
+ *   index   which problem of the batch, 0 <= index < batch
+ *   k1..k3  |k1| <= Kx, |k2| <= Ky, |k3| <= Kr (K = (L - 1) / 2)
+ *   out     device, 2 doubles: real and imaginary part (written on `stream`)
+ * Errors: SE2_ERR_INVALID_ARG for k outside the range, NULL or misaligned
+ * pointers.
+ */
+se2_status se2_grid_ffc_at(se2_grid_plan_t plan, const void* coeffs, int index, int k1, int k2, int k3, double* out,
+                           void* stream);
 
 /*
  * se2_accuracy_order -- Algorithm 1 (Section 4.2; Theorem fkLmain and the

@@ -32,6 +32,8 @@ PERSISTENT = 0x2
 GRID_ORIGIN_ZERO = 0x4        # grids sampled at x_i = i/N: the plain cyclic convolution (no W)
 MASS_RENORM = 0x8             # FP64 mass renormalisation of convolve / convolve_chain outputs
 KERNEL_YSYM = 0x10            # kernel spectra mirror-symmetric in y (radial kernels): half the C rows read
+HOST_STAGING = 0x20           # convolve_host staging allocated with the plan
+CHECK_FINITE = 0x40           # outputs checked for NaN / infinity (status(): SE2_ERR_NUMERIC)
 
 _STATUS = {0: "SE2_OK", 1: "SE2_ERR_INVALID_ARG", 2: "SE2_ERR_UNSUPPORTED", 3: "SE2_ERR_OOM",
            4: "SE2_ERR_CUDA", 5: "SE2_ERR_TIMEOUT", 6: "SE2_ERR_NUMERIC"}
@@ -77,6 +79,9 @@ def load_library(path: str = LIB_PATH):
     lib.se2_grid_plan_launches.argtypes = [vp]
     lib.se2_grid_plan_launches.restype = ctypes.c_ulonglong
     lib.se2_grid_coeffs.argtypes = [vp, vp, ip, vp, vp]
+    lib.se2_grid_ffc_at.argtypes = [vp, vp, ip, ip, ip, ip, vp, vp]
+    lib.se2_debug_alloc_stats.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.se2_debug_fail_alloc.argtypes = [ctypes.c_longlong]
     lib.se2_grid_convolve_chain.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ip, vp, vp]
     lib.se2_grid_convolve_chain_all.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ip, vp, vp]
     lib.se2_grid_sample_se2_gaussian.argtypes = [vp, dptr, dptr, ctypes.c_int, vp, vp]
@@ -94,10 +99,10 @@ def load_library(path: str = LIB_PATH):
                  "se2_convolve_chain", "se2_convolve_chain_all",
                  "se2_plan_status", "se2_debug_wait_timeout", "se2_backward", "se2_sample_radial_gaussian",
                  "se2_sample_se2_gaussian", "se2_sample_deformed_gaussian",
-                 "se2_grid_plan_create", "se2_grid_plan_destroy", "se2_grid_coeffs", "se2_grid_convolve_chain",
-                 "se2_grid_convolve_chain_all",
+                 "se2_grid_plan_create", "se2_grid_plan_destroy", "se2_grid_coeffs", "se2_grid_ffc_at",
+                 "se2_grid_convolve_chain", "se2_grid_convolve_chain_all",
                  "se2_accuracy_order", "se2_plan_timing", "se2_plan_timing_read", "se2_grid_sample_se2_gaussian", "se2_grid_sample_deformed_gaussian",
-                 "se2_separable_tables", "se2_convolve_separable"):
+                 "se2_separable_tables", "se2_convolve_separable", "se2_debug_alloc_stats", "se2_debug_fail_alloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -488,19 +493,14 @@ def accuracy_order(eps: float, grad_inf: float, k=(0, 0, 0), constant: float = 3
 
 def ffc_at(plan: GridPlan, C: torch.Tensor, k, index: int = 0) -> complex:
     """f^[k; L] = (-1)^(k1+k2) C(tau(k)) (Eq. FkLv) read from grid coefficients
-    C = DFT(P)/|L| ([n, Lr, Ly, Kx+1]) of real samples; k = (k1, k2, k3) with
-    |k_i| <= K_i.  Negative k1 use the Hermitian partner."""
+    C = DFT(P)/|L| ([n, Lr, Ly, Kx+1]) of real samples by se2_grid_ffc_at;
+    k = (k1, k2, k3) with |k_i| <= K_i (negative k1: the Hermitian partner)."""
     k1, k2, k3 = (int(v) for v in k)
-    Kx, Ky, Kr = (plan.Lx - 1) // 2, (plan.Ly - 1) // 2, (plan.Lr - 1) // 2
-    if abs(k1) > Kx or abs(k2) > Ky or abs(k3) > Kr:
-        raise ValueError(f"k = {k} outside |k| <= K = ({Kx}, {Ky}, {Kr})")
-    conj = k1 < 0
-    if conj:
-        k1, k2, k3 = -k1, -k2, -k3
-    v = complex(C[index, k3 % plan.Lr, k2 % plan.Ly, k1].item())
-    if conj:
-        v = v.conjugate()
-    return -v if (k1 + k2) % 2 else v
+    out = torch.empty(2, dtype=torch.float64, device=C.device)
+    _check(load_library().se2_grid_ffc_at(plan.handle, _ptr(C), int(index), k1, k2, k3, _ptr(out),
+                                          _stream(C.device)))
+    re, im = out.cpu().tolist()
+    return complex(re, im)
 
 
 def ffc_convergence(sample, k, Ks, precision: str = "f64", device: Optional[int] = None):
@@ -518,6 +518,18 @@ def ffc_convergence(sample, k, Ks, precision: str = "f64", device: Optional[int]
         prev = v
         plan.close()
     return out
+
+
+def alloc_stats():
+    """(live, total) device allocations the library has made (se2_debug_alloc_stats)."""
+    live, total = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load_library().se2_debug_alloc_stats(ctypes.byref(live), ctypes.byref(total)))
+    return int(live.value), int(total.value)
+
+
+def fail_alloc(n: int):
+    """Make the n-th next device allocation of the library fail (0: off)."""
+    _check(load_library().se2_debug_fail_alloc(int(n)))
 
 
 def table_len(plan: Plan) -> int:
@@ -561,14 +573,27 @@ class SE2Conv(torch.autograd.Function):
     have the SHARED_KERNEL flag."""
 
     @staticmethod
+    def _spectra(plan, params):
+        """C, dC/dsigma, dC/dsigma_theta for params, cached on the plan: while
+        the params tensor is unchanged (same storage and version counter) the
+        spectra are reused without reading its values, so a step that trains
+        only f neither synchronises nor resamples.  params may live on the CPU
+        (no device read at all) or on the device (read when they change)."""
+        key = (params.data_ptr(), params._version, params.device)
+        cache = getattr(plan, "_se2conv_cache", None)
+        if cache is not None and cache[0] == key:
+            return cache[1]
+        sigma, sigma_t = (float(v) for v in params.detach().cpu().tolist())
+        P, dPs, dPt = sample_radial_gaussian(plan, sigma, sigma_t, 0.0, derivs=True)
+        spectra = (coeffs(plan, P)[0], coeffs(plan, dPs)[0], coeffs(plan, dPt)[0])
+        plan._se2conv_cache = (key, spectra)
+        return spectra
+
+    @staticmethod
     def forward(ctx, f, params, plan):
         if not plan.flags & SHARED_KERNEL:
             raise ValueError("SE2Conv needs a plan with SHARED_KERNEL")
-        sigma, sigma_t = (float(v) for v in params.detach().cpu().tolist())
-        P, dPs, dPt = sample_radial_gaussian(plan, sigma, sigma_t, 0.0, derivs=True)
-        C, _ = coeffs(plan, P)
-        dCs, _ = coeffs(plan, dPs)
-        dCt, _ = coeffs(plan, dPt)
+        C, dCs, dCt = SE2Conv._spectra(plan, params)
         out = convolve(plan, f.contiguous(), C)
         ctx.plan = plan
         ctx.save_for_backward(f, C, dCs, dCt)
@@ -590,4 +615,4 @@ __all__ = ["Plan", "SE2Error", "coeffs", "convolve", "convolve_host", "convolve_
            "GridPlan", "grid_coeffs", "grid_convolve_chain", "grid_convolve_chain_all", "accuracy_order", "ffc_at", "ffc_convergence",
            "SE2Conv", "separable_tables", "convolve_separable", "table_len", "load_library", "LIB_PATH",
            "SHARED_KERNEL", "PERSISTENT", "GRID_ORIGIN_ZERO", "MASS_RENORM",
-           "KERNEL_YSYM"]
+           "KERNEL_YSYM", "HOST_STAGING", "CHECK_FINITE", "alloc_stats", "fail_alloc"]

@@ -1,27 +1,26 @@
-"""Batched execution of many independent SE(2) convolutions of uneven sizes.
+"""Batched execution of many independent SE(2) convolutions of uneven sizes,
+on the library's batch plan (se2_batch_plan_*).
 
-Problems are grouped by grid size (N, M).  Each size class gets its own plan
-and runs as one stream of `se2_convolve_separable` calls; the classes run
-concurrently on forked CUDA streams, and the whole batch is captured once in
-a CUDA graph and replayed.  Each problem carries a chain of separable radial
-kernels (Gaussian x wrapped normal), whose product is kept in factored form
-(three 1-D tables per problem, built on the GPU by se2_separable_tables).
-
-A small autotuner picks, per size class, between the three-kernel sequence
-and the persistent dataflow kernel and the number of problems per call
-(which bounds the plan's scratch), by timing the candidates on the class's
-own data; choices are cached in a JSON file keyed by GPU name, size, class
-population and precision.
+The C runtime groups the problems into size classes (equal grid N x N x M),
+gives each class its own plan, runs the classes concurrently on forked
+streams (one `se2_batch_convolve_separable` call, capturable in a CUDA
+graph) and tunes, per class, the schedule of its launches (pipeline depth and
+group size of the FP32 fast path, or the persistent dataflow kernel) by
+timing the candidates on the class's own data (`se2_batch_tune`).  Each
+problem carries a chain of separable radial kernels (Gaussian x wrapped
+normal), whose product is kept in factored form (three 1-D tables per
+problem).  This module only holds the packed tensors and marshals calls.
 """
 from __future__ import annotations
 
+import ctypes
 import json
 import os
 from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
-from . import PERSISTENT, Plan, convolve_separable, separable_tables, table_len
+from . import _check, _ptr, _stream, load_library
 
 _CACHE_ENV = "SE2_AUTOTUNE_CACHE"
 
@@ -30,187 +29,184 @@ def _default_cache() -> str:
     return os.environ.get(_CACHE_ENV, os.path.join(os.path.expanduser("~"), ".cache", "se2_autotune.json"))
 
 
+class _Shape(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int)]
+
+
+def _bind(lib):
+    if getattr(lib, "_se2_batch_bound", False):
+        return lib
+    vp, ip = ctypes.c_void_p, ctypes.c_int
+    ll = ctypes.POINTER(ctypes.c_longlong)
+    lib.se2_batch_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Shape), ip, ip, ctypes.c_uint, ip]
+    lib.se2_batch_plan_destroy.argtypes = [vp]
+    lib.se2_batch_plan_layout.argtypes = [vp, ctypes.POINTER(ip), ll, ll, ll, ll]
+    lib.se2_batch_separable_tables.argtypes = [vp, vp, vp, ip, vp, vp]
+    lib.se2_batch_convolve_separable.argtypes = [vp, vp, vp, vp, vp]
+    lib.se2_batch_tune.argtypes = [vp, vp, vp, vp, ip, vp]
+    lib.se2_batch_plan_config.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(_Shape), ctypes.POINTER(ip),
+                                          ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                          ctypes.POINTER(ctypes.c_double)]
+    lib.se2_batch_plan_launches.argtypes = [vp]
+    lib.se2_batch_plan_launches.restype = ctypes.c_ulonglong
+    for name in ("se2_batch_plan_create", "se2_batch_plan_destroy", "se2_batch_plan_layout", "se2_batch_separable_tables",
+                 "se2_batch_convolve_separable", "se2_batch_tune", "se2_batch_plan_config"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib._se2_batch_bound = True
+    return lib
+
+
 class BatchRunner:
-    """Holds per-class input/output/table tensors and plans for a fixed set
-    of problem shapes.  Usage: fill `f_of(i)` and `set_chain(...)`, then
-    `run()` (or `capture()` once and `replay()`)."""
+    """Packed inputs/outputs/tables of a fixed set of problem shapes over one
+    batch plan.  Usage: fill `f_of(i)` and `set_chain(...)`, then `run()` (or
+    `capture()` once and `replay()`)."""
 
     def __init__(self, shapes: Sequence[Tuple[int, int]], device: int = 0, autotune: bool = True,
                  cache_path: Optional[str] = None, kmax: int = 16):
+        self.lib = _bind(load_library())
         self.device = device
         self.dev = torch.device("cuda", device)
-        self.shapes = list(shapes)
+        self.shapes = [(int(N), int(M)) for N, M in shapes]
         self.kmax = kmax
+        n = len(self.shapes)
+        arr = (_Shape * n)(*[_Shape(N, M) for N, M in self.shapes])
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.dev):
+            _check(self.lib.se2_batch_plan_create(ctypes.byref(self._h), arr, n, 1, 0, device))
+        pos = (ctypes.c_int * n)()
+        goff = (ctypes.c_longlong * n)()
+        toff = (ctypes.c_longlong * n)()
+        gtot, ttot = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self.lib.se2_batch_plan_layout(self._h, pos, goff, toff, ctypes.byref(gtot), ctypes.byref(ttot)))
+        self.pos, self.goff, self.toff = list(pos), list(goff), list(toff)
+        self.f_packed = torch.zeros(int(gtot.value), dtype=torch.float32, device=self.dev)
+        self.out_packed = torch.empty_like(self.f_packed)
+        self.tab_packed = torch.empty(int(ttot.value), dtype=torch.complex64, device=self.dev)
+        self.params = torch.zeros((n, kmax, 3), dtype=torch.float64, device=self.dev)
+        self.params[:, :, 0] = 0.02
+        self.params[:, :, 1] = 0.3
+        self.k = torch.ones(n, dtype=torch.int32, device=self.dev)
         self.classes: Dict[Tuple[int, int], List[int]] = {}
         for i, s in enumerate(self.shapes):
-            self.classes.setdefault((int(s[0]), int(s[1])), []).append(i)
-        # classes in decreasing work order (largest grids first)
-        self.order = sorted(self.classes, key=lambda c: -c[0] * c[0] * c[1] * len(self.classes[c]))
-        self.where = {}                            # problem -> (class, slot)
-        self.f: Dict[Tuple[int, int], torch.Tensor] = {}
-        self.out: Dict[Tuple[int, int], torch.Tensor] = {}
-        self.tab: Dict[Tuple[int, int], torch.Tensor] = {}
-        self.params: Dict[Tuple[int, int], torch.Tensor] = {}
-        self.k: Dict[Tuple[int, int], torch.Tensor] = {}
+            self.classes.setdefault(s, []).append(i)
+        self.order = [c for c, *_ in self._config()]   # the plan's class order (largest work first)
+        # per-class views of the packed output (classes are contiguous blocks)
+        self.out = {}
         for c in self.order:
-            N, M = c
-            n = len(self.classes[c])
-            for slot, i in enumerate(self.classes[c]):
-                self.where[i] = (c, slot)
-            self.f[c] = torch.zeros((n, M, N, N), dtype=torch.float32, device=self.dev)
-            self.out[c] = torch.empty_like(self.f[c])
-            self.params[c] = torch.zeros((n, kmax, 3), dtype=torch.float64, device=self.dev)
-            self.params[c][:, :, 0] = 0.02
-            self.params[c][:, :, 1] = 0.3
-            self.k[c] = torch.ones(n, dtype=torch.int32, device=self.dev)
-            self.tab[c] = None
+            first = min(self.goff[i] for i in self.classes[c])
+            size = c[0] * c[0] * c[1] * len(self.classes[c])
+            self.out[c] = self.out_packed[first:first + size]
         self.cache_path = cache_path or _default_cache()
         self.config: Dict[Tuple[int, int], Tuple[str, int]] = {}
-        self.plans: Dict[Tuple[int, int], Plan] = {}
-        self.streams = [torch.cuda.Stream(self.dev) for _ in self.order]
-        self.graph = None
         self._autotune = autotune
-        self._plan_cache = {}
+        self._tuned = False
+        self._tables = False
+        self.graph = None
+        self._graph_launches = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.se2_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     # -- inputs ---------------------------------------------------------------
+    def _view(self, t: torch.Tensor, i: int) -> torch.Tensor:
+        N, M = self.shapes[i]
+        return t[self.goff[i]:self.goff[i] + N * N * M].view(M, N, N)
+
     def f_of(self, i: int) -> torch.Tensor:
-        c, slot = self.where[i]
-        return self.f[c][slot]
+        return self._view(self.f_packed, i)
 
     def out_of(self, i: int) -> torch.Tensor:
-        c, slot = self.where[i]
-        return self.out[c][slot]
+        return self._view(self.out_packed, i)
 
     def set_chain(self, i: int, kernels: Sequence[Tuple[float, float, float]]):
         """Kernel chain of problem i: a list of (sigma, sigma_theta, nu)."""
         if not 1 <= len(kernels) <= self.kmax:
             raise ValueError(f"chain length must be in [1, {self.kmax}]")
-        c, slot = self.where[i]
         p = torch.zeros((self.kmax, 3), dtype=torch.float64)
         for j, kp in enumerate(kernels):
             p[j] = torch.tensor([float(v) for v in kp], dtype=torch.float64)
-        self.params[c][slot] = p.to(self.dev)
-        self.k[c][slot] = len(kernels)
+        self.params[self.pos[i]] = p.to(self.dev)
+        self.k[self.pos[i]] = len(kernels)
 
     def build_tables(self):
-        """Factored chain coefficients for every problem (one launch per class)."""
-        for c in self.order:
-            plan = self._plan_for(c, "three", min(4, len(self.classes[c])))
-            self.tab[c] = separable_tables(plan, self.params[c], self.k[c])
+        """Factored chain coefficients for every problem (se2_batch_separable_tables)."""
+        _check(self.lib.se2_batch_separable_tables(self._h, _ptr(self.params), _ptr(self.k), self.kmax,
+                                                   _ptr(self.tab_packed), _stream(self.dev)))
+        self._tables = True
 
-    # -- planning / autotuning ------------------------------------------------
-    def _plan_for(self, c, path: str, per_call: int) -> Plan:
-        key = (c, path, per_call)
-        if key not in self._plan_cache:
-            N, M = c
-            self._plan_cache[key] = Plan(N, M, batch=per_call, precision="f32",
-                                         flags=PERSISTENT if path == "persistent" else 0, device=self.device)
-        return self._plan_cache[key]
+    # -- tuning -----------------------------------------------------------------
+    def _config(self):
+        nc = ctypes.c_int()
+        _check(self.lib.se2_batch_plan_config(self._h, ctypes.byref(nc), None, None, None, None, None, None))
+        m = nc.value
+        shp = (_Shape * m)()
+        cnt, dep, grp, per = ((ctypes.c_int * m)() for _ in range(4))
+        ms = (ctypes.c_double * m)()
+        _check(self.lib.se2_batch_plan_config(self._h, ctypes.byref(nc), shp, cnt, dep, grp, per, ms))
+        return [((shp[j].N, shp[j].M), cnt[j], dep[j], grp[j], per[j], ms[j]) for j in range(m)]
 
-    def _candidates(self, c):
-        n = len(self.classes[c])
-        sizes = sorted({min(n, s) for s in (n, 64, 16, 4)}, reverse=True)
-        return [(p, s) for p in ("three", "persistent") for s in sizes]
-
-    def _load_cache(self):
+    def tune(self, reps: int = 3):
+        """se2_batch_tune on the current data; the choices per class are also
+        written to a JSON record keyed by GPU name, size, class population."""
+        if not self._tables:
+            self.build_tables()
+        _check(self.lib.se2_batch_tune(self._h, _ptr(self.f_packed), _ptr(self.tab_packed), _ptr(self.out_packed),
+                                       int(reps), _stream(self.dev)))
+        self._tuned = True
+        gpu = torch.cuda.get_device_name(self.dev)
+        record = {}
+        for c, n, depth, group, pers, ms in self._config():
+            path = "persistent" if pers else ("pipelined" if depth > 1 else "three")
+            self.config[c] = (path, group)
+            record[f"{gpu}|N={c[0]}|M={c[1]}|n={n}|f32"] = [path, depth, group, ms]
         try:
-            with open(self.cache_path) as fh:
-                return json.load(fh)
-        except Exception:
-            return {}
-
-    def _save_cache(self, data):
-        try:
-            os.makedirs(os.path.dirname(self.cache_path), exist_ok=True)
+            os.makedirs(os.path.dirname(self.cache_path) or ".", exist_ok=True)
+            old = {}
+            if os.path.exists(self.cache_path):
+                with open(self.cache_path) as fh:
+                    old = json.load(fh)
+            old.update(record)
             with open(self.cache_path, "w") as fh:
-                json.dump(data, fh, indent=1, sort_keys=True)
+                json.dump(old, fh, indent=1, sort_keys=True)
         except Exception:
             pass
 
-    def tune(self, reps: int = 3):
-        """Choose (path, problems per call) per class by timing each candidate."""
-        gpu = torch.cuda.get_device_name(self.dev)
-        cache = self._load_cache()
-        for c in self.order:
-            n = len(self.classes[c])
-            key = f"{gpu}|N={c[0]}|M={c[1]}|n={n}|f32"
-            if key in cache:
-                self.config[c] = (cache[key][0], int(cache[key][1]))
-                continue
-            best = None
-            for path, per in self._candidates(c):
-                try:
-                    plan = self._plan_for(c, path, per)
-                except Exception:
-                    continue
-                self._run_class(c, plan, per)          # warm-up
-                torch.cuda.synchronize(self.dev)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(reps):
-                    self._run_class(c, plan, per)
-                e1.record()
-                torch.cuda.synchronize(self.dev)
-                ms = e0.elapsed_time(e1) / reps
-                if best is None or ms < best[0]:
-                    best = (ms, path, per)
-            self.config[c] = (best[1], best[2])
-            cache[key] = [best[1], best[2], best[0]]
-        self._save_cache(cache)
-        # release the scratch of plans that were not chosen
-        keep = {(c, p, s) for c, (p, s) in self.config.items()}
-        for key in list(self._plan_cache):
-            if key not in keep and not (key[1] == "three" and key[2] == min(4, len(self.classes[key[0]]))):
-                self._plan_cache.pop(key).close()
-
-    def _ensure_config(self):
-        for c in self.order:
-            if c not in self.config:
-                if self._autotune:
-                    self.tune()
-                    return
-                self.config[c] = ("three", len(self.classes[c]))
-
     # -- execution --------------------------------------------------------------
-    def _run_class(self, c, plan: Plan, per: int):
-        n = len(self.classes[c])
-        for s in range(0, n, per):
-            e = min(n, s + per)
-            convolve_separable(plan, self.f[c][s:e], self.tab[c][s:e], self.out[c][s:e])
-
     def run(self):
-        """All classes on forked streams, joined back into the current stream."""
-        if any(self.tab[c] is None for c in self.order):
+        """Every problem, classes concurrently, on the current stream."""
+        if not self._tables:
             self.build_tables()
-        self._ensure_config()
-        cur = torch.cuda.current_stream(self.dev)
-        for st in self.streams:
-            st.wait_stream(cur)
-        for c, st in zip(self.order, self.streams):
-            path, per = self.config[c]
-            with torch.cuda.stream(st):
-                self._run_class(c, self._plan_for(c, path, per), per)
-        for st in self.streams:
-            cur.wait_stream(st)
+        if self._autotune and not self._tuned:
+            self.tune()
+        _check(self.lib.se2_batch_convolve_separable(self._h, _ptr(self.f_packed), _ptr(self.tab_packed),
+                                                     _ptr(self.out_packed), _stream(self.dev)))
+
+    def launches(self) -> int:
+        return int(self.lib.se2_batch_plan_launches(self._h))
 
     def capture(self):
-        """Record run() into a CUDA graph (plans and tables are set up first)."""
-        if any(self.tab[c] is None for c in self.order):
+        """Record run() into a CUDA graph (tables and tuning done first)."""
+        if not self._tables:
             self.build_tables()
-        self._ensure_config()
+        if self._autotune and not self._tuned:
+            self.tune()
         self.run()                                   # warm-up outside capture
         torch.cuda.synchronize(self.dev)
         g = torch.cuda.CUDAGraph()
-        before = self._launch_count()
+        before = self.launches()
         with torch.cuda.graph(g):
             self.run()
-        self._graph_launches = self._launch_count() - before
+        self._graph_launches = self.launches() - before
         self.graph = g
         return g
-
-    def _launch_count(self) -> int:
-        used = {self._plan_for(c, *self.config[c]) for c in self.order}
-        return sum(p.launches() for p in used)
 
     def replay(self):
         if self.graph is None:
@@ -218,14 +214,13 @@ class BatchRunner:
         self.graph.replay()
 
     def launches_per_run(self) -> int:
-        """Kernel launches of one run() with the chosen configuration, as
-        counted by the plans (se2_plan_launches) while the graph was captured,
-        or over one eager run()."""
-        if getattr(self, "_graph_launches", None) is not None:
+        """Kernel launches of one run(), counted by the plan while the graph was
+        captured, or over one eager run()."""
+        if self._graph_launches is not None:
             return self._graph_launches
-        before = self._launch_count()
+        before = self.launches()
         self.run()
-        return self._launch_count() - before
+        return self.launches() - before
 
     def points(self) -> int:
         return sum(N * N * M * len(v) for (N, M), v in self.classes.items())

@@ -90,7 +90,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 if verbose:
                     print("built", obj, file=sys.stderr)
     if todo or not os.path.exists(LIB):
-        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

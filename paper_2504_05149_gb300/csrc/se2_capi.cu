@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -13,10 +14,12 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/se2.h"
 #include "se2_internal.h"
+#include "se2_nvtx.h"
 #include "se2_tc.cuh"
 
 using namespace se2;
@@ -56,6 +59,44 @@ struct DeviceGuard {
 }  // namespace
 
 void se2::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+std::atomic<long long> g_live_allocs{0}, g_total_allocs{0}, g_fail_countdown{0};
+}
+cudaError_t se2::dev_alloc(void** p, size_t bytes) {
+    // the countdown reaches 1 at the allocation that is to fail
+    long long c = g_fail_countdown.load();
+    while (c > 0 && !g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        ++g_live_allocs;
+        ++g_total_allocs;
+    }
+    return e;
+}
+void se2::dev_free(void* p) {
+    if (p != nullptr && cudaFree(p) == cudaSuccess) --g_live_allocs;
+}
+
+se2_status se2_debug_alloc_stats(long long* live, long long* total) {
+    SE2_RANGE("se2_debug_alloc_stats");
+    if (live == nullptr || total == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    *live = g_live_allocs.load();
+    *total = g_total_allocs.load();
+    return SE2_OK;
+}
+
+se2_status se2_debug_fail_alloc(long long n) {
+    SE2_RANGE("se2_debug_fail_alloc");
+    if (n < 0) return fail(SE2_ERR_INVALID_ARG, "n=%lld must be >= 0", n);
+    g_fail_countdown.store(n);
+    return SE2_OK;
+}
 
 constexpr int kMaxPipe = 4;
 constexpr int kPipeDepth = 2, kPipeGroup = 2;   // default pipelining of the FP32 fast path
@@ -203,7 +244,7 @@ se2_status plan_init(se2_plan_s* p) {
         all.insert(all.end(), img.begin(), img.end());
         tc_dft_matrix(+1, fmt, img);
         all.insert(all.end(), img.begin(), img.end());
-        r = cudaMalloc(&p->tcB, all.size());
+        r = dev_alloc((void**)&p->tcB, all.size());
         if (r != cudaSuccess) return fail(SE2_ERR_OOM, "tensor-core DFT matrix: %s", cudaGetErrorString(r));
         r = cudaMemcpy(p->tcB, all.data(), all.size(), cudaMemcpyHostToDevice);
         if (r != cudaSuccess) return cuda_fail(r, "cudaMemcpy");
@@ -248,8 +289,8 @@ se2_status plan_init(se2_plan_s* p) {
         }
     }
     cudaError_t e;
-    if ((e = cudaMalloc(&p->twN, sizeof(c2<T>) * p->N)) != cudaSuccess) return fail(SE2_ERR_OOM, "twiddles: %s", cudaGetErrorString(e));
-    if ((e = cudaMalloc(&p->twM, sizeof(c2<T>) * p->M)) != cudaSuccess) return fail(SE2_ERR_OOM, "twiddles: %s", cudaGetErrorString(e));
+    if ((e = dev_alloc((void**)&p->twN, sizeof(c2<T>) * p->N)) != cudaSuccess) return fail(SE2_ERR_OOM, "twiddles: %s", cudaGetErrorString(e));
+    if ((e = dev_alloc((void**)&p->twM, sizeof(c2<T>) * p->M)) != cudaSuccess) return fail(SE2_ERR_OOM, "twiddles: %s", cudaGetErrorString(e));
     if ((e = make_twiddles<T>((c2<T>*)p->twN, p->N, 0)) != cudaSuccess) return cuda_fail(e, "twiddle kernel");
     if ((e = make_twiddles<T>((c2<T>*)p->twM, p->M, 0)) != cudaSuccess) return cuda_fail(e, "twiddle kernel");
     return SE2_OK;
@@ -268,7 +309,7 @@ void plan_free(se2_plan_s* p) {
     if (p->hev_start) cudaEventDestroy(p->hev_start);
     if (p->hin) cudaStreamDestroy(p->hin);
     if (p->hout) cudaStreamDestroy(p->hout);
-    if (p->hstage) cudaFree(p->hstage);
+    if (p->hstage) dev_free(p->hstage);
     p->hev_start = nullptr;
     p->hin = p->hout = nullptr;
     p->hstage = nullptr;
@@ -280,19 +321,19 @@ void plan_free(se2_plan_s* p) {
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     p->ev_fork = nullptr;
-    if (p->ctr) cudaFree(p->ctr);
-    if (p->err) cudaFree(p->err);
-    if (p->tab) cudaFree(p->tab);
-    if (p->tcB) cudaFree(p->tcB);
+    if (p->ctr) dev_free(p->ctr);
+    if (p->err) dev_free(p->err);
+    if (p->tab) dev_free(p->tab);
+    if (p->tcB) dev_free(p->tcB);
     p->tcB = nullptr;
     p->ctr = nullptr;
     p->err = nullptr;
     p->tab = nullptr;
-    if (p->scratch) cudaFree(p->scratch);
-    if (p->twN) cudaFree(p->twN);
-    if (p->twM) cudaFree(p->twM);
-    if (p->abs_sum) cudaFree(p->abs_sum);
-    if (p->mass) cudaFree(p->mass);
+    if (p->scratch) dev_free(p->scratch);
+    if (p->twN) dev_free(p->twN);
+    if (p->twM) dev_free(p->twM);
+    if (p->abs_sum) dev_free(p->abs_sum);
+    if (p->mass) dev_free(p->mass);
     p->scratch = p->twN = p->twM = nullptr;
     p->abs_sum = nullptr;
     p->mass = nullptr;
@@ -544,6 +585,27 @@ void launch_unit_c(const FastTable& ft, int N, int nb, cudaStream_t s, const FAr
         ft.inv2<<<dim3(N, nb), kThreads, ft.smem_xt2, s>>>(a);
     else
         ft.inv<<<dim3(N, nb), kThreads, ft.smem_xt, s>>>(a);
+}
+
+// SE2_CHECK_FINITE: one pass over an output; the first NaN or infinity sets
+// the plan's error word to 5 (se2_plan_status: SE2_ERR_NUMERIC).
+template <typename T>
+__global__ void k_check_finite(const T* x, size_t n, int* err) {
+    bool bad = false;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(err, 0, 5);
+}
+se2_status check_finite(se2_plan_s* p, const void* x, size_t n, cudaStream_t s) {
+    if (!(p->flags & SE2_CHECK_FINITE)) return SE2_OK;
+    const int grid = 4 * (p->nsm > 0 ? p->nsm : 152);
+    if (p->prec == SE2_F64)
+        k_check_finite<double><<<grid, 256, 0, s>>>(static_cast<const double*>(x), n, p->err);
+    else
+        k_check_finite<float><<<grid, 256, 0, s>>>(static_cast<const float*>(x), n, p->err);
+    ++p->launches;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SE2_OK : cuda_fail(e, "finite check");
 }
 
 // Tensor maps of the dataflow kernel over the scratch [nslots M][N][4 tp/2
@@ -889,8 +951,45 @@ const char* se2_last_error(void) { return g_err.c_str(); }
 
 const char* se2_version(void) { return "se2-gb300 0.1 (sm_103a)"; }
 
+// Staging of se2_convolve_host (plan flag SE2_HOST_STAGING): kHostBufs
+// groups of f and out in device memory, two copy streams and their events,
+// made once at plan creation so that no convolve call allocates.
+se2_status host_staging_init(se2_plan_s* p) {
+    const size_t gbytes = (size_t)p->N * p->N * p->M * (p->elem / 2);   // one grid
+    int G = kHostGroup;   // SE2_HOST_GROUP (environment) overrides the group size
+    if (const char* v = getenv("SE2_HOST_GROUP")) G = (int)strtol(v, nullptr, 10);
+    if (G < 1) G = 1;
+    if (G > p->batch) G = p->batch;
+    cudaError_t e = dev_alloc((void**)&p->hstage, 2 * gbytes * (size_t)G * kHostBufs);
+    if (e != cudaSuccess) { p->hstage = nullptr; return fail(SE2_ERR_OOM, "host staging: %s", cudaGetErrorString(e)); }
+    p->host_group = G;
+    e = cudaStreamCreateWithFlags(&p->hin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->hout, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_start, cudaEventDisableTiming);
+    for (int k = 0; k < kHostBufs && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&p->hev_in[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_done[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_out[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "host staging streams");
+    return SE2_OK;
+}
+
+namespace {
+se2_status plan_create_impl(se2_plan_t* out, int N, int M, int batch, se2_precision precision, unsigned flags,
+                            int device, size_t max_scratch);
+}
+
 se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precision precision,
                            unsigned flags, int device) {
+    SE2_RANGE("se2_plan_create");
+    return plan_create_impl(out, N, M, batch, precision, flags, device, 0);
+}
+
+namespace {
+// max_scratch > 0 caps the scratch (problem slots) below the default 1 GiB.
+se2_status plan_create_impl(se2_plan_t* out, int N, int M, int batch, se2_precision precision, unsigned flags,
+                            int device, size_t max_scratch) {
     if (out == nullptr) return fail(SE2_ERR_INVALID_ARG, "plan output pointer is NULL");
     *out = nullptr;
     if (!is_pow2(N) || N < 8 || N > 512) return fail(SE2_ERR_UNSUPPORTED, "N=%d: need a power of two in [8, 512]", N);
@@ -899,7 +998,8 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     if (precision != SE2_F32 && precision != SE2_F64 && precision != SE2_SPLIT_BF16 && precision != SE2_BF16 &&
         precision != SE2_SPLIT_F16)
         return fail(SE2_ERR_UNSUPPORTED, "precision %d not supported", (int)precision);
-    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT | SE2_GRID_ORIGIN_ZERO | SE2_MASS_RENORM | SE2_KERNEL_YSYM))
+    if (flags & ~(SE2_SHARED_KERNEL | SE2_PERSISTENT | SE2_GRID_ORIGIN_ZERO | SE2_MASS_RENORM | SE2_KERNEL_YSYM |
+                  SE2_HOST_STAGING | SE2_CHECK_FINITE))
         return fail(SE2_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -922,7 +1022,7 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     // scratch for `chunk` problems at a time (whole batch up to 1 GiB);
     // SE2_MAX_CHUNK (environment) caps it, e.g. to exercise ragged chunks.
     const size_t per = p->s_pstride * p->elem;
-    size_t chunk = (size_t)1 << 30;
+    size_t chunk = max_scratch > 0 ? max_scratch : (size_t)1 << 30;
     chunk = chunk / per;
     if (const char* env = getenv("SE2_MAX_CHUNK")) {
         const long v = strtol(env, nullptr, 10);
@@ -940,7 +1040,7 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
     // at least two slots: the adjoint transforms grad_out and f side by side
     p->nslots = chunk < 2 ? 2 : (int)chunk;
     const size_t scratch_bytes = per * p->nslots;
-    e = cudaMalloc(&p->scratch, scratch_bytes);
+    e = dev_alloc((void**)&p->scratch, scratch_bytes);
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "scratch (%zu bytes): %s", scratch_bytes, cudaGetErrorString(e)); }
     if (p->fast && p->ft.flow != nullptr && !encode_flow_maps(p)) p->ft.flow = nullptr;   // keep the pipelined units
     if (p->fast) {
@@ -967,27 +1067,33 @@ se2_status se2_plan_create(se2_plan_t* out, int N, int M, int batch, se2_precisi
             p->pipe_group = group;
         }
     }
-    e = cudaMalloc((void**)&p->tab, sizeof(double) * 2 * ((size_t)N + M));
+    e = dev_alloc((void**)&p->tab, sizeof(double) * 2 * ((size_t)N + M));
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "tables: %s", cudaGetErrorString(e)); }
-    e = cudaMalloc((void**)&p->abs_sum, sizeof(double) * chunk);
+    e = dev_alloc((void**)&p->abs_sum, sizeof(double) * chunk);
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "accumulators: %s", cudaGetErrorString(e)); }
     if (flags & SE2_MASS_RENORM) {
-        e = cudaMalloc((void**)&p->mass, sizeof(double) * 2 * (size_t)batch);
+        e = dev_alloc((void**)&p->mass, sizeof(double) * 2 * (size_t)batch);
         if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "mass sums: %s", cudaGetErrorString(e)); }
     }
-    e = cudaMalloc((void**)&p->ctr, sizeof(unsigned) * (1 + 3 * (size_t)batch));
+    e = dev_alloc((void**)&p->ctr, sizeof(unsigned) * (1 + 3 * (size_t)batch));
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "counters: %s", cudaGetErrorString(e)); }
-    e = cudaMalloc((void**)&p->err, sizeof(int));
+    e = dev_alloc((void**)&p->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
     if (e != cudaSuccess) { plan_free(p); delete p; return fail(SE2_ERR_OOM, "error word: %s", cudaGetErrorString(e)); }
+    if (flags & SE2_HOST_STAGING) {
+        st = host_staging_init(p);
+        if (st != SE2_OK) { plan_free(p); delete p; return st; }
+    }
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { plan_free(p); delete p; return cuda_fail(e, "plan setup"); }
     p->ws_bytes = per * p->nslots + sizeof(double) * 2 * ((size_t)N + M) + p->elem * (N + M) + sizeof(double) * chunk + sizeof(unsigned) * (1 + 3 * (size_t)batch) + sizeof(int);
     *out = p;
     return SE2_OK;
 }
+}  // namespace
 
 se2_status se2_plan_destroy(se2_plan_t p) {
+    SE2_RANGE("se2_plan_destroy");
     if (p == nullptr) return SE2_OK;
     DeviceGuard guard(p->dev);
     cudaDeviceSynchronize();
@@ -1000,6 +1106,7 @@ size_t se2_plan_workspace_bytes(se2_plan_t p) { return p ? p->ws_bytes : 0; }
 
 se2_status se2_coeffs(se2_plan_t p, const void* samples, int n, void* coeffs, double* log_scale,
                       void* stream) {
+    SE2_RANGE("se2_coeffs");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (samples == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "samples/coeffs is NULL");
@@ -1015,6 +1122,7 @@ se2_status se2_coeffs(se2_plan_t p, const void* samples, int n, void* coeffs, do
 
 se2_status se2_convolve_chain(se2_plan_t p, const void* f, int B, const void* const* coeffs,
                               const double* const* log_scales, int k, void* out, void* stream) {
+    SE2_RANGE("se2_convolve_chain");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (f == nullptr || out == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -1039,15 +1147,18 @@ se2_status se2_convolve_chain(se2_plan_t p, const void* f, int B, const void* co
     }
     st = !is_f64(p) ? run_chain<float>(p, f, B, coeffs, log_scales, k, out, s)
                     : run_chain<double>(p, f, B, coeffs, log_scales, k, out, s);
-    if (st != SE2_OK || !renorm) return st;
-    cudaError_t e = !is_f64(p) ? launch_mass_fix<float>(p, out, B, coeffs, log_scales, k, s)
-                               : launch_mass_fix<double>(p, out, B, coeffs, log_scales, k, s);
-    if (e != cudaSuccess) return cuda_fail(e, "mass renormalisation");
-    return SE2_OK;
+    if (st != SE2_OK) return st;
+    if (renorm) {
+        cudaError_t e = !is_f64(p) ? launch_mass_fix<float>(p, out, B, coeffs, log_scales, k, s)
+                                   : launch_mass_fix<double>(p, out, B, coeffs, log_scales, k, s);
+        if (e != cudaSuccess) return cuda_fail(e, "mass renormalisation");
+    }
+    return check_finite(p, out, (size_t)p->N * p->N * p->M * B, s);
 }
 
 se2_status se2_convolve_host(se2_plan_t p, const void* f, int B, const void* coeffs, const double* log_scale,
                              void* out, void* stream) {
+    SE2_RANGE("se2_convolve_host");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (f == nullptr || out == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -1060,24 +1171,8 @@ se2_status se2_convolve_host(se2_plan_t p, const void* f, int B, const void* coe
     if (fa < oa + len && oa < fa + len) return fail(SE2_ERR_INVALID_ARG, "out overlaps f");
     DeviceGuard guard(p->dev);
     cudaError_t e = cudaSuccess;
-    if (p->hstage == nullptr) {   // first call: staging buffers, copy streams, events
-        int G = kHostGroup;   // SE2_HOST_GROUP (environment) overrides the group size
-        if (const char* v = getenv("SE2_HOST_GROUP")) G = (int)strtol(v, nullptr, 10);
-        if (G < 1) G = 1;
-        if (G > p->batch) G = p->batch;
-        e = cudaMalloc(&p->hstage, 2 * gbytes * (size_t)G * kHostBufs);
-        if (e != cudaSuccess) { p->hstage = nullptr; return fail(SE2_ERR_OOM, "host staging: %s", cudaGetErrorString(e)); }
-        p->host_group = G;
-        e = cudaStreamCreateWithFlags(&p->hin, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->hout, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_start, cudaEventDisableTiming);
-        for (int k = 0; k < kHostBufs && e == cudaSuccess; ++k) {
-            e = cudaEventCreateWithFlags(&p->hev_in[k], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_done[k], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hev_out[k], cudaEventDisableTiming);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "host staging streams");
-    }
+    if (p->hstage == nullptr)
+        return fail(SE2_ERR_INVALID_ARG, "the plan was created without SE2_HOST_STAGING (no staging buffers)");
     const int G = p->host_group;
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
     const long long lps = (p->flags & SE2_SHARED_KERNEL) ? 0 : 1;
@@ -1119,6 +1214,7 @@ se2_status se2_convolve_host(se2_plan_t p, const void* f, int B, const void* coe
 
 se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void* const* coeffs,
                                   const double* const* log_scales, int k, void* out, void* stream) {
+    SE2_RANGE("se2_convolve_chain_all");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (f == nullptr || out == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -1145,7 +1241,7 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
                             : run_chain<double>(p, f, B, coeffs, log_scales, q, op, s);
             if (st != SE2_OK) return st;
         }
-        return SE2_OK;
+        return check_finite(p, out, gs * (size_t)k * B, s);
     }
     const FastTable& ft = p->ft;
     const long long cps = (p->flags & SE2_SHARED_KERNEL) ? 0 : (long long)p->M * p->N * (p->N / 2 + 1);
@@ -1162,6 +1258,7 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
         a.twM = (const float2*)p->twM;
         a.inv_L = 1.0 / ((double)p->N * p->N * p->M);
         a.wsign = (p->flags & SE2_GRID_ORIGIN_ZERO) ? 0 : 1;
+        a.ymirror = (p->flags & SE2_KERNEL_YSYM) ? 1 : 0;   // the running-product pass folds rows too
         a.k = k;
         a.c_pstride = cps;
         a.ls_pstride = lps;
@@ -1191,12 +1288,13 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-    return SE2_OK;
+    return check_finite(p, out, gs * (size_t)k * B, s);
 }
 
 se2_status se2_backward(se2_plan_t p, const void* grad_out, const void* f, int B, const void* coeffs,
                         const double* log_scale, int n_params, const void* const* dcoeffs,
                         double* grad_params, void* grad_f, void* stream) {
+    SE2_RANGE("se2_backward");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (grad_out == nullptr || coeffs == nullptr) return fail(SE2_ERR_INVALID_ARG, "grad_out/coeffs is NULL");
@@ -1214,13 +1312,16 @@ se2_status se2_backward(se2_plan_t p, const void* grad_out, const void* f, int B
     if (grad_f != nullptr && (grad_f == grad_out || grad_f == f)) return fail(SE2_ERR_INVALID_ARG, "grad_f aliases an input");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
-    return !is_f64(p)
-               ? run_backward<float>(p, grad_out, f, B, coeffs, log_scale, n_params, dcoeffs, grad_params, grad_f, s)
-               : run_backward<double>(p, grad_out, f, B, coeffs, log_scale, n_params, dcoeffs, grad_params, grad_f, s);
+    st = !is_f64(p)
+             ? run_backward<float>(p, grad_out, f, B, coeffs, log_scale, n_params, dcoeffs, grad_params, grad_f, s)
+             : run_backward<double>(p, grad_out, f, B, coeffs, log_scale, n_params, dcoeffs, grad_params, grad_f, s);
+    if (st != SE2_OK || grad_f == nullptr) return st;
+    return check_finite(p, grad_f, (size_t)p->N * p->N * p->M * B, s);
 }
 
 se2_status se2_sample_radial_gaussian(se2_plan_t p, double sigma, double sigma_theta, double nu, void* P,
                                       void* dP_dsigma, void* dP_dsigma_theta, void* stream) {
+    SE2_RANGE("se2_sample_radial_gaussian");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (!(sigma > 0) || !(sigma_theta > 0)) return fail(SE2_ERR_INVALID_ARG, "sigma and sigma_theta must be > 0");
@@ -1252,6 +1353,7 @@ static int sampler_blocks(const se2_plan_s* p) {
 
 se2_status se2_sample_se2_gaussian(se2_plan_t p, const double* beta, const double* Sigma, int images, void* P,
                                    void* stream) {
+    SE2_RANGE("se2_sample_se2_gaussian");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (beta == nullptr || Sigma == nullptr || P == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -1277,6 +1379,7 @@ se2_status se2_sample_se2_gaussian(se2_plan_t p, const double* beta, const doubl
 
 se2_status se2_sample_deformed_gaussian(se2_plan_t p, const double* H, double nu, double s_theta, int images, void* P,
                                         void* stream) {
+    SE2_RANGE("se2_sample_deformed_gaussian");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (H == nullptr || P == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -1302,6 +1405,7 @@ se2_status se2_sample_deformed_gaussian(se2_plan_t p, const double* H, double nu
 
 se2_status se2_separable_tables(se2_plan_t p, const double* params, const int* k, int kmax, int B, void* tables,
                                 void* stream) {
+    SE2_RANGE("se2_separable_tables");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (params == nullptr || k == nullptr || tables == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -1325,6 +1429,7 @@ se2_status se2_separable_tables(se2_plan_t p, const double* params, const int* k
 }
 
 se2_status se2_convolve_separable(se2_plan_t p, const void* f, int B, const void* tables, void* out, void* stream) {
+    SE2_RANGE("se2_convolve_separable");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (f == nullptr || tables == nullptr || out == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -1334,10 +1439,13 @@ se2_status se2_convolve_separable(se2_plan_t p, const void* f, int B, const void
     if (f == out) return fail(SE2_ERR_INVALID_ARG, "out aliases f");
     DeviceGuard guard(p->dev);
     cudaStream_t s = (cudaStream_t)stream;
-    return !is_f64(p) ? run_sep<float>(p, f, B, tables, out, s) : run_sep<double>(p, f, B, tables, out, s);
+    st = !is_f64(p) ? run_sep<float>(p, f, B, tables, out, s) : run_sep<double>(p, f, B, tables, out, s);
+    if (st != SE2_OK) return st;
+    return check_finite(p, out, (size_t)p->N * p->N * p->M * B, s);
 }
 
 se2_status se2_plan_status(se2_plan_t p, void* stream) {
+    SE2_RANGE("se2_plan_status");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     DeviceGuard guard(p->dev);
@@ -1349,12 +1457,15 @@ se2_status se2_plan_status(se2_plan_t p, void* stream) {
     if (h != 0) {
         e = cudaMemset(p->err, 0, sizeof(int));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
-        return fail(SE2_ERR_TIMEOUT, "a bounded device-side wait gave up (code %d: 1 persistent kernel, 2 tensor cores)", h);
+        if (h == 5) return fail(SE2_ERR_NUMERIC, "an output held NaN or infinity (SE2_CHECK_FINITE)");
+        return fail(SE2_ERR_TIMEOUT, "a bounded device-side wait gave up (code %d: 1 persistent kernel, 2 tensor cores, "
+                                     "3 bulk-copy units, 4 dataflow kernel)", h);
     }
     return SE2_OK;
 }
 
 se2_status se2_debug_wait_timeout(se2_plan_t p, const void* f, const void* coeffs, void* out, void* stream) {
+    SE2_RANGE("se2_debug_wait_timeout");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (!p->persist) return fail(SE2_ERR_UNSUPPORTED, "plan does not use the persistent kernel");
@@ -1368,6 +1479,7 @@ se2_status se2_debug_wait_timeout(se2_plan_t p, const void* f, const void* coeff
 unsigned long long se2_plan_launches(se2_plan_t p) { return p == nullptr ? 0ull : p->launches; }
 
 se2_status se2_plan_timing(se2_plan_t p, int on) {
+    SE2_RANGE("se2_plan_timing");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     p->timing = on != 0;
@@ -1376,6 +1488,7 @@ se2_status se2_plan_timing(se2_plan_t p, int on) {
 }
 
 se2_status se2_plan_timing_read(se2_plan_t p, double* ms, long long* count) {
+    SE2_RANGE("se2_plan_timing_read");
     se2_status st = check_plan(p);
     if (st != SE2_OK) return st;
     if (ms == nullptr || count == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -1397,9 +1510,342 @@ se2_status se2_plan_timing_read(se2_plan_t p, double* ms, long long* count) {
 
 se2_status se2_convolve(se2_plan_t p, const void* f, int B, const void* coeffs, const double* log_scale,
                         void* out, void* stream) {
+    SE2_RANGE("se2_convolve");
     const void* c[1] = {coeffs};
     const double* l[1] = {log_scale};
     return se2_convolve_chain(p, f, B, c, l, 1, out, stream);
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch plans: many independent problems of uneven sizes (N, M), each with a
+// chain of separable radial kernels in factored form.
+// ---------------------------------------------------------------------------
+struct se2_batch_plan_s {
+    struct Class {
+        int N = 0, M = 0, count = 0, first = 0;   // first: packed position of its first problem
+        long long goff = 0, toff = 0;             // offsets of its block in the packed grids / tables
+        se2_plan_s* plan = nullptr;               // sub-plan (the chosen path)
+        se2_plan_s* alt = nullptr;                // the other path's plan while tuning
+        bool persistent = false;
+        cudaStream_t st = nullptr;                // own stream (class 0 uses the caller's)
+        cudaEvent_t done = nullptr;
+        double tuned_ms = 0;
+    };
+    int n = 0, dev = 0;
+    se2_precision prec = SE2_F32;
+    unsigned flags = 0;
+    std::vector<Class> cls;
+    std::vector<int> pos;                         // problem -> packed position
+    std::vector<long long> goff, toff;            // per problem: packed grid / table offset
+    long long gtotal = 0, ttotal = 0;
+    cudaEvent_t fork = nullptr;
+};
+
+namespace {
+
+constexpr size_t kBatchScratch = (size_t)512 << 20;   // scratch cap of one class's sub-plan
+
+void batch_free(se2_batch_plan_s* b) {
+    for (auto& c : b->cls) {
+        if (c.plan) se2_plan_destroy(c.plan);
+        if (c.alt) se2_plan_destroy(c.alt);
+        if (c.st) cudaStreamDestroy(c.st);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+// Pipeline streams (depth 2) for a sub-plan whose creation chose depth 1, so
+// that the tuner can try both.
+se2_status ensure_pipe_streams(se2_plan_s* p) {
+    if (p->aux[1] != nullptr) return SE2_OK;
+    cudaError_t e = cudaSuccess;
+    if (p->ev_fork == nullptr) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux[1], cudaStreamNonBlocking);
+    if (e == cudaSuccess && p->ev_join[1] == nullptr) e = cudaEventCreateWithFlags(&p->ev_join[1], cudaEventDisableTiming);
+    return e == cudaSuccess ? SE2_OK : cuda_fail(e, "pipeline streams");
+}
+
+se2_status batch_check(se2_batch_plan_s* b) {
+    if (b == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL batch plan");
+    return SE2_OK;
+}
+
+// One class's convolutions on stream s with its current sub-plan.
+se2_status batch_run_class(se2_batch_plan_s* b, se2_batch_plan_s::Class& c, const unsigned char* f, const unsigned char* tab,
+                           unsigned char* out, cudaStream_t s) {
+    const size_t re = b->prec == SE2_F64 ? sizeof(double) : sizeof(float);
+    return se2_convolve_separable(c.plan, f + c.goff * re, c.count, tab + c.toff * 2 * re, out + c.goff * re, s);
+}
+
+}  // namespace
+
+se2_status se2_batch_plan_create(se2_batch_plan_t* out, const se2_shape* shapes, int n, se2_precision precision,
+                                 unsigned flags, int device) {
+    SE2_RANGE("se2_batch_plan_create");
+    if (out == nullptr || shapes == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    *out = nullptr;
+    if (n < 1) return fail(SE2_ERR_INVALID_ARG, "n_problems=%d must be >= 1", n);
+    if (flags & ~(SE2_GRID_ORIGIN_ZERO | SE2_CHECK_FINITE)) return fail(SE2_ERR_INVALID_ARG, "unsupported flags 0x%x", flags);
+    for (int i = 0; i < n; ++i) {
+        const int N = shapes[i].N, M = shapes[i].M;
+        if (!is_pow2(N) || N < 8 || N > 512 || !is_pow2(M) || M < 2 || M > 128)
+            return fail(SE2_ERR_UNSUPPORTED, "problem %d: N=%d, M=%d outside the plan sizes", i, N, M);
+    }
+    se2_batch_plan_s* b = new (std::nothrow) se2_batch_plan_s();
+    if (b == nullptr) return fail(SE2_ERR_OOM, "host allocation failed");
+    b->n = n;
+    b->dev = device;
+    b->prec = precision;
+    b->flags = flags;
+    // size classes, largest total work first; problems keep their order inside a class
+    std::vector<std::pair<long long, long long>> key;   // (N, M) packed -> index
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < n; ++i) {
+        const long long k = (long long)shapes[i].N << 32 | (unsigned)shapes[i].M;
+        size_t c = 0;
+        while (c < key.size() && key[c].first != k) ++c;
+        if (c == key.size()) {
+            key.push_back({k, (long long)c});
+            members.emplace_back();
+        }
+        members[c].push_back(i);
+    }
+    std::vector<size_t> order(key.size());
+    for (size_t c = 0; c < order.size(); ++c) order[c] = c;
+    auto work = [&](size_t c) {
+        const long long N = key[c].first >> 32, M = key[c].first & 0xffffffffll;
+        return N * N * M * (long long)members[c].size();
+    };
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t c) { return work(a) > work(c) || (work(a) == work(c) && a < c); });
+    b->pos.assign(n, 0);
+    b->goff.assign(n, 0);
+    b->toff.assign(n, 0);
+    int at = 0;
+    for (size_t oc : order) {
+        se2_batch_plan_s::Class c;
+        c.N = (int)(key[oc].first >> 32);
+        c.M = (int)(key[oc].first & 0xffffffffll);
+        c.count = (int)members[oc].size();
+        c.first = at;
+        c.goff = b->gtotal;
+        c.toff = b->ttotal;
+        for (int i : members[oc]) {
+            b->pos[i] = at++;
+            b->goff[i] = b->gtotal;
+            b->toff[i] = b->ttotal;
+            b->gtotal += (long long)c.N * c.N * c.M;
+            b->ttotal += (long long)(c.N / 2 + 1 + c.N + c.M);
+        }
+        b->cls.push_back(c);
+    }
+    DeviceGuard guard(device);
+    se2_status st = SE2_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) { batch_free(b); return cuda_fail(e, "events"); }
+    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+        auto& c = b->cls[ci];
+        st = plan_create_impl(&c.plan, c.N, c.M, c.count, precision, flags, device, kBatchScratch);
+        if (st == SE2_OK && c.plan->fast && c.plan->nslots >= 2) st = ensure_pipe_streams(c.plan);
+        if (st == SE2_OK && ci > 0) {
+            e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming);
+            if (e != cudaSuccess) st = cuda_fail(e, "class streams");
+        }
+        if (st != SE2_OK) { batch_free(b); return st; }
+    }
+    *out = b;
+    return SE2_OK;
+}
+
+se2_status se2_batch_plan_destroy(se2_batch_plan_t b) {
+    SE2_RANGE("se2_batch_plan_destroy");
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    DeviceGuard guard(b->dev);
+    cudaDeviceSynchronize();
+    batch_free(b);
+    return SE2_OK;
+}
+
+se2_status se2_batch_plan_layout(se2_batch_plan_t b, int* position, long long* grid_offset, long long* table_offset,
+                                 long long* grid_total, long long* table_total) {
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    for (int i = 0; i < b->n; ++i) {
+        if (position) position[i] = b->pos[i];
+        if (grid_offset) grid_offset[i] = b->goff[i];
+        if (table_offset) table_offset[i] = b->toff[i];
+    }
+    if (grid_total) *grid_total = b->gtotal;
+    if (table_total) *table_total = b->ttotal;
+    return SE2_OK;
+}
+
+se2_status se2_batch_separable_tables(se2_batch_plan_t b, const double* params, const int* k, int kmax, void* tables,
+                                      void* stream) {
+    SE2_RANGE("se2_batch_separable_tables");
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    if (params == nullptr || k == nullptr || tables == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    const size_t re = b->prec == SE2_F64 ? sizeof(double) : sizeof(float);
+    DeviceGuard guard(b->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto& c : b->cls) {
+        st = se2_separable_tables(c.plan, params + (size_t)c.first * kmax * 3, k + c.first, kmax, c.count,
+                                  static_cast<unsigned char*>(tables) + c.toff * 2 * re, s);
+        if (st != SE2_OK) return st;
+    }
+    return SE2_OK;
+}
+
+se2_status se2_batch_convolve_separable(se2_batch_plan_t b, const void* f, const void* tables, void* out, void* stream) {
+    SE2_RANGE("se2_batch_convolve_separable");
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    if (f == nullptr || tables == nullptr || out == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    const size_t re = b->prec == SE2_F64 ? sizeof(double) : sizeof(float);
+    if (!aligned(f, re) || !aligned(out, re) || !aligned(tables, 2 * re)) return fail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    const uintptr_t fa = (uintptr_t)f, oa = (uintptr_t)out, len = (uintptr_t)b->gtotal * re;
+    if (fa < oa + len && oa < fa + len) return fail(SE2_ERR_INVALID_ARG, "out overlaps f");
+    DeviceGuard guard(b->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto* fb = static_cast<const unsigned char*>(f);
+    const auto* tb = static_cast<const unsigned char*>(tables);
+    auto* ob = static_cast<unsigned char*>(out);
+    // the classes run concurrently: class 0 on the caller's stream, the others
+    // on their own streams forked from it and joined back (capturable)
+    cudaError_t e = cudaEventRecord(b->fork, s);
+    for (size_t ci = 1; ci < b->cls.size() && e == cudaSuccess; ++ci) e = cudaStreamWaitEvent(b->cls[ci].st, b->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "class fork");
+    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+        auto& c = b->cls[ci];
+        st = batch_run_class(b, c, fb, tb, ob, ci == 0 ? s : c.st);
+        if (st != SE2_OK) return st;
+    }
+    for (size_t ci = 1; ci < b->cls.size() && e == cudaSuccess; ++ci) {
+        e = cudaEventRecord(b->cls[ci].done, b->cls[ci].st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->cls[ci].done, 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "class join");
+    return SE2_OK;
+}
+
+// The autotuner: per class, time the candidate schedules on the caller's data
+// and keep the fastest.  Candidates: the FP32 fast path with pipeline depth 1
+// (groups of the scratch size) or depth 2 with groups of 1, 2, 4, 8 .. 64
+// problems (as the scratch allows), and the persistent dataflow kernel
+// (SE2_PERSISTENT).  Synchronous; not for stream capture.
+se2_status se2_batch_tune(se2_batch_plan_t b, const void* f, const void* tables, void* out, int reps, void* stream) {
+    SE2_RANGE("se2_batch_tune");
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    if (f == nullptr || tables == nullptr || out == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (reps < 1) reps = 1;
+    DeviceGuard guard(b->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(e, "events");
+    const auto* fb = static_cast<const unsigned char*>(f);
+    const auto* tb = static_cast<const unsigned char*>(tables);
+    auto* ob = static_cast<unsigned char*>(out);
+    auto time_class = [&](se2_batch_plan_s::Class& c, float* ms) -> se2_status {
+        se2_status r = batch_run_class(b, c, fb, tb, ob, s);   // warm-up
+        if (r != SE2_OK) return r;
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < reps && r == SE2_OK; ++i) r = batch_run_class(b, c, fb, tb, ob, s);
+        cudaEventRecord(e1, s);
+        if (r != SE2_OK) return r;
+        cudaError_t x = cudaEventSynchronize(e1);
+        if (x == cudaSuccess) x = cudaEventElapsedTime(ms, e0, e1);
+        if (x != cudaSuccess) return cuda_fail(x, "tuning events");
+        *ms /= reps;
+        return SE2_OK;
+    };
+    for (auto& c : b->cls) {
+        float best = 0.f, ms = 0.f;
+        int bd = c.plan->pipe_depth, bg = c.plan->pipe_group;
+        bool bp = false;
+        if (c.plan->fast) {
+            std::vector<std::pair<int, int>> cand{{1, c.plan->chunk}};
+            if (c.plan->aux[1] != nullptr)
+                for (int g = 1; g <= 64 && g < c.count; g *= 2)
+                    if (2 * g <= c.plan->nslots) cand.push_back({2, g});
+            bool first = true;
+            for (auto [d, g] : cand) {
+                c.plan->pipe_depth = d;
+                c.plan->pipe_group = d > 1 ? g : 0;
+                st = time_class(c, &ms);
+                if (st != SE2_OK) break;
+                if (first || ms < best) {
+                    best = ms;
+                    bd = d;
+                    bg = c.plan->pipe_group;
+                }
+                first = false;
+            }
+            c.plan->pipe_depth = bd;
+            c.plan->pipe_group = bg;
+            if (st != SE2_OK) break;
+            if (b->prec == SE2_F32) {   // the persistent dataflow kernel
+                se2_plan_s* fast = c.plan;
+                se2_plan_s* pers = nullptr;
+                if (plan_create_impl(&pers, c.N, c.M, c.count, b->prec, b->flags | SE2_PERSISTENT, b->dev, kBatchScratch) == SE2_OK) {
+                    c.plan = pers;
+                    st = time_class(c, &ms);
+                    c.plan = fast;
+                    if (st == SE2_OK && ms < best) {
+                        best = ms;
+                        bp = true;
+                        c.alt = fast;
+                        c.plan = pers;
+                    } else {
+                        se2_plan_destroy(pers);
+                    }
+                    if (st != SE2_OK) break;
+                }
+            }
+        } else {
+            st = time_class(c, &best);
+            if (st != SE2_OK) break;
+        }
+        c.persistent = bp;
+        c.tuned_ms = best;
+        if (c.alt) {   // keep only the chosen path's scratch
+            se2_plan_destroy(c.alt);
+            c.alt = nullptr;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+se2_status se2_batch_plan_config(se2_batch_plan_t b, int* n_classes, se2_shape* shape, int* count, int* depth,
+                                 int* group, int* persistent, double* tuned_ms) {
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    if (n_classes) *n_classes = (int)b->cls.size();
+    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+        const auto& c = b->cls[ci];
+        if (shape) shape[ci] = se2_shape{c.N, c.M};
+        if (count) count[ci] = c.count;
+        if (depth) depth[ci] = c.persistent ? 0 : c.plan->pipe_depth;
+        if (group) group[ci] = c.persistent ? 0 : (c.plan->pipe_depth > 1 ? c.plan->pipe_group : c.plan->chunk);
+        if (persistent) persistent[ci] = c.persistent ? 1 : 0;
+        if (tuned_ms) tuned_ms[ci] = c.tuned_ms;
+    }
+    return SE2_OK;
+}
+
+unsigned long long se2_batch_plan_launches(se2_batch_plan_t b) {
+    if (b == nullptr) return 0;
+    unsigned long long n = 0;
+    for (const auto& c : b->cls) n += c.plan->launches;
+    return n;
+}

@@ -31,6 +31,7 @@
 
 #include "../../include/se2.h"
 #include "se2_internal.h"
+#include "se2_nvtx.h"
 #include "se2_kernels.cuh"
 
 using namespace se2;
@@ -502,10 +503,35 @@ se2_status check_gplan(se2_grid_plan_t p) {
 
 }  // namespace
 
+namespace {
+// f^[k; L] = (-1)^(k1 + k2) C(tau(k)) (Eq. FkLv) from the half spectrum C of
+// real samples; a negative k1 reads the Hermitian partner -k and conjugates.
+template <typename T>
+__global__ void k_ffc_at(const c2<T>* C, int Lx, int Ly, int Lr, int Hx, int k1, int k2, int k3, double* out) {
+    const bool conj = k1 < 0;
+    if (conj) {
+        k1 = -k1;
+        k2 = -k2;
+        k3 = -k3;
+    }
+    const int ty = ((k2 % Ly) + Ly) % Ly, tr = ((k3 % Lr) + Lr) % Lr;
+    const c2<T> v = C[((size_t)tr * Ly + ty) * Hx + k1];
+    double re = (double)v.x, im = conj ? -(double)v.y : (double)v.y;
+    if ((k1 + k2) & 1) {
+        re = -re;
+        im = -im;
+    }
+    out[0] = re;
+    out[1] = im;
+    (void)Lx;
+}
+}  // namespace
+
 extern "C" {
 
 se2_status se2_grid_plan_create(se2_grid_plan_t* out, const int* L, const int* N, int batch, int precision,
                                 unsigned flags, int device) {
+    SE2_RANGE("se2_grid_plan_create");
     if (out == nullptr) return gfail(SE2_ERR_INVALID_ARG, "plan pointer is NULL");
     *out = nullptr;
     if (L == nullptr || N == nullptr) return gfail(SE2_ERR_INVALID_ARG, "L or N is NULL");
@@ -546,10 +572,10 @@ se2_status se2_grid_plan_create(se2_grid_plan_t* out, const int* L, const int* N
     }
     ta.total = acc;
     const size_t ws = (size_t)batch * p->Nr * p->Ny * p->Hx * p->celem;
-    cudaError_t e = cudaMalloc(&p->tab, (size_t)acc * p->celem);
-    if (e == cudaSuccess) e = cudaMalloc(&p->buf[0], ws);
-    if (e == cudaSuccess) e = cudaMalloc(&p->buf[1], ws);
-    if (e == cudaSuccess) e = cudaMalloc(&p->buf[2], (size_t)batch * p->Lr * p->Ly * p->Hx * p->celem);
+    cudaError_t e = dev_alloc((void**)&p->tab, (size_t)acc * p->celem);
+    if (e == cudaSuccess) e = dev_alloc((void**)&p->buf[0], ws);
+    if (e == cudaSuccess) e = dev_alloc((void**)&p->buf[1], ws);
+    if (e == cudaSuccess) e = dev_alloc((void**)&p->buf[2], (size_t)batch * p->Lr * p->Ly * p->Hx * p->celem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         se2_grid_plan_destroy(p);
@@ -575,13 +601,14 @@ se2_status se2_grid_plan_create(se2_grid_plan_t* out, const int* L, const int* N
 }
 
 se2_status se2_grid_plan_destroy(se2_grid_plan_t p) {
+    SE2_RANGE("se2_grid_plan_destroy");
     if (p == nullptr) return SE2_OK;
     {
         GDevice guard(p->dev);
-        if (p->tab) cudaFree(p->tab);
-        if (p->buf[0]) cudaFree(p->buf[0]);
-        if (p->buf[1]) cudaFree(p->buf[1]);
-        if (p->buf[2]) cudaFree(p->buf[2]);
+        if (p->tab) dev_free(p->tab);
+        if (p->buf[0]) dev_free(p->buf[0]);
+        if (p->buf[1]) dev_free(p->buf[1]);
+        if (p->buf[2]) dev_free(p->buf[2]);
     }
     delete p;
     return SE2_OK;
@@ -596,6 +623,7 @@ static int grid_sampler_blocks(const se2_grid_plan_s* p) {
 
 se2_status se2_grid_sample_se2_gaussian(se2_grid_plan_t p, const double* beta, const double* Sigma, int images,
                                         void* P, void* stream) {
+    SE2_RANGE("se2_grid_sample_se2_gaussian");
     se2_status st = check_gplan(p);
     if (st != SE2_OK) return st;
     if (beta == nullptr || Sigma == nullptr || P == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -621,6 +649,7 @@ se2_status se2_grid_sample_se2_gaussian(se2_grid_plan_t p, const double* beta, c
 
 se2_status se2_grid_sample_deformed_gaussian(se2_grid_plan_t p, const double* H, double nu, double s_theta,
                                              int images, void* P, void* stream) {
+    SE2_RANGE("se2_grid_sample_deformed_gaussian");
     se2_status st = check_gplan(p);
     if (st != SE2_OK) return st;
     if (H == nullptr || P == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -645,6 +674,7 @@ se2_status se2_grid_sample_deformed_gaussian(se2_grid_plan_t p, const double* H,
 }
 
 se2_status se2_accuracy_order(double eps, double grad_inf, int k_inf, double constant, long long* K) {
+    SE2_RANGE("se2_accuracy_order");
     if (K == nullptr) return gfail(SE2_ERR_INVALID_ARG, "K is NULL");
     *K = 0;
     if (!(eps > 0) || !(eps < 1e300)) return gfail(SE2_ERR_INVALID_ARG, "eps=%g must be finite and > 0", eps);
@@ -662,6 +692,7 @@ se2_status se2_accuracy_order(double eps, double grad_inf, int k_inf, double con
 }
 
 se2_status se2_grid_coeffs(se2_grid_plan_t p, const void* samples, int n, void* coeffs, void* stream) {
+    SE2_RANGE("se2_grid_coeffs");
     se2_status st = check_gplan(p);
     if (st != SE2_OK) return st;
     if (samples == nullptr || coeffs == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -680,8 +711,35 @@ se2_status se2_grid_coeffs(se2_grid_plan_t p, const void* samples, int n, void* 
     return SE2_OK;
 }
 
+se2_status se2_grid_ffc_at(se2_grid_plan_t p, const void* coeffs, int index, int k1, int k2, int k3, double* out,
+                           void* stream) {
+    SE2_RANGE("se2_grid_ffc_at");
+    se2_status st = check_gplan(p);
+    if (st != SE2_OK) return st;
+    if (coeffs == nullptr || out == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    if (index < 0 || index >= p->batch) return gfail(SE2_ERR_INVALID_ARG, "index=%d outside [0, %d)", index, p->batch);
+    const int Kx = (p->Lx - 1) / 2, Ky = (p->Ly - 1) / 2, Kr = (p->Lr - 1) / 2;
+    if (k1 < -Kx || k1 > Kx || k2 < -Ky || k2 > Ky || k3 < -Kr || k3 > Kr)
+        return gfail(SE2_ERR_INVALID_ARG, "k = (%d, %d, %d) outside |k| <= K = (%d, %d, %d)", k1, k2, k3, Kx, Ky, Kr);
+    if (!galigned(coeffs, p->celem) || !galigned(out, 8)) return gfail(SE2_ERR_INVALID_ARG, "misaligned pointer");
+    GDevice guard(p->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t per = (size_t)p->Lr * p->Ly * p->Hx;
+    if (p->prec == SE2_F64)
+        k_ffc_at<double><<<1, 1, 0, s>>>(static_cast<const c2<double>*>(coeffs) + (size_t)index * per, p->Lx, p->Ly, p->Lr,
+                                         p->Hx, k1, k2, k3, out);
+    else
+        k_ffc_at<float><<<1, 1, 0, s>>>(static_cast<const c2<float>*>(coeffs) + (size_t)index * per, p->Lx, p->Ly, p->Lr,
+                                        p->Hx, k1, k2, k3, out);
+    ++p->launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gcuda(e, "kernel launch");
+    return SE2_OK;
+}
+
 se2_status se2_grid_convolve_chain(se2_grid_plan_t p, const void* f, int B, const void* const* coeffs, int k,
                                    void* out, void* stream) {
+    SE2_RANGE("se2_grid_convolve_chain");
     se2_status st = check_gplan(p);
     if (st != SE2_OK) return st;
     if (f == nullptr || out == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
@@ -704,6 +762,7 @@ se2_status se2_grid_convolve_chain(se2_grid_plan_t p, const void* f, int B, cons
 
 se2_status se2_grid_convolve_chain_all(se2_grid_plan_t p, const void* f, int B, const void* const* coeffs, int k,
                                        void* out, void* stream) {
+    SE2_RANGE("se2_grid_convolve_chain_all");
     se2_status st = check_gplan(p);
     if (st != SE2_OK) return st;
     if (f == nullptr || out == nullptr || coeffs == nullptr) return gfail(SE2_ERR_INVALID_ARG, "NULL pointer argument");

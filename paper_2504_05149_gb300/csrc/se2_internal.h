@@ -80,6 +80,11 @@ using TcKernel = void (*)(TcArgs);
 bool tc_kernel(int M, int dir, int split, int fmt, TcKernel* out, size_t* smem);
 void tc_dft_matrix(int dir, int fmt, std::vector<unsigned char>& img);
 
+// Device allocations of the library (plans, grid plans): counted, and made
+// to fail on request (se2_debug_alloc_stats, se2_debug_fail_alloc).
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+
 // Sets the thread-local text returned by se2_last_error().
 void set_last_error(const char* msg);
 

@@ -240,7 +240,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(TcArgs a) {
         }
         phase ^= 1u;
         ok = __syncthreads_and((int)done) != 0;      // one decision for the whole block
-        if (!ok && tid == 0) atomicExch(a.err, 2);
+        if (!ok) {
+            // the block leaves the tile loop: no further operand writes or MMAs;
+            // one more bounded wait lets the MMAs in flight finish before the
+            // tensor memory is released
+            if (tid == 0) atomicExch(a.err, 2);
+            uint32_t late = done;
+            for (long it = 0; it < (1L << 22) && !late; ++it) {
+                asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                             : "=r"(late) : "r"(smem_u32(&mbar)), "r"(phase ^ 1u) : "memory");
+            }
+            break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // 4. read the lines back and write them in place: warps w and w + 4
         //    share the lanes 32 (w % 4) .. +31 and take columns [0, 64) and

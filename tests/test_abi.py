@@ -117,3 +117,27 @@ def test_accuracy_order_rejects_bad_input(lib, eps, grad, kinf):
                                        ctypes.POINTER(ctypes.c_longlong)]
     K = ctypes.c_longlong(-1)
     assert lib.se2_accuracy_order(eps, grad, kinf, 0.0, ctypes.byref(K)) == 1
+
+
+def test_unknown_plan_flag_rejected_on_host(lib):
+    h = ctypes.c_void_p(1)
+    lib.se2_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_uint, ctypes.c_int]
+    assert lib.se2_plan_create(ctypes.byref(h), 32, 16, 1, 1, 0x80, 0) == 1
+    assert not h.value
+
+
+def test_allocation_accounting_entry_points(lib):
+    """se2_debug_alloc_stats / se2_debug_fail_alloc work without a device:
+    nothing has been allocated in this process, bad arguments are rejected,
+    and arming or disarming the failure injection succeeds."""
+    ll = ctypes.c_longlong
+    lib.se2_debug_alloc_stats.argtypes = [ctypes.POINTER(ll), ctypes.POINTER(ll)]
+    lib.se2_debug_fail_alloc.argtypes = [ll]
+    live, total = ll(-1), ll(-1)
+    assert lib.se2_debug_alloc_stats(ctypes.byref(live), ctypes.byref(total)) == 0
+    assert live.value == 0 and total.value == 0
+    assert lib.se2_debug_alloc_stats(None, ctypes.byref(total)) == 1
+    assert lib.se2_debug_fail_alloc(-1) == 1
+    assert lib.se2_debug_fail_alloc(3) == 0
+    assert lib.se2_debug_fail_alloc(0) == 0

@@ -108,12 +108,50 @@ def test_autograd_function_c5_shape_against_finite_differences(se2):
     gP = O.grad_kernel_samples(Fd, R)
     want = np.array([np.sum(gP * dPs), np.sum(gP * dPt)])
     got = params.grad.cpu().numpy()
-    assert np.max(np.abs(got - want) / np.abs(want)) < 1e-3    # FP32 forward/adjoint vs FP64 oracle
+    # The gradient is an inner product of the residual R = out - target with
+    # f * dP: an FP32 forward output (error ~3e-7 of max|out|) moves R, and
+    # the sum cancels.  The oracle gradient taken on the GPU's own residual
+    # (its FP32 output, exactly) separates that conditioning from the adjoint
+    # kernel's own arithmetic, which must meet the FP32 bar.
+    Rg = out.detach().double().cpu().numpy() - Td
+    gPg = O.grad_kernel_samples(Fd, Rg)
+    want_g = np.array([np.sum(gPg * dPs), np.sum(gPg * dPt)])
+    err_adjoint = float(np.max(np.abs(got - want_g) / np.abs(want_g)))
+    cond = float(np.max(np.abs(want_g - want) / np.abs(want)))
+    err_total = float(np.max(np.abs(got - want) / np.abs(want)))
+    print(f"c5 parameter gradients: vs oracle {err_total:.2e}; adjoint alone {err_adjoint:.2e}; "
+          f"FP32 forward through the loss (oracle on the GPU residual) {cond:.2e}")
+    assert err_adjoint < 1e-5
+    assert err_total < max(1e-5, 2 * cond + 1e-5)
     h = 1e-4
     fd = np.array([(oloss(0.025 + h, 0.25) - oloss(0.025 - h, 0.25)) / (2 * h),
                    (oloss(0.025, 0.25 + h) - oloss(0.025, 0.25 - h)) / (2 * h)])
     assert np.max(np.abs(want - fd) / np.abs(fd)) < 1e-5         # oracle gradient vs FD
-    assert np.max(np.abs(got - fd) / np.abs(fd)) < 1e-3
+    assert np.max(np.abs(got - fd) / np.abs(fd)) < max(1e-5, 2 * cond + 2e-5)
     gf = f.grad.double().cpu().numpy()
     for b in range(B):
-        assert _rel(gf[b], O.adjoint(R[b], [P])) < 1e-4
+        assert _rel(gf[b], O.adjoint(Rg[b], [P])) < 1e-5           # the adjoint of the GPU residual
+        assert _rel(gf[b], O.adjoint(R[b], [P])) < 1e-5
+
+
+def test_autograd_spectra_cached_while_params_unchanged(se2):
+    """SE2Conv reuses the kernel spectra while the params tensor is unchanged
+    (no resampling: fewer launches) and recomputes them after an in-place
+    update; the outputs follow the parameters."""
+    N, M, B = 32, 8, 2
+    plan = se2.Plan(N, M, batch=B, precision="f32", flags=se2.SHARED_KERNEL)
+    f = torch.rand((B, M, N, N), device="cuda")
+    params = torch.tensor([0.04, 0.3], dtype=torch.float64)      # on the host: never read from the device
+    out1 = se2.SE2Conv.apply(f, params, plan)
+    n1 = plan.launches()
+    out2 = se2.SE2Conv.apply(f, params, plan)
+    n2 = plan.launches()
+    assert torch.equal(out1, out2)
+    with torch.no_grad():
+        params[0] = 0.05
+    out3 = se2.SE2Conv.apply(f, params, plan)
+    n3 = plan.launches()
+    assert n3 - n2 > n2 - n1                                     # sampling and coefficients ran again
+    P = O.kernel_samples_and_derivs(N, M, 0.05, 0.3)[0]
+    want = O.convolve(f[0].double().cpu().numpy(), P)
+    assert _rel(out3[0].double().cpu().numpy(), want) < 1e-5

@@ -93,3 +93,38 @@ def test_batch_runner_uneven_sizes_graph(se2, tmp_path):
             assert _rel(runner.out_of(i).double().cpu().numpy(), want) < 1e-5, (i, prob.N, prob.M, len(prob.kernels))
     assert runner.launches_per_run() > 0
     assert (tmp_path / "tune.json").exists()
+
+
+def test_batch_runner_c4_classes_with_256x64(se2, tmp_path):
+    """The batching config's size classes including N = 256 and M = 64, chains
+    of 1..16 kernels: 64 seeded problems drawn as the config draws them, run
+    through the batched runner (autotuned, graph-captured), each against the
+    FP64 oracle."""
+    from paper_2504_05149_gb300.batch import BatchRunner
+    rng = synth.SplitMix64(synth.config_seed(4, 0))
+    shapes, bumps, chains = [], [], []
+    for i in range(64):
+        N = [32, 64, 128, 256][rng.randint(0, 3)]
+        M = [16, 32, 64][rng.randint(0, 2)]
+        k = rng.randint(1, 16)
+        nb = rng.randint(3, 16)
+        shapes.append((N, M))
+        bumps.append(synth.draw_bumps(rng, nb))
+        chains.append([synth.draw_kernel(rng) for _ in range(k)])
+    assert (256, 64) in shapes and max(len(c) for c in chains) >= 12
+    runner = BatchRunner(shapes, cache_path=str(tmp_path / "tune.json"))
+    for i in range(64):
+        N, M = shapes[i]
+        runner.f_of(i).copy_(torch.from_numpy(synth.sample_bumps(N, M, bumps[i]).astype(np.float32)))
+        runner.set_chain(i, [(kp.sigma, kp.sigma_theta, kp.nu) for kp in chains[i]])
+    runner.build_tables()
+    runner.tune(reps=1)
+    runner.capture()
+    runner.replay()
+    torch.cuda.synchronize()
+    for i in range(64):
+        N, M = shapes[i]
+        F = synth.sample_bumps(N, M, bumps[i]).astype(np.float32).astype(np.float64)
+        C = _oracle_chain_coeffs(N, M, chains[i])
+        want = O.convolve_chain(F, None, coeffs=[C] if len(chains[i]) % 2 else [C, 1.0])
+        assert _rel(runner.out_of(i).double().cpu().numpy(), want) < 1e-5, (i, N, M, len(chains[i]))

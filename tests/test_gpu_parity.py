@@ -286,16 +286,20 @@ def test_host_buffer_convolution(se2, pinned):
     rng = np.random.default_rng(13)
     F = rng.standard_normal((B, M, N, N)).astype(np.float32)
     P = rng.random((B, M, N, N)).astype(np.float32)
-    plan = se2.Plan(N, M, batch=B)
+    plan = se2.Plan(N, M, batch=B, flags=se2.HOST_STAGING)
     C, _ = se2.coeffs(plan, torch.from_numpy(P).cuda())
     hf = torch.from_numpy(F)
     if pinned:
         hf = hf.pin_memory()
-    for _ in range(2):   # the second call reuses the staging buffers
+    for _ in range(2):   # the second call reuses the staging buffers; no call allocates
+        before = se2.alloc_stats()
         out = se2.convolve_host(plan, hf, C).double().numpy()
+        assert se2.alloc_stats() == before
         for b in range(B):
             want = O.convolve(F[b].astype(float), P[b].astype(float))
             assert _rel(out[b], want) < 1e-5
+    with pytest.raises(se2.SE2Error):   # a plan without the staging flag
+        se2.convolve_host(se2.Plan(N, M, batch=B), hf, C)
     import ctypes
     lib = se2.load_library()
     st = lib.se2_convolve_host(plan.handle, ctypes.c_void_p(hf.data_ptr()), 2, ctypes.c_void_p(C.data_ptr()), None,
@@ -512,3 +516,9 @@ def test_kernel_ysym_flag_reads_half_the_rows(se2, N, M, k):
     for b in range(B):
         want = O.convolve_chain(Fs[b].astype(np.float64), [P.astype(np.float64) for P in Ps])
         assert _rel(out[b], want) < 1e-5
+    # every intermediate of the chain (Algorithm 6) reads the same folded rows
+    allv = se2.convolve_chain_all(plan, _dev(np.stack(Fs), "f32"), Cs).double().cpu().numpy()
+    for b in range(B):
+        wants = O.convolve_all(Fs[b].astype(np.float64), [P.astype(np.float64) for P in Ps])
+        for p in range(k):
+            assert _rel(allv[p, b], wants[p]) < 1e-5

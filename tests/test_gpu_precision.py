@@ -123,3 +123,66 @@ def test_mass_renormalisation(se2, prec, k, shared):
         assert _rel(outs[flags][b], want) < tol
         # without the flag the mass carries the mode's rounding
         assert abs(outs[0][b].sum() - target) >= abs(got - target)
+
+
+def _chain_coeffs_separable(N, M, kernels):
+    """prod_i C_i of separable kernels, built from the product of their 1-D
+    factors (the exact product of outer products)."""
+    fx = np.ones(N, dtype=np.complex128)
+    fy = np.ones(N, dtype=np.complex128)
+    ft = np.ones(M, dtype=np.complex128)
+    for kp in kernels:
+        gx, gy, gt = synth.kernel_factors(N, M, kp)
+        fx = fx * np.fft.fft(gx) / N
+        fy = fy * np.fft.fft(gy) / N
+        ft = ft * np.fft.fft(gt) / M
+    return ft[:, None, None] * fy[None, :, None] * fx[None, None, :]
+
+
+def test_separable_factor_product_matches_the_oracle_coefficients():
+    """The factor-wise product used below equals the oracle's product of
+    coeffs_separable arrays (checked at a small size)."""
+    N, M = 16, 8
+    rng = synth.SplitMix64(99)
+    kernels = [synth.draw_kernel(rng) for _ in range(5)]
+    want = np.ones((M, N, N), dtype=np.complex128)
+    for kp in kernels:
+        want = want * O.coeffs_separable(*synth.kernel_factors(N, M, kp))
+    got = _chain_coeffs_separable(N, M, kernels)
+    assert np.max(np.abs(got - want)) < 1e-14 * np.max(np.abs(want))
+
+
+def test_c3_full_size_split_modes_vs_oracle(se2):
+    """The precision config at its stated size: N = 512, M = 128, batch 8,
+    32-bump f1 with amplitudes log-uniform in [1e-6, 1], a 32-fold separable
+    kernel chain per problem; split-bf16, split-fp16 and FP32 against the FP64
+    oracle on problems 0 and 7 (bars 1e-3, 1e-5, 1e-5)."""
+    N, M, B, K = 512, 128, 8, 32
+    dev = torch.device("cuda", 0)
+    probs = [synth.make_problem(3, b, N, M, n_bumps=32, n_kernels=K, log_amp=True) for b in range(B)]
+    f = torch.stack([synth.sample_bumps_torch(N, M, p.bumps, dev, torch.float32) for p in probs]).contiguous()
+    params = torch.zeros((B, K, 3), dtype=torch.float64)
+    for b, p in enumerate(probs):
+        for j, kp in enumerate(p.kernels):
+            params[b, j] = torch.tensor([kp.sigma, kp.sigma_theta, kp.nu])
+    params = params.to(dev)
+    kk = torch.full((B,), K, dtype=torch.int32, device=dev)
+    outs = {}
+    for prec in ("split_bf16", "split_f16", "f32"):
+        plan = se2.Plan(N, M, batch=B, precision=prec)
+        tab = se2.separable_tables(plan, params, kk)
+        outs[prec] = se2.convolve_separable(plan, f, tab)
+        plan.status()
+        plan.close()
+    errs = {p: 0.0 for p in outs}
+    for b in (0, 7):
+        F = f[b].double().cpu().numpy()
+        C = _chain_coeffs_separable(N, M, probs[b].kernels)
+        want = O.convolve_chain(F, None, coeffs=[C, 1.0])   # q = 2 coefficient factors: even, no W (32 kernels)
+        for p, o in outs.items():
+            errs[p] = max(errs[p], _rel(o[b].double().cpu().numpy(), want))
+        del C, want
+    print("c3 max-rel errors", errs)
+    assert errs["f32"] < 1e-5
+    assert errs["split_f16"] < 1e-5
+    assert errs["split_bf16"] < 1e-3
