@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--ysym", action="store_true",
                     help="c2: declare the (radial) kernel spectra mirror-symmetric in y (SE2_KERNEL_YSYM)")
     ap.add_argument("--problems", type=int, default=4096, help="c4 batch size")
-    ap.add_argument("--precision", default="f32", choices=["f32", "split_bf16", "split_f16", "bf16"],
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "split_bf16", "split_f16", "bf16"],
                     help="c2: arithmetic of the angular DFT (tensor cores for split_bf16 / split_f16 / bf16)")
     return ap.parse_args()
 
@@ -259,6 +259,8 @@ def main():
     L = N * N * M
 
     F, P = workload_inputs(N, M, B, rank)
+    if args.precision == "f64":   # the paper's arithmetic, for context
+        F, P = F.astype(np.float64), P.astype(np.float64)
     plan = se2.Plan(N, M, batch=B, precision=args.precision, device=local,
                     flags=se2.HOST_STAGING | (se2.KERNEL_YSYM if args.ysym else 0))
     f = torch.from_numpy(F).to(dev)
@@ -338,7 +340,7 @@ def main():
     # end to end through the public API with host buffers (se2_convolve_host):
     # pinned host f -> device, convolve, device -> host out, overlapped by groups
     hf = torch.from_numpy(F).pin_memory()
-    hout = torch.empty(F.shape, dtype=torch.float32).pin_memory()
+    hout = torch.empty(F.shape, dtype=torch.float64 if args.precision == "f64" else torch.float32).pin_memory()
     for _ in range(2):
         se2.convolve_host(plan, hf, C, out=hout)
     barrier()
@@ -395,7 +397,8 @@ def main():
 
     hbm, src = peaks()
     c_rows = N // 2 + 1 if args.ysym else N                        # kernel-spectrum rows read per problem
-    alg_bytes = B * (4 * L + 4 * L + 8 * M * c_rows * (N // 2 + 1))   # read f, write out, read the spectrum
+    re = 8 if args.precision == "f64" else 4                          # bytes per real value
+    alg_bytes = B * (2 * re * L + 2 * re * M * c_rows * (N // 2 + 1))  # read f, write out, read the spectrum
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
 
     line = None
@@ -405,7 +408,8 @@ def main():
             "metric": METRIC_C2,
             "value": value, "unit": "conv/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "f32" else f"f32 storage, {args.precision} tensor-core angular DFT",
+            "dtype": args.precision if args.precision in ("f32", "f64") else
+                     f"f32 storage, {args.precision} tensor-core angular DFT",
             "data": "synthetic",
             "config": {**c2_config(N, M, B, world),
                        "l2": f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB moved per step)"},
@@ -486,7 +490,8 @@ def mixed_vs_fp32(se2, torch, dev, stream, N, M, B, F, P, f, f32_value, f32_out0
 # flushes the caches before each kernel, so the scratch that the live run keeps
 # in L2 is counted as DRAM traffic: an upper bound.  None where the kernel has
 # changed since the capture.
-NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.602304 + 0.463360) * 1e6, None, (37.777408 + 1.117184) * 1e6)}
+NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.602304 + 0.463360) * 1e6, (71.602688 + 1.382656) * 1e6,
+                                             (37.777408 + 1.117184) * 1e6)}
 NCU_TRAFFIC_PER_CONV = {k: (None if any(x is None for x in v) else sum(v) / 2) for k, v in NCU_TRAFFIC_PER_LAUNCH.items()}
 UNIT_NAMES = ("kf_fwd_xt", "kf_lines", "kf_inv_tx")
 

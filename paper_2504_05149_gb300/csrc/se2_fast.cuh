@@ -475,25 +475,6 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
             im[jj] = pf(v.z, v.w);
         }
     }
-    // ask L2 for this lane's coefficient rows now, so that the product after
-    // the forward FFT finds them there
-    if constexpr (MODE == FL_CONV || MODE == FL_ACC || MODE == FL_ADJ) {
-        if (act && t < R1) {
-            const int kxa = u < Q ? u : N / 2;
-            const int i0 = MODE == FL_ACC ? a.p - 1 : 0, i1 = MODE == FL_ACC ? a.p : (a.k < 2 ? a.k : 2);
-            for (int i = i0; i < i1; ++i) {
-                const float2* cb = a.C[i] + (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa + (size_t)t * CP;
-#pragma unroll
-                for (int kk = 0; kk < R2; ++kk) {
-                    int row = t + R1 * kk;   // folded like the loads below
-                    if (a.ymirror && row > N / 2) row = N - row;
-                    const float2* r = cb + (size_t)(row - t) * CP;
-                    asm volatile("prefetch.global.L2 [%0];" :: "l"(r));
-                    if (u < Q) asm volatile("prefetch.global.L2 [%0];" :: "l"(r + Q));
-                }
-            }
-        }
-    }
     // table fills and the scale overlap the loads
     fill_tw4<R1, R2>(TWF, a.twN);
     fill_tw4<R2, R1>(TWI, a.twN);

@@ -16,7 +16,7 @@ def test_kernel_roofline_picks_the_dominant_unit_and_counts_algorithmic_bytes():
     assert r["avg_launch_ms"] == pytest.approx(0.032)
     assert r["achieved"] == pytest.approx(r["alg_bytes_per_launch"] / 0.032e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6780.7)
-    assert r["traffic"] is None          # kf_lines has changed since its ncu capture
+    assert r["traffic"] == pytest.approx((71.602688 + 1.382656) * 1e6)
     assert [k["kernel"] for k in r["kernels"]] == ["kf_fwd_xt", "kf_lines", "kf_inv_tx"]
     assert r["kernels"][0]["alg_bytes_per_launch"] == 2 * 4 * L
     assert r["step"]["achieved"] == 2100.0
