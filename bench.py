@@ -493,6 +493,11 @@ def mixed_vs_fp32(se2, torch, dev, stream, N, M, B, F, P, f, f32_value, f32_out0
 NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.602304 + 0.463360) * 1e6, (71.602688 + 1.382656) * 1e6,
                                              (37.777408 + 1.117184) * 1e6)}
 NCU_TRAFFIC_PER_CONV = {k: (None if any(x is None for x in v) else sum(v) / 2) for k, v in NCU_TRAFFIC_PER_LAUNCH.items()}
+# The same counters with the cache left warm (`ncu --cache-control none`, one
+# pass, launches 49-72 of a batch-16 bench run; profiles/kf_units_*_warm_*):
+# the scratch stays in L2 as in the live run, so this is the live-like figure.
+NCU_TRAFFIC_WARM_PER_LAUNCH = {(256, 64, "f32"): ((33.787168 + 27.261472) * 1e6, (36.289920 + 6.271296) * 1e6,
+                                                  (0.024800 + 30.836576) * 1e6)}
 UNIT_NAMES = ("kf_fwd_xt", "kf_lines", "kf_inv_tx")
 
 
@@ -532,12 +537,18 @@ def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_by
     dom = max(kern, key=lambda d: d["total_ms"])
     tr = NCU_TRAFFIC_PER_LAUNCH.get((N, M, precision))
     ti = UNIT_NAMES.index(dom["kernel"])
-    traffic = tr[ti] if (tr is not None and abs(dom["problems_per_launch"] - 2) < 1e-9 and c_rows in (None, N)) else None
+    same = abs(dom["problems_per_launch"] - 2) < 1e-9 and c_rows in (None, N)
+    traffic = tr[ti] if (tr is not None and same) else None
+    tw = NCU_TRAFFIC_WARM_PER_LAUNCH.get((N, M, precision))
+    warm = tw[ti] if (tw is not None and same) else None
     return {"bound": "hbm", "achieved": dom["achieved"], "peak": hbm, "unit": "GB/s", "frac": dom["frac"],
             "peak_source": src, "kernel": dom["kernel"], "avg_launch_ms": dom["avg_launch_ms"],
             "alg_bytes_per_launch": dom["alg_bytes_per_launch"], "traffic": traffic,
             "traffic_source": "ncu --set full, caches flushed (upper bound), per launch of 2 problems; "
                               "profiles/kf_units_f32_256x256x64_b4_full.md",
+            "traffic_warm_cache": warm,
+            "traffic_warm_cache_source": "ncu --cache-control none (L2 as the previous launch left it), per launch of "
+                                         "2 problems; profiles/kf_units_f32_256x256x64_b16_warm_l2_traffic.md",
             "timing": "CUDA events around each launch, serialised pass (one stream, 2 problems per launch, "
                       "no other kernel running); the pipelined step is roofline.step",
             "kernels": kern, "kernels_overlapped": over, "step": step}
@@ -547,9 +558,13 @@ def traffic_fields(N, M, precision):
     t = NCU_TRAFFIC_PER_CONV.get((N, M, precision))
     if t is None:
         return {"traffic": None}
+    tw = NCU_TRAFFIC_WARM_PER_LAUNCH.get((N, M, precision))
     return {"traffic": t, "traffic_unit": "bytes per convolution",
             "traffic_source": "ncu --set full, caches flushed per kernel (upper bound); "
-                              "profiles/kf_units_f32_256x256x64_b4_full.md"}
+                              "profiles/kf_units_f32_256x256x64_b4_full.md",
+            "traffic_warm_cache": None if tw is None else sum(tw) / 2,
+            "traffic_warm_cache_source": "ncu --cache-control none; "
+                                         "profiles/kf_units_f32_256x256x64_b16_warm_l2_traffic.md"}
 
 
 def _clock_and_time(fn, steps, warmup, dev, settle=0.6, plans=()):

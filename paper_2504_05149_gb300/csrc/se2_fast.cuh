@@ -259,6 +259,7 @@ struct FArgs {
     float4* sout;
     int p;                       // 1-based index of C_p in C[] (chain step)
     int* err;                    // plan's device error word (bounded waits of the bulk-copy units)
+    int discard;                 // 1: unit C drops the scratch rows it has read from L2 (no write-back)
 };
 
 // y-pass modes: the convolution / chain product, the separable product, the
@@ -638,6 +639,24 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     }
 }
 
+// Unit C is the last reader of a y row's scratch rows (m, j): once the block
+// holds them in shared memory they can be dropped from L2 without being
+// written back (discard.global.L2; the slot is rewritten by a later unit A
+// before it is read again), so that dead scratch costs no DRAM writes (opt-in,
+// FArgs::discard).  Rows are ftp4<N>() float4 = a whole number of 128-byte
+// lines, 128-byte aligned.
+template <int N, int M>
+__device__ __forceinline__ void discard_scratch_rows(const float4* row0) {
+    constexpr int TP4 = ftp4<N>();
+    constexpr int LPR = TP4 * 16 / 128;
+    static_assert(TP4 * 16 % 128 == 0, "scratch rows are whole 128-byte lines");
+    const char* base = reinterpret_cast<const char*>(row0);
+    for (int i = threadIdx.x; i < M * LPR; i += blockDim.x) {
+        const int r = i / LPR, l = i - (i / LPR) * LPR;
+        asm volatile("discard.global.L2 [%0], 128;" :: "l"(base + ((size_t)r * N * TP4) * 16 + l * 128) : "memory");
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Unit C: paired inverse angular FFT of the slab columns (DC and Nyquist
 // columns recombined into one complex column first), then the inverse x FFTs
@@ -685,6 +704,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
         }
     }
     __syncthreads();
+    if (a.discard) discard_scratch_rows<N, M>(a.s + (size_t)b * a.s_pstride + (size_t)j * TP4);
     if (tid < M) {   // DC column + i * Nyquist column
         float4 e = S[frow(tid, P)];
         const float4 ny = S[frow(tid, P) + Q];

@@ -17,6 +17,9 @@ def test_kernel_roofline_picks_the_dominant_unit_and_counts_algorithmic_bytes():
     assert r["achieved"] == pytest.approx(r["alg_bytes_per_launch"] / 0.032e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6780.7)
     assert r["traffic"] == pytest.approx((71.602688 + 1.382656) * 1e6)
+    assert r["traffic_warm_cache"] == pytest.approx((36.289920 + 6.271296) * 1e6)
+    # warm-cache traffic of the whole step: 1.33x the algorithmic 12 bytes per point
+    assert r["step"]["traffic_warm_cache"] / (12 * L) == pytest.approx(1.33, abs=0.01)
     assert [k["kernel"] for k in r["kernels"]] == ["kf_fwd_xt", "kf_lines", "kf_inv_tx"]
     assert r["kernels"][0]["alg_bytes_per_launch"] == 2 * 4 * L
     assert r["step"]["achieved"] == 2100.0
@@ -29,7 +32,7 @@ def test_kernel_roofline_half_rows_and_other_group_sizes_drop_the_ncu_traffic():
     assert r["traffic"] is None
     stats = [(1.0, 24), (2.0, 24), (1.0, 24)]          # 2 problems per launch, half the C rows
     r = bench.kernel_roofline(stats, N, M, B, steps, 6780.7, "measured", 1.0, 1.0, "f32", c_rows=N // 2 + 1)
-    assert r["traffic"] is None
+    assert r["traffic"] is None and r["traffic_warm_cache"] is None
     assert r["alg_bytes_per_launch"] == 2 * 8 * M * (N // 2 + 1) * (N // 2 + 1)
 
 

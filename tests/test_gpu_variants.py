@@ -3,6 +3,9 @@
 * SE2_FAST2=1: units A and C with bulk row copies and the real-FFT split in
   registers (N = 256 or 64).
 * SE2_FLOW=1: the whole batch as one persistent dataflow launch (N = 256).
+* SE2_L2_DISCARD=1: unit C drops the scratch rows it has consumed from L2;
+  the scratch slots are rewritten before any later read, so repeated calls,
+  the pipelined schedule and the chain outputs are unchanged.
 
 Both perform the same floating-point operations in the same order as the
 default units, so the outputs are identical; the default path itself is
@@ -125,3 +128,41 @@ def test_dataflow_kernel_against_oracle(se2):
         want = O.convolve_chain(F[b].astype(np.float64), [P[b].astype(np.float64) for P in Ps])
         err = np.max(np.abs(got[b] - want)) / np.max(np.abs(want))
         assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("N,M,B,k,normalize", [(256, 64, 6, 1, False), (256, 32, 5, 3, True), (64, 32, 9, 2, False)])
+def test_l2_discard_matches_default(se2, N, M, B, k, normalize):
+    F, Ps = _inputs(N, M, B, k, 35)
+    ref, _ = _convolve(se2, {}, F, Ps, normalize)
+    for _ in range(2):   # the second call reuses scratch slots whose lines were discarded
+        got, _ = _convolve(se2, {"SE2_L2_DISCARD": "1"}, F, Ps, normalize)
+        assert np.array_equal(got, ref)
+
+
+def test_l2_discard_chain_all_and_backward(se2):
+    """Every chain prefix (unit C after each running product) and the input
+    gradient (unit C after the adjoint lines) with discarding on."""
+    N, M, B, k = 64, 16, 3, 3
+    F, Ps = _inputs(N, M, B, k, 36)
+    outs = {}
+    for env in ({}, {"SE2_L2_DISCARD": "1"}):
+        old = {key: os.environ.get(key) for key in env}
+        os.environ.update(env)
+        try:
+            plan = se2.Plan(N, M, batch=B)
+        finally:
+            for key, v in old.items():
+                if v is None:
+                    os.environ.pop(key, None)
+                else:
+                    os.environ[key] = v
+        f = torch.from_numpy(F).cuda()
+        Cs = [se2.coeffs(plan, torch.from_numpy(P).cuda())[0] for P in Ps]
+        allp = se2.convolve_chain_all(plan, f, Cs)
+        g = torch.from_numpy(F[::-1].copy()).cuda()
+        gf, _ = se2.backward(plan, g, Cs[0])
+        plan.status()
+        torch.cuda.synchronize()
+        outs[bool(env)] = (allp.cpu().numpy(), gf.cpu().numpy())
+    assert np.array_equal(outs[True][0], outs[False][0])
+    assert np.array_equal(outs[True][1], outs[False][1])

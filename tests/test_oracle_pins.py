@@ -354,3 +354,45 @@ def test_origin_conventions_differ_by_a_half_period_shift():
     for P in P0:
         seq = O.convolve(seq, P, origin_zero=True)
     assert np.max(np.abs(chain - seq)) < 1e-12 * np.max(np.abs(seq))
+
+
+def _rot90(F):
+    """Left translation by the rotation R_{pi/2} on Omega_L: f'(x, y, theta) =
+    f(y, -x, theta - pi/2).  The grid x_i = -1/2 + i/N is closed under
+    x -> -x (index i -> -i mod N), so this is an index map; theta shifts by M/4."""
+    M, N = F.shape[0], F.shape[-1]
+    Y, X = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    Fr = np.roll(F, M // 4, axis=0)
+    return Fr[:, (-X) % N, Y]
+
+
+@pytest.mark.parametrize("N,M", [(8, 4), (16, 8)])
+def test_convolution_commutes_with_rotation_and_translation(N, M):
+    """Theorem f*gP: for a kernel radial in translations the SE(2) convolution
+    commutes with left translations of f.  On the grid: a 90-degree rotation
+    (with theta shifted by M/4) and cyclic grid shifts commute with the
+    scheme; an anisotropic kernel breaks the rotation identity but not the
+    shifts (checked against the direct sum as well)."""
+    rng = np.random.default_rng(N + M)
+    F = rng.standard_normal((M, N, N))
+    P = synth.sample_kernel(N, M, synth.KernelParams(0.11, 0.5, 0.7))
+    out = O.convolve(F, P)
+    assert np.max(np.abs(O.convolve(_rot90(F), P) - _rot90(out))) < 1e-12 * np.max(np.abs(out))
+    sh = (1, 3, N - 2)
+    assert np.max(np.abs(O.convolve(np.roll(F, sh, axis=(0, 1, 2)), P) - np.roll(out, sh, axis=(0, 1, 2)))) < 1e-12
+    assert np.max(np.abs(direct.direct_conv(F, P) - out)) < 1e-12 * np.max(np.abs(out))
+    # an anisotropic kernel: x and y widths differ
+    Pa = P * np.exp(-4.0 * ((np.arange(N) - N / 2) / N) ** 2)[None, None, :]
+    outa = O.convolve(F, Pa)
+    assert np.max(np.abs(O.convolve(_rot90(F), Pa) - _rot90(outa))) > 1e-3 * np.max(np.abs(outa))
+    assert np.max(np.abs(O.convolve(np.roll(F, sh, axis=(0, 1, 2)), Pa) - np.roll(outa, sh, axis=(0, 1, 2)))) < 1e-12
+
+
+def test_convolution_is_linear_in_f():
+    N, M = 16, 8
+    rng = np.random.default_rng(5)
+    F1, F2 = rng.standard_normal((2, M, N, N))
+    P = synth.sample_kernel(N, M, synth.KernelParams(0.05, 0.3))
+    lhs = O.convolve(2.5 * F1 - 0.75 * F2, P)
+    rhs = 2.5 * O.convolve(F1, P) - 0.75 * O.convolve(F2, P)
+    assert np.max(np.abs(lhs - rhs)) < 1e-13 * np.max(np.abs(rhs))
