@@ -743,6 +743,7 @@ def run_batch(args):
         runner.set_chain(i, [(kp.sigma, kp.sigma_theta, kp.nu) for kp in chains[i]])
     runner.build_tables()
     runner.tune()
+    lanes, lane_of, lane_ms = runner.lanes()
     runner.capture()
     ms, clocks, _ = _clock_and_time(runner.replay, args.steps, args.warmup, dev)
     pts = runner.points()
@@ -752,9 +753,10 @@ def run_batch(args):
     _line("SE(2) convolutions/s, 4096 uneven problems with separable kernel chains (FP32)",
           args.problems * args.steps / (ms / 1e3), "conv/s", args, ms,
           {"workload": "4096 problems, N~U{32,64,128,256}, M~U{16,32,64}, chains k~U{1..16}, 3..16 bumps; "
-                       "per-size-class plans on forked streams in one CUDA graph", "points_per_step": pts,
+                       "per-size-class plans on tuned stream lanes in one CUDA graph", "points_per_step": pts,
            "classes": {f"{N}x{M}": [len(v), runner.config[(N, M)][0], runner.config[(N, M)][1]]
-                       for (N, M), v in runner.classes.items()}},
+                       for (N, M), v in runner.classes.items()},
+           "lanes": lanes, "tuned_ms_by_lanes": {str(L): round(v, 4) for L, v in lane_ms.items()}},
           {"points_per_s": pts * args.steps / (ms / 1e3),
            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "traffic": None, "peak_source": src, "alg_bytes_per_step": alg},

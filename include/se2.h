@@ -302,16 +302,27 @@ se2_status se2_convolve_separable(se2_plan_t plan, const void* f, int B, const v
  *   tables  device, the packed tables (written)
  * se2_batch_convolve_separable -- the convolution of every problem: f and out
  * the packed grids (device, must not overlap), tables the packed tables.
- * The classes run concurrently on streams forked from `stream` and joined back
- * into it (events only), so the call can be captured in a CUDA graph.
+ * The classes run on `lanes` stream lanes: lane 0 is `stream`, the others
+ * are plan-owned streams forked from it and joined back into it (events
+ * only), so the call can be captured in a CUDA graph.  A new plan has one
+ * lane (the classes one after another).
  *
  * se2_batch_tune -- the autotuner: for each class, time the candidate
  * schedules (`reps` calls each, on the given data, on `stream`) and keep the
  * fastest: FP32 fast path with pipeline depth 1 or depth 2 with groups of
- * 1, 2, 4, .. 64 problems, or the persistent dataflow kernel.  Synchronous;
- * not for stream capture.  se2_batch_plan_config reports per class (host
- * arrays of n_classes, each may be NULL): shape, count, pipeline depth (0 for
- * the persistent kernel), group, persistent (0/1) and the tuned ms per call.
+ * 1, 2, 4, .. 64 problems, or the persistent dataflow kernel.  Then time the
+ * whole batch on 1, 2, 3, 4 and n_classes lanes and keep the fastest.
+ * Synchronous; not for stream capture.  se2_batch_plan_config reports per
+ * class (host arrays of n_classes, each may be NULL): shape, count, pipeline
+ * depth (0 for the persistent kernel), group, persistent (0/1) and the tuned
+ * ms per call.
+ *
+ * se2_batch_plan_lanes -- set the number of lanes (lanes >= 1, clamped to
+ * n_classes; classes are assigned longest first to the least-loaded lane,
+ * by tuned ms once tuned, by grid points before) or, with lanes <= 0, leave
+ * it.  Returns, each output may be NULL: *current, the lanes in force;
+ * lane_of_class[n_classes]; lane_ms[n_classes], entry L - 1 the tuner's
+ * whole-batch ms on L lanes (0 where not timed).  Host only.
  * se2_batch_plan_launches: kernels launched through the plan so far.
  */
 typedef struct { int N, M; } se2_shape;
@@ -327,6 +338,7 @@ se2_status se2_batch_convolve_separable(se2_batch_plan_t plan, const void* f, co
 se2_status se2_batch_tune(se2_batch_plan_t plan, const void* f, const void* tables, void* out, int reps, void* stream);
 se2_status se2_batch_plan_config(se2_batch_plan_t plan, int* n_classes, se2_shape* shape, int* count, int* depth,
                                  int* group, int* persistent, double* tuned_ms);
+se2_status se2_batch_plan_lanes(se2_batch_plan_t plan, int lanes, int* current, int* lane_of_class, double* lane_ms);
 unsigned long long se2_batch_plan_launches(se2_batch_plan_t plan);
 
 /*

@@ -2,11 +2,12 @@
 on the library's batch plan (se2_batch_plan_*).
 
 The C runtime groups the problems into size classes (equal grid N x N x M),
-gives each class its own plan, runs the classes concurrently on forked
-streams (one `se2_batch_convolve_separable` call, capturable in a CUDA
-graph) and tunes, per class, the schedule of its launches (pipeline depth and
-group size of the FP32 fast path, or the persistent dataflow kernel) by
-timing the candidates on the class's own data (`se2_batch_tune`).  Each
+gives each class its own plan, runs the classes on one or more stream lanes
+forked from the caller's (one `se2_batch_convolve_separable` call,
+capturable in a CUDA graph) and tunes, per class, the schedule of its
+launches (pipeline depth and group size of the FP32 fast path, or the
+persistent dataflow kernel) by timing the candidates on the class's own
+data, then the number of lanes for the whole batch (`se2_batch_tune`).  Each
 problem carries a chain of separable radial kernels (Gaussian x wrapped
 normal), whose product is kept in factored form (three 1-D tables per
 problem).  This module only holds the packed tensors and marshals calls.
@@ -47,10 +48,11 @@ def _bind(lib):
     lib.se2_batch_plan_config.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(_Shape), ctypes.POINTER(ip),
                                           ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip),
                                           ctypes.POINTER(ctypes.c_double)]
+    lib.se2_batch_plan_lanes.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_double)]
     lib.se2_batch_plan_launches.argtypes = [vp]
     lib.se2_batch_plan_launches.restype = ctypes.c_ulonglong
     for name in ("se2_batch_plan_create", "se2_batch_plan_destroy", "se2_batch_plan_layout", "se2_batch_separable_tables",
-                 "se2_batch_convolve_separable", "se2_batch_tune", "se2_batch_plan_config"):
+                 "se2_batch_convolve_separable", "se2_batch_tune", "se2_batch_plan_config", "se2_batch_plan_lanes"):
         getattr(lib, name).restype = ctypes.c_int
     lib._se2_batch_bound = True
     return lib
@@ -167,6 +169,8 @@ class BatchRunner:
             path = "persistent" if pers else ("pipelined" if depth > 1 else "three")
             self.config[c] = (path, group)
             record[f"{gpu}|N={c[0]}|M={c[1]}|n={n}|f32"] = [path, depth, group, ms]
+        lanes, _, lane_ms = self.lanes()
+        record[f"{gpu}|batch|classes={len(self.order)}|n={len(self.shapes)}|f32"] = ["lanes", lanes, lane_ms]
         try:
             os.makedirs(os.path.dirname(self.cache_path) or ".", exist_ok=True)
             old = {}
@@ -178,6 +182,17 @@ class BatchRunner:
                 json.dump(old, fh, indent=1, sort_keys=True)
         except Exception:
             pass
+
+    def lanes(self, n: Optional[int] = None):
+        """Set the number of stream lanes (n >= 1) or leave it (None); returns
+        (lanes in force, lane of each class in plan order, {L: tuned
+        whole-batch ms on L lanes})."""
+        m = len(self.order)
+        cur = ctypes.c_int()
+        lane = (ctypes.c_int * m)()
+        ms = (ctypes.c_double * m)()
+        _check(self.lib.se2_batch_plan_lanes(self._h, int(n) if n else 0, ctypes.byref(cur), lane, ms))
+        return cur.value, list(lane), {L + 1: ms[L] for L in range(m) if ms[L] > 0}
 
     # -- execution --------------------------------------------------------------
     def run(self):

@@ -584,13 +584,13 @@ void launch_unit_a(const FastTable& ft, int N, int nb, cudaStream_t s, const FAr
     if (ft.fwd2 != nullptr && aligned(a.f, 16))
         ft.fwd2<<<dim3(N, nb), kThreads, ft.smem_xt2, s>>>(a);
     else
-        ft.fwd<<<dim3(N, nb), kThreads, ft.smem_xt, s>>>(a);
+        ft.fwd<<<dim3(N / ft.yr, nb), kThreads, ft.smem_xt, s>>>(a);
 }
 void launch_unit_c(const FastTable& ft, int N, int nb, cudaStream_t s, const FArgs& a) {
     if (ft.inv2 != nullptr && aligned(a.out, 16))
         ft.inv2<<<dim3(N, nb), kThreads, ft.smem_xt2, s>>>(a);
     else
-        ft.inv<<<dim3(N, nb), kThreads, ft.smem_xt, s>>>(a);
+        ft.inv<<<dim3(N / ft.yr, nb), kThreads, ft.smem_xt, s>>>(a);
 }
 
 // SE2_CHECK_FINITE: one pass over an output; the first NaN or infinity sets
@@ -1541,6 +1541,7 @@ struct se2_batch_plan_s {
         cudaStream_t st = nullptr;                // own stream (class 0 uses the caller's)
         cudaEvent_t done = nullptr;
         double tuned_ms = 0;
+        int lane = 0;                             // stream lane it runs on (0: the caller's stream)
     };
     int n = 0, dev = 0;
     se2_precision prec = SE2_F32;
@@ -1550,6 +1551,8 @@ struct se2_batch_plan_s {
     std::vector<long long> goff, toff;            // per problem: packed grid / table offset
     long long gtotal = 0, ttotal = 0;
     cudaEvent_t fork = nullptr;
+    int lanes = 1;                                // concurrent stream lanes (1: classes one after another)
+    std::vector<double> lane_ms;                  // tuned whole-batch ms per lane count (index = lanes)
 };
 
 namespace {
@@ -1583,11 +1586,58 @@ se2_status batch_check(se2_batch_plan_s* b) {
     return SE2_OK;
 }
 
+// Spread the classes over `lanes` stream lanes: longest first, each to the
+// lane with the least work so far (tuned ms once tuned, grid points before).
+// Lane l > 0 runs on the stream of class l.
+void batch_assign_lanes(se2_batch_plan_s* b, int lanes) {
+    const int nc = (int)b->cls.size();
+    lanes = lanes < 1 ? 1 : (lanes > nc ? nc : lanes);
+    b->lanes = lanes;
+    auto weight = [&](const se2_batch_plan_s::Class& c) {
+        return c.tuned_ms > 0 ? c.tuned_ms : (double)c.N * c.N * c.M * c.count;
+    };
+    std::vector<int> order(nc);
+    for (int i = 0; i < nc; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return weight(b->cls[a]) > weight(b->cls[c]); });
+    std::vector<double> load(lanes, 0.0);
+    for (int i : order) {
+        int l = 0;
+        for (int q = 1; q < lanes; ++q)
+            if (load[q] < load[l]) l = q;
+        b->cls[i].lane = l;
+        load[l] += weight(b->cls[i]);
+    }
+}
+
 // One class's convolutions on stream s with its current sub-plan.
 se2_status batch_run_class(se2_batch_plan_s* b, se2_batch_plan_s::Class& c, const unsigned char* f, const unsigned char* tab,
                            unsigned char* out, cudaStream_t s) {
     const size_t re = b->prec == SE2_F64 ? sizeof(double) : sizeof(float);
     return se2_convolve_separable(c.plan, f + c.goff * re, c.count, tab + c.toff * 2 * re, out + c.goff * re, s);
+}
+
+// Every class, on its lane: lane 0 is the caller's stream, lanes 1.. are
+// class streams forked from it and joined back (events only: capturable).
+// Inside a lane the classes run in class order.
+se2_status batch_run(se2_batch_plan_s* b, const unsigned char* f, const unsigned char* tab, unsigned char* out,
+                     cudaStream_t s) {
+    const int L = b->lanes;
+    cudaError_t e = cudaSuccess;
+    if (L > 1) {
+        e = cudaEventRecord(b->fork, s);
+        for (int l = 1; l < L && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->cls[l].st, b->fork, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "class fork");
+    }
+    for (auto& c : b->cls) {
+        se2_status st = batch_run_class(b, c, f, tab, out, c.lane == 0 ? s : b->cls[c.lane].st);
+        if (st != SE2_OK) return st;
+    }
+    for (int l = 1; l < L && e == cudaSuccess; ++l) {
+        e = cudaEventRecord(b->cls[l].done, b->cls[l].st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->cls[l].done, 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "class join");
+    return SE2_OK;
 }
 
 }  // namespace
@@ -1666,6 +1716,7 @@ se2_status se2_batch_plan_create(se2_batch_plan_t* out, const se2_shape* shapes,
         }
         if (st != SE2_OK) { batch_free(b); return st; }
     }
+    batch_assign_lanes(b, 1);
     *out = b;
     return SE2_OK;
 }
@@ -1725,29 +1776,15 @@ se2_status se2_batch_convolve_separable(se2_batch_plan_t b, const void* f, const
     const auto* fb = static_cast<const unsigned char*>(f);
     const auto* tb = static_cast<const unsigned char*>(tables);
     auto* ob = static_cast<unsigned char*>(out);
-    // the classes run concurrently: class 0 on the caller's stream, the others
-    // on their own streams forked from it and joined back (capturable)
-    cudaError_t e = cudaEventRecord(b->fork, s);
-    for (size_t ci = 1; ci < b->cls.size() && e == cudaSuccess; ++ci) e = cudaStreamWaitEvent(b->cls[ci].st, b->fork, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "class fork");
-    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
-        auto& c = b->cls[ci];
-        st = batch_run_class(b, c, fb, tb, ob, ci == 0 ? s : c.st);
-        if (st != SE2_OK) return st;
-    }
-    for (size_t ci = 1; ci < b->cls.size() && e == cudaSuccess; ++ci) {
-        e = cudaEventRecord(b->cls[ci].done, b->cls[ci].st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->cls[ci].done, 0);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "class join");
-    return SE2_OK;
+    return batch_run(b, fb, tb, ob, s);
 }
 
 // The autotuner: per class, time the candidate schedules on the caller's data
 // and keep the fastest.  Candidates: the FP32 fast path with pipeline depth 1
 // (groups of the scratch size) or depth 2 with groups of 1, 2, 4, 8 .. 64
 // problems (as the scratch allows), and the persistent dataflow kernel
-// (SE2_PERSISTENT).  Synchronous; not for stream capture.
+// (SE2_PERSISTENT).  Then the number of stream lanes for the whole batch.
+// Synchronous; not for stream capture.
 se2_status se2_batch_tune(se2_batch_plan_t b, const void* f, const void* tables, void* out, int reps, void* stream) {
     SE2_RANGE("se2_batch_tune");
     se2_status st = batch_check(b);
@@ -1830,9 +1867,50 @@ se2_status se2_batch_tune(se2_batch_plan_t b, const void* f, const void* tables,
             c.alt = nullptr;
         }
     }
+    // then the concurrency of the classes: the whole batch with 1, 2, 3, 4 ..
+    // and all lanes; concurrent classes compete for L2, where each pipeline
+    // keeps its scratch, so more lanes is not always faster
+    const int nc = (int)b->cls.size();
+    b->lane_ms.assign(nc + 1, 0.0);
+    if (st == SE2_OK) {
+        int best_l = 1;
+        double best_ms = 0;
+        for (int L = 1; L <= nc && st == SE2_OK; L = (L < 4 || L == nc) ? L + 1 : nc) {
+            batch_assign_lanes(b, L);
+            st = batch_run(b, fb, tb, ob, s);   // warm-up
+            cudaEventRecord(e0, s);
+            for (int i = 0; i < reps && st == SE2_OK; ++i) st = batch_run(b, fb, tb, ob, s);
+            cudaEventRecord(e1, s);
+            if (st != SE2_OK) break;
+            float ms = 0.f;
+            e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) { st = cuda_fail(e, "tuning events"); break; }
+            b->lane_ms[L] = ms / reps;
+            if (L == 1 || b->lane_ms[L] < best_ms) {
+                best_ms = b->lane_ms[L];
+                best_l = L;
+            }
+            if (L == nc) break;
+        }
+        batch_assign_lanes(b, best_l);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+se2_status se2_batch_plan_lanes(se2_batch_plan_t b, int lanes, int* current, int* lane_of_class, double* lane_ms) {
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    if (lanes > 0) batch_assign_lanes(b, lanes);
+    if (current) *current = b->lanes;
+    const int nc = (int)b->cls.size();
+    for (int ci = 0; ci < nc; ++ci) {
+        if (lane_of_class) lane_of_class[ci] = b->cls[ci].lane;
+        if (lane_ms) lane_ms[ci] = (size_t)(ci + 1) < b->lane_ms.size() ? b->lane_ms[ci + 1] : 0.0;
+    }
+    return SE2_OK;
 }
 
 se2_status se2_batch_plan_config(se2_batch_plan_t b, int* n_classes, se2_shape* shape, int* count, int* depth,

@@ -23,6 +23,7 @@ bool fill_fast_nm(FastTable* t) {
         t->smem_xt = sx;
         t->smem_y = sy;
         t->lines_per_block = fast_lines<N>();
+        t->yr = fast_yr<N, M>();
         if constexpr (fast2_ok<N>()) {
             constexpr size_t s2 = fast2_smem<N, M>();
             if constexpr (s2 <= kMaxDynSmem) {

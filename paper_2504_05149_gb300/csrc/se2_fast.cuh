@@ -293,6 +293,15 @@ __device__ __forceinline__ void angular_twiddles(const float2* twM, int lm, floa
     }
 }
 
+// y rows per block of units A and C.  One y row gives M / 4 x jobs (four
+// theta rows each) and N / 4 angular columns; at small M that leaves most
+// teams idle, so a block takes YR consecutive y rows, enough that every x
+// team has a job (YR * M / 4 >= teams), and its slab holds YR * M rows.
+template <int N, int M> __host__ __device__ constexpr int fast_yr() {
+    constexpr int want = (kThreads / team_size<N>()) * 4 / M;
+    return want < 1 ? 1 : (want > 8 ? 8 : want);
+}
+
 // ---------------------------------------------------------------------------
 // Unit A: forward real x FFT of the M theta rows of y row j (rows 4q, 4q+1
 // packed as one complex line, rows 4q+2, 4q+3 as the other half), the split
@@ -301,28 +310,30 @@ __device__ __forceinline__ void angular_twiddles(const float2* twM, int lm, floa
 // ---------------------------------------------------------------------------
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
+    constexpr int YR = fast_yr<N, M>(), MR = YR * M;   // slab rows: YR y rows of M theta rows
     constexpr int Q = N / 4, P = fpitch<N>(), TP4 = ftp4<N>();
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
-    constexpr int TEAMS = kThreads / TS, JOBS = M / 4;
+    constexpr int TEAMS = kThreads / TS, JOBS = MR / 4, JY = M / 4;
     constexpr int QK = Q / R1;            // register distance between x bins u and u + Q
     constexpr int HK = N / (2 * R1);      // register of bin N/2 on lane 0
     constexpr size_t NN = (size_t)N * N;
     static_assert(Q % R1 == 0 && Q % R2 == 0, "pairing needs N/4 divisible by the radices");
+    static_assert(M % 8 == 0 && MR <= kThreads && N % YR == 0, "slab of whole y rows");
     extern __shared__ float4 fsm[];
     float4* S = fsm;
-    float4* TW = fsm + fslab4<N, M>();
+    float4* TW = fsm + fslab4<N, MR>();
     float2* TWM = reinterpret_cast<float2*>(TW + N);
-    const int tid = threadIdx.x, j = blockIdx.x, b = blockIdx.y;
-    const float* fb = a.f + (size_t)b * NN * M + (size_t)j * N;
+    const int tid = threadIdx.x, j0 = blockIdx.x * YR, b = blockIdx.y;
+    const float* fb = a.f + (size_t)b * NN * M + (size_t)j0 * N;
     const int team = tid / TS, lane = tid % TS;
     for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
-        const int q = q0 + team;
+        const int q = q0 + team;            // slab rows 4q .. 4q + 3: y row q / JY, theta rows 4 (q % JY) ..
         const bool act = q < JOBS;
         float2 re[RM], im[RM];
 #pragma unroll
         for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
         if (act && lane < R2) {
-            const float* r0 = fb + (size_t)(4 * q) * NN;
+            const float* r0 = fb + (size_t)(q / JY) * N + (size_t)(4 * (q % JY)) * NN;
 #pragma unroll
             for (int jj = 0; jj < R1; ++jj) {
                 const int x = lane + R2 * jj;
@@ -387,22 +398,22 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
         const int tm = tid / TSM, lm = tid % TSM;
         float2 wr[Fac<M>::R1], wi[Fac<M>::R1];
         angular_twiddles<M>(TWM, lm, wr, wi);
-        for (int c0 = 0; c0 < Q; c0 += TEAMSM) {
-            const int u = c0 + tm;
-            const bool act = u < Q;
-            column_fft2<M, P, -1>(S, act ? u : 0, lm, act, wr, wi, SyncWarp());
+        for (int c0 = 0; c0 < YR * Q; c0 += TEAMSM) {
+            const int c = c0 + tm;          // column u = c % Q of y row c / Q (M % 8 == 0: frow adds)
+            const bool act = c < YR * Q;
+            column_fft2<M, P, -1>(S + frow((act ? c / Q : 0) * M, P), act ? c % Q : 0, lm, act, wr, wi, SyncWarp());
         }
     }
     __syncthreads();
     // split the DC column's transform Y = F(X[.,0] + i X[.,N/2]) into the two
     // real columns' transforms: (Y + conj Y[-m]) / 2 and (Y - conj Y[-m]) / 2i
     float4 yv = make_float4(0.f, 0.f, 0.f, 0.f), ym = yv;
-    if (tid < M) {
+    if (tid < MR) {
         yv = S[frow(tid, P)];
-        ym = S[frow((M - tid) & (M - 1), P)];
+        ym = S[frow((tid & ~(M - 1)) + ((M - tid) & (M - 1)), P)];
     }
     __syncthreads();
-    if (tid < M) {
+    if (tid < MR) {
         float4 e = yv;
         e.x = 0.5f * (yv.x + ym.x);
         e.z = 0.5f * (yv.z - ym.z);
@@ -412,10 +423,10 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
     __syncthreads();
     {
         constexpr int E = Q + 1;
-        float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * TP4;
-        for (int e = tid; e < M * E; e += kThreads) {
-            const int r = e / E, u = e - r * E;
-            __stcg(sb + (size_t)r * N * TP4 + u, S[frow(r, P) + u]);
+        float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j0 * TP4;
+        for (int e = tid; e < MR * E; e += kThreads) {
+            const int r = e / E, u = e - r * E;      // slab row r: theta row r % M of y row j0 + r / M
+            __stcg(sb + (size_t)(r / M) * TP4 + (size_t)(r % M) * N * TP4 + u, S[frow(r, P) + u]);
         }
     }
 }
@@ -664,29 +675,31 @@ __device__ __forceinline__ void discard_scratch_rows(const float4* row0) {
 // ---------------------------------------------------------------------------
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
+    constexpr int YR = fast_yr<N, M>(), MR = YR * M;   // slab rows: YR y rows of M theta rows
     constexpr int Q = N / 4, P = fpitch<N>(), TP4 = ftp4<N>(), E = Q + 1;
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
-    constexpr int TEAMS = kThreads / TS, JOBS = M / 4;
+    constexpr int TEAMS = kThreads / TS, JOBS = MR / 4, JY = M / 4;
     constexpr int QJ = Q / R2, HJ = N / (2 * R2);
     constexpr size_t NN = (size_t)N * N;
-    constexpr int LOADS = (M * E + kThreads - 1) / kThreads;
+    constexpr int LOADS = (MR * E + kThreads - 1) / kThreads;
+    static_assert(M % 8 == 0 && MR <= kThreads && N % YR == 0, "slab of whole y rows");
     extern __shared__ float4 fsm[];
     float4* S = fsm;
-    float4* TW = fsm + fslab4<N, M>();
+    float4* TW = fsm + fslab4<N, MR>();
     float2* TWM = reinterpret_cast<float2*>(TW + N);
-    const int tid = threadIdx.x, j = blockIdx.x, b = blockIdx.y;
+    const int tid = threadIdx.x, j0 = blockIdx.x * YR, b = blockIdx.y;
     {
         // batches of at most ~20 loads in flight per thread (registers)
         constexpr int CH = LOADS <= 20 ? LOADS : (LOADS + 1) / 2;
-        const float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j * TP4;
+        const float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j0 * TP4;
         for (int i0 = 0; i0 < LOADS; i0 += CH) {
             float4 v[CH];
 #pragma unroll
             for (int i = 0; i < CH; ++i) {
                 const int e = tid + kThreads * (i0 + i);
-                if (i0 + i < LOADS && e < M * E) {
+                if (i0 + i < LOADS && e < MR * E) {
                     const int r = e / E, u = e - r * E;
-                    v[i] = __ldcg(sb + (size_t)r * N * TP4 + u);
+                    v[i] = __ldcg(sb + (size_t)(r / M) * TP4 + (size_t)(r % M) * N * TP4 + u);
                 }
             }
             if (i0 == 0) {   // the table fills overlap the loads
@@ -696,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
 #pragma unroll
             for (int i = 0; i < CH; ++i) {
                 const int e = tid + kThreads * (i0 + i);
-                if (i0 + i < LOADS && e < M * E) {
+                if (i0 + i < LOADS && e < MR * E) {
                     const int r = e / E, u = e - r * E;
                     S[frow(r, P) + u] = v[i];
                 }
@@ -704,8 +717,9 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
         }
     }
     __syncthreads();
-    if (a.discard) discard_scratch_rows<N, M>(a.s + (size_t)b * a.s_pstride + (size_t)j * TP4);
-    if (tid < M) {   // DC column + i * Nyquist column
+    if (a.discard)
+        for (int yr = 0; yr < YR; ++yr) discard_scratch_rows<N, M>(a.s + (size_t)b * a.s_pstride + (size_t)(j0 + yr) * TP4);
+    if (tid < MR) {   // DC column + i * Nyquist column
         float4 e = S[frow(tid, P)];
         const float4 ny = S[frow(tid, P) + Q];
         e.x -= ny.z;
@@ -718,17 +732,17 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
         const int tm = tid / TSM, lm = tid % TSM;
         float2 wr[Fac<M>::R1], wi[Fac<M>::R1];
         angular_twiddles<M>(TWM, lm, wr, wi);
-        for (int c0 = 0; c0 < Q; c0 += TEAMSM) {
-            const int u = c0 + tm;
-            const bool act = u < Q;
-            column_fft2<M, P, +1>(S, act ? u : 0, lm, act, wr, wi, SyncWarp());
+        for (int c0 = 0; c0 < YR * Q; c0 += TEAMSM) {
+            const int c = c0 + tm;          // column u = c % Q of y row c / Q
+            const bool act = c < YR * Q;
+            column_fft2<M, P, +1>(S + frow((act ? c / Q : 0) * M, P), act ? c % Q : 0, lm, act, wr, wi, SyncWarp());
         }
     }
     __syncthreads();
     // entry (m, 0) now holds (X_m[0], X_m[Q].re, X_m[N/2], X_m[Q].im) with
     // X_m[0], X_m[N/2] real
     const int team = tid / TS, lane = tid % TS;
-    float* ob = a.out + (size_t)b * NN * M + (size_t)j * N;
+    float* ob = a.out + (size_t)b * NN * M + (size_t)j0 * N;
     for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
         const int q = q0 + team;
         const bool act = q < JOBS;
@@ -774,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
         float4* xb = S + frow(4 * (act ? q : 0), P);
         team_fft2<R1, R2, +1>(re, im, lane, act, xb, TW, SyncWarp());
         if (act && lane < R1) {
-            float* o0 = ob + (size_t)(4 * q) * NN;
+            float* o0 = ob + (size_t)(q / JY) * N + (size_t)(4 * (q % JY)) * NN;
 #pragma unroll
             for (int k = 0; k < R2; ++k) {
                 const int x = lane + R1 * k;
@@ -787,7 +801,9 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
     }
 }
 
-template <int N, int M> constexpr size_t fast_xt_smem() { return (size_t)(fslab4<N, M>() + N + M / 2) * sizeof(float4); }
+template <int N, int M> constexpr size_t fast_xt_smem() {
+    return (size_t)(fslab4<N, fast_yr<N, M>() * M>() + N + M / 2) * sizeof(float4);
+}
 template <int N, int M> constexpr size_t fast_lines_smem() {
     return (size_t)(fast_lines<N>() * fast_xs<N>() + 2 * N) * sizeof(float4) + (size_t)(N / 2 + 1 + N + M) * sizeof(float2);
 }

@@ -60,6 +60,7 @@ struct FastTable {
        inv = nullptr;
     size_t smem_xt = 0, smem_y = 0;
     int lines_per_block = 0;
+    int yr = 1;                  // y rows per block of fwd and inv (grid N / yr)
     // units A and C with bulk row copies and the real-FFT split in registers
     // (se2_fast2.cuh, N = 64, 256); they copy rows of f and out, so a call
     // whose f (or out) is not 16-byte aligned runs fwd (or inv) instead

@@ -129,14 +129,16 @@ def test_unknown_plan_flag_rejected_on_host(lib):
 
 def test_allocation_accounting_entry_points(lib):
     """se2_debug_alloc_stats / se2_debug_fail_alloc work without a device:
-    nothing has been allocated in this process, bad arguments are rejected,
-    and arming or disarming the failure injection succeeds."""
+    the counts are consistent (both 0 where nothing has been allocated in this
+    process; GPU tests earlier in the same process may have allocated), bad
+    arguments are rejected, and arming or disarming the failure injection
+    succeeds."""
     ll = ctypes.c_longlong
     lib.se2_debug_alloc_stats.argtypes = [ctypes.POINTER(ll), ctypes.POINTER(ll)]
     lib.se2_debug_fail_alloc.argtypes = [ll]
     live, total = ll(-1), ll(-1)
     assert lib.se2_debug_alloc_stats(ctypes.byref(live), ctypes.byref(total)) == 0
-    assert live.value == 0 and total.value == 0
+    assert 0 <= live.value <= total.value
     assert lib.se2_debug_alloc_stats(None, ctypes.byref(total)) == 1
     assert lib.se2_debug_fail_alloc(-1) == 1
     assert lib.se2_debug_fail_alloc(3) == 0

@@ -128,3 +128,43 @@ def test_batch_runner_c4_classes_with_256x64(se2, tmp_path):
         C = _oracle_chain_coeffs(N, M, chains[i])
         want = O.convolve_chain(F, None, coeffs=[C] if len(chains[i]) % 2 else [C, 1.0])
         assert _rel(runner.out_of(i).double().cpu().numpy(), want) < 1e-5, (i, N, M, len(chains[i]))
+
+
+def test_batch_lanes_give_identical_results_and_tuner_keeps_the_fastest(se2, tmp_path):
+    """The classes on 1, 2 and all stream lanes compute the same outputs bit
+    for bit (each class runs the same kernels; only their concurrency
+    changes); the tuner times the lane counts and keeps the fastest."""
+    from paper_2504_05149_gb300.batch import BatchRunner
+    rng = synth.SplitMix64(4100)
+    shapes = [([32, 64, 128][rng.randint(0, 2)], [16, 32][rng.randint(0, 1)]) for _ in range(24)]
+    runner = BatchRunner(shapes, cache_path=str(tmp_path / "tune.json"))
+    for i, (N, M) in enumerate(shapes):
+        b = synth.draw_bumps(rng, 6)
+        runner.f_of(i).copy_(torch.from_numpy(synth.sample_bumps(N, M, b).astype(np.float32)))
+        runner.set_chain(i, [(0.03, 0.4, 0.2)] * (1 + i % 3))
+    runner.build_tables()
+    nc = len(runner.order)
+    assert runner.lanes()[0] == 1                      # a new plan runs the classes one after another
+    outs = []
+    for L in (1, 2, nc):
+        cur, lane_of, _ = runner.lanes(L)
+        assert cur == min(L, nc) and max(lane_of) == cur - 1 and min(lane_of) == 0
+        runner.out_packed.zero_()
+        _run_untuned(runner)
+        torch.cuda.synchronize()
+        outs.append(runner.out_packed.cpu().clone())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    runner.tune(reps=1)
+    cur, _, lane_ms = runner.lanes()
+    assert 1 in lane_ms and nc in lane_ms
+    assert lane_ms[cur] == min(lane_ms.values())
+    runner.out_packed.zero_()
+    runner.run()
+    torch.cuda.synchronize()
+    assert torch.equal(runner.out_packed.cpu(), outs[0])
+
+
+def _run_untuned(runner):
+    from paper_2504_05149_gb300 import _check, _ptr, _stream
+    _check(runner.lib.se2_batch_convolve_separable(runner._h, _ptr(runner.f_packed), _ptr(runner.tab_packed),
+                                                   _ptr(runner.out_packed), _stream(runner.dev)))
