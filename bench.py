@@ -359,6 +359,7 @@ def main():
         reps.append(e2.elapsed_time(e3))
     _, e2e_val = aggregate(sorted(reps)[1], B * ke, world, reduce_max)
     assert np.isfinite(hout.numpy()).all()
+    link = host_link_rate(torch, stream, hf, f, out, hout)
 
     # comparator (context only, not the product): the same convolution written
     # with torch.fft (cuFFT) on the same batch: irfftn(W . rfftn(f) . C)
@@ -418,7 +419,11 @@ def main():
             "mixed_vs_fp32": mixed,
             "cpu_baseline": base,
             "e2e": {"value": e2e_val, "unit": "conv/s", "h2d_bytes_per_step": int(F.nbytes),
-                    "d2h_bytes_per_step": int(F.nbytes)},
+                    "d2h_bytes_per_step": int(F.nbytes),
+                    "host_link": {"achieved_GBps": e2e_val / B * 2 * F.nbytes / 1e9,
+                                  "copy_GBps": link, "frac": e2e_val / B * 2 * F.nbytes / 1e9 / link,
+                                  "what": "host<->device bytes of the e2e run per second, against plain "
+                                          "cudaMemcpyAsync of the same buffers, both directions at once"}},
             "gpu_launches": launches_timed,
             "comparators": comp,
             "clocks": clocks,
@@ -499,6 +504,31 @@ NCU_TRAFFIC_PER_CONV = {k: (None if any(x is None for x in v) else sum(v) / 2) f
 NCU_TRAFFIC_WARM_PER_LAUNCH = {(256, 64, "f32"): ((33.787168 + 27.261472) * 1e6, (36.289920 + 6.271296) * 1e6,
                                                   (0.024800 + 30.836576) * 1e6)}
 UNIT_NAMES = ("kf_fwd_xt", "kf_lines", "kf_inv_tx")
+
+
+def host_link_rate(torch, stream, hf, f, out, hout, reps=3):
+    """GB/s of the host link for the e2e traffic: pinned hf -> device f and
+    device out -> pinned hout as plain copies on two streams at once (median
+    of `reps`).  Both copies rewrite data that is already there."""
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    times = []
+    for _ in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_in.wait_stream(stream)
+        s_out.wait_stream(stream)
+        with torch.cuda.stream(s_in):
+            f.copy_(hf, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            hout.copy_(out, non_blocking=True)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sorted(times[1:])[len(times[1:]) // 2]
+    return (hf.numel() * hf.element_size() + out.numel() * out.element_size()) / (ms / 1e3) / 1e9
 
 
 def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_bytes, precision, c_rows=None,
