@@ -148,17 +148,19 @@ class ClockSampler:
 
 
 def _oracle_worker(args):
-    """Single convolutions of the oracle for `seconds` (one process)."""
-    N, M, seconds = args
+    """Convolutions (k = 1) or k-fold chains of the oracle for `seconds` (one
+    process; at least one)."""
+    N, M, seconds = args[:3]
+    k = args[3] if len(args) > 3 else 1
     from oracle import se2_oracle as O
     import synth
-    prob = synth.make_problem(2, 0, N, M, n_bumps=16, n_kernels=1)
+    prob = synth.make_problem(2, 0, N, M, n_bumps=16, n_kernels=k)
     F = synth.sample_bumps(N, M, prob.bumps)
-    C = O.coeffs_full(synth.sample_kernel(N, M, prob.kernels[0]))
+    Cs = [O.coeffs_full(synth.sample_kernel(N, M, kp)) for kp in prob.kernels]
     n = 0
     t0 = time.perf_counter()
     while True:
-        O.convolve_chain(F, None, coeffs=[C])
+        O.convolve_chain(F, None, coeffs=Cs)
         n += 1
         el = time.perf_counter() - t0
         if el >= seconds or n >= 64:
@@ -177,22 +179,26 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(N, M, seconds=10.0):
+def cpu_baseline(N, M, seconds=10.0, k=1, unit="conv/s", procs=None):
     """The FP64 oracle (numpy FFT route, as it stands) on host cores: single
-    convolutions of the same workload with precomputed kernel spectra, on one
-    core, then one process per core (spawned) for the same time."""
+    convolutions (k = 1) or k-fold chains of the same workload with
+    precomputed kernel spectra, on one core, then one process per core
+    (spawned; `procs` caps the count where one problem needs much memory) for
+    the same time."""
     import multiprocessing as mp
-    n1, el1 = _oracle_worker((N, M, seconds))
+    n1, el1 = _oracle_worker((N, M, seconds, k))
     ncores = os.cpu_count() or 1
-    with mp.get_context("spawn").Pool(ncores) as pool:
-        res = pool.map(_oracle_worker, [(N, M, seconds)] * ncores)
+    np_ = min(ncores, procs) if procs else ncores
+    with mp.get_context("spawn").Pool(np_) as pool:
+        res = pool.map(_oracle_worker, [(N, M, seconds, k)] * np_)
     total = sum(n / el for n, el in res)
-    return {"value": total, "unit": "conv/s", "cores": ncores, "kind": "oracle", "nproc": ncores,
+    what = "single convolutions" if k == 1 else f"{k}-fold chains"
+    return {"value": total, "unit": unit, "cores": np_, "kind": "oracle", "nproc": ncores,
             "cpu_model": cpu_model(),
-            "single_core": {"value": n1 / el1, "unit": "conv/s", "cores": 1},
-            "sample": f"numpy FFT route, FP64, precomputed kernel spectrum: {n1} single convolutions N={N} M={M} "
-                      f"on one core in {el1:.1f} s; then {ncores} spawned processes, one per core, "
-                      f"{sum(n for n, _ in res)} convolutions in about {seconds:.0f} s"}
+            "single_core": {"value": n1 / el1, "unit": unit, "cores": 1},
+            "sample": f"numpy FFT route, FP64, precomputed kernel spectra: {n1} {what} N={N} M={M} "
+                      f"on one core in {el1:.1f} s; then {np_} spawned processes, one per core, "
+                      f"{sum(n for n, _ in res)} in about {seconds:.0f} s"}
 
 
 METRIC_C2 = "SE(2) convolutions/s at N=256, M=64 (FP32) and fraction of HBM roofline"
@@ -668,11 +674,13 @@ def run_chain8(args, emit_all=False):
     ms, clocks, launched = _clock_and_time(fn, args.steps, args.warmup, dev, plans=(plan,))
     hbm, src = peaks()
     ach = alg / (ms / args.steps / 1e3) / 1e9
+    # the oracle computes the final chain; emit-all adds only writes of V_p
+    cpu = None if args.no_cpu_baseline else cpu_baseline(N, M, k=k, unit="chain/s")
     _line(metric, B * args.steps / (ms / 1e3), "chain/s", args, ms,
           {"workload": what, "grid": [M, N, N]},
           {"roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "traffic": None, "peak_source": src, "alg_bytes_per_chain": alg / B},
-           "gpu_launches": launched, "clocks": clocks})
+           "cpu_baseline": cpu, "gpu_launches": launched, "clocks": clocks})
 
 
 def grid_flops(L, N, k=1):
@@ -826,7 +834,14 @@ def run_precision(args):
     for kp in probs[0].kernels:
         gx, gy, gt = synth.kernel_factors(N, M, kp)
         coeffs.append(O.coeffs_separable(gx, gy, gt))
+    t0 = time.perf_counter()
     want = O.convolve_chain(F0, None, coeffs=coeffs)
+    el = time.perf_counter() - t0
+    # one core only: the 32 full FP64 spectra of one problem take 17 GB, too
+    # many for a process per core
+    cpu = {"value": 1.0 / el, "unit": "conv/s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": f"one 32-fold chain of problem 0 (N={N}, M={M}, precomputed separable spectra), numpy FFT "
+                     f"route, FP64, {el:.1f} s on one core"}
     err = {p: float(np.max(np.abs(res[p][2] - want)) / np.max(np.abs(want))) for p in res}
     v, ms, _, clocks = res["split_bf16"]
     _line("SE(2) convolutions/s at N=512, M=128, 32-fold chain: split-bf16 tensor-core angular DFT",
@@ -834,7 +849,7 @@ def run_precision(args):
           {"workload": "batch 8, 32-bump f1 with amplitudes log-uniform in [1e-6, 1], 32-fold separable chain",
            "grid": [M, N, N]},
           {"fp32_value": res["f32"][0], "split_f16_value": res["split_f16"][0], "max_rel_err_vs_fp64_oracle": err,
-           "clocks": clocks, "gpu_launches": 5 * args.steps})
+           "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 5 * args.steps})
 
 
 def run_adjoint(args):

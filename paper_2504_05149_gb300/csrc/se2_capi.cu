@@ -744,7 +744,7 @@ se2_status run_chain_fast(se2_plan_s* p, const float* f, int B, const void* cons
         ++p->launches;
         time_end(p, t0, s);
         const size_t t1 = time_begin(p, 1, s);
-        (sep_tables != nullptr ? ft.lines_sep : ft.lines)<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);
+        (sep_tables != nullptr ? ft.lines_sep : ft.lines)<<<dim3(yb, nb), kLineThreads, ft.smem_y, s>>>(a);
         ++p->launches;
         time_end(p, t1, s);
         const size_t t2 = time_begin(p, 2, s);
@@ -856,7 +856,7 @@ se2_status run_backward_fast(se2_plan_s* p, const float* g, const float* f, int 
             a.s = s1;
             launch_unit_a(ft, p->N, nb, st, a);
             ++p->launches;
-            ft.lines_fwd<<<dim3(yb, nb), kThreads, ft.smem_y, st>>>(a);
+            ft.lines_fwd<<<dim3(yb, nb), kLineThreads, ft.smem_y, st>>>(a);
             ++p->launches;
         }
         a.s = s0;
@@ -870,7 +870,7 @@ se2_status run_backward_fast(se2_plan_s* p, const float* g, const float* f, int 
         for (int i = 0; i < n_params; ++i) a.dC[i] = (const float2*)dcoeffs[i] + c0 * cps;
         a.grad_params = grad_params;
         a.want_grad = grad_f != nullptr;
-        ft.lines_adj<<<dim3(yb, nb), kThreads, ft.smem_y, st>>>(a);
+        ft.lines_adj<<<dim3(yb, nb), kLineThreads, ft.smem_y, st>>>(a);
         ++p->launches;
         if (grad_f) {
             a.out = grad_f + c0 * gs;
@@ -1282,11 +1282,11 @@ se2_status se2_convolve_chain_all(se2_plan_t p, const void* f, int B, const void
         a.sout = s1;
         launch_unit_a(ft, p->N, nb, s, a);       // x, theta
         ++p->launches;
-        ft.lines_fwd<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);     // y: the full spectrum of f
+        ft.lines_fwd<<<dim3(yb, nb), kLineThreads, ft.smem_y, s>>>(a);     // y: the full spectrum of f
         ++p->launches;
         for (int q = 1; q <= k; ++q) {
             a.p = q;
-            ft.lines_acc<<<dim3(yb, nb), kThreads, ft.smem_y, s>>>(a);   // R_q = R_{q-1} C_q; iDFT_y -> s1
+            ft.lines_acc<<<dim3(yb, nb), kLineThreads, ft.smem_y, s>>>(a);   // R_q = R_{q-1} C_q; iDFT_y -> s1
             ++p->launches;
             FArgs c = a;
             c.s = s1;

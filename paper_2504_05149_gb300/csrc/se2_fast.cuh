@@ -443,10 +443,13 @@ template <int N> __host__ __device__ constexpr int fast_xs() {
     constexpr int a = xslots<Fac<N>::R1, Fac<N>::R2>(), b = xslots<Fac<N>::R2, Fac<N>::R1>();
     return ((a > b ? a : b) + 7) / 8 * 8 + 1;
 }
-template <int N> __host__ __device__ constexpr int fast_lines() { return kThreads / team_size<N>(); }
+// Threads of a unit-B block (its line pairs x team lanes); blocks per SM
+// such that the SM holds as many threads as with units A and C.
+constexpr int kLineThreads = 256;
+template <int N> __host__ __device__ constexpr int fast_lines() { return kLineThreads / team_size<N>(); }
 
 template <int N, int M, int MODE>
-__global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
+__global__ void __launch_bounds__(kLineThreads, 2 * kThreads / kLineThreads) kf_lines(FArgs a) {
     constexpr bool SEP = MODE == FL_SEP;
     constexpr int Q = N / 4, P1 = Q + 1, CP = N / 2 + 1, TP4 = ftp4<N>();
     constexpr int TL = N / 2 + 1 + N + M;    // separable table length
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
     float4* TWI = TWF + N;
     float2* TSEP = reinterpret_cast<float2*>(TWI + N);   // this problem's separable tables
     __shared__ double sh_scale;
-    __shared__ double red[kThreads / 32];
+    __shared__ double red[kLineThreads / 32];
     const int tid = threadIdx.x, b = blockIdx.y;
     const int c = tid % LINES, t = tid / LINES;
     const int pl = blockIdx.x * LINES + c;
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_lines(FArgs a) {
                 __syncthreads();
                 if (tid == 0) {
                     double tsum = 0;
-                    for (int w = 0; w < kThreads / 32; ++w) tsum += red[w];
+                    for (int w = 0; w < kLineThreads / 32; ++w) tsum += red[w];
                     atomicAdd(a.grad_params + i, 0.25 * a.inv_L * tsum);
                 }
                 __syncthreads();
