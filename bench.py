@@ -167,6 +167,32 @@ def _oracle_worker(args):
             return n, el
 
 
+def _oracle_adjoint_worker(args):
+    """Forward + adjoint steps of the oracle for `seconds` (one process; at
+    least one): the convolution with the sampled kernel, the residual, the
+    input gradient and the two parameter partials through the kernel
+    samples' derivatives.  Returns (steps, seconds)."""
+    N, M, seconds = args
+    import numpy as np
+    from oracle import se2_oracle as O
+    import synth
+    F = synth.sample_bumps(N, M, synth.make_problem(5, 0, N, M, n_bumps=16).bumps)
+    target = np.random.default_rng(5).standard_normal((M, N, N))
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        P, dPs, dPt = O.kernel_samples_and_derivs(N, M, 0.025, 0.25)
+        C = O.coeffs_full(P)
+        G = O.convolve_chain(F, None, coeffs=[C]) - target
+        O.adjoint(G, None, coeffs=[C])
+        gk = O.grad_kernel_samples(F, G)
+        float((gk * dPs).sum()), float((gk * dPt).sum())
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= 64:
+            return n, el
+
+
 def cpu_model():
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -825,9 +851,10 @@ def run_precision(args):
         plan = se2.Plan(N, M, batch=B, precision=prec)
         tab = se2.separable_tables(plan, params, kk)
         out = torch.empty_like(f)
-        ms, clocks, _ = _clock_and_time(lambda: se2.convolve_separable(plan, f, tab, out), args.steps, args.warmup, dev)
+        ms, clocks, launched = _clock_and_time(lambda: se2.convolve_separable(plan, f, tab, out), args.steps,
+                                               args.warmup, dev, plans=(plan,))
         plan.status()
-        res[prec] = (B * args.steps / (ms / 1e3), ms, out[0].double().cpu().numpy(), clocks)
+        res[prec] = (B * args.steps / (ms / 1e3), ms, out[0].double().cpu().numpy(), clocks, launched)
         plan.close()
     F0 = f[0].double().cpu().numpy()
     coeffs = []
@@ -843,13 +870,13 @@ def run_precision(args):
            "sample": f"one 32-fold chain of problem 0 (N={N}, M={M}, precomputed separable spectra), numpy FFT "
                      f"route, FP64, {el:.1f} s on one core"}
     err = {p: float(np.max(np.abs(res[p][2] - want)) / np.max(np.abs(want))) for p in res}
-    v, ms, _, clocks = res["split_bf16"]
+    v, ms, _, clocks, launched = res["split_bf16"]
     _line("SE(2) convolutions/s at N=512, M=128, 32-fold chain: split-bf16 tensor-core angular DFT",
           v, "conv/s", args, ms,
           {"workload": "batch 8, 32-bump f1 with amplitudes log-uniform in [1e-6, 1], 32-fold separable chain",
            "grid": [M, N, N]},
           {"fp32_value": res["f32"][0], "split_f16_value": res["split_f16"][0], "max_rel_err_vs_fp64_oracle": err,
-           "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 5 * args.steps})
+           "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launched})
 
 
 def run_adjoint(args):
@@ -871,11 +898,25 @@ def run_adjoint(args):
         loss = 0.5 * ((out - target) ** 2).sum()
         loss.backward()
     ms, clocks, launched = _clock_and_time(step, args.steps, args.warmup, dev, plans=(plan,))
+    cpu = None
+    if not args.no_cpu_baseline:
+        import multiprocessing as mp
+        n1, el1 = _oracle_adjoint_worker((N, M, 10.0))
+        ncores = os.cpu_count() or 1
+        with mp.get_context("spawn").Pool(ncores) as pool:
+            res = pool.map(_oracle_adjoint_worker, [(N, M, 10.0)] * ncores)
+        cpu = {"value": sum(n / el for n, el in res), "unit": "conv/s", "cores": ncores, "kind": "oracle",
+               "nproc": ncores, "cpu_model": cpu_model(),
+               "single_core": {"value": n1 / el1, "unit": "conv/s", "cores": 1},
+               "sample": f"forward + adjoint steps of one problem (kernel samples and derivatives, coefficients, "
+                         f"convolution, input gradient, two parameter partials), numpy FFT route, FP64: {n1} on "
+                         f"one core in {el1:.1f} s; then {ncores} spawned processes, "
+                         f"{sum(n for n, _ in res)} in about 10 s"}
     _line("SE(2) forward+adjoint convolutions/s at N=256, M=64, batch 64 (FP32)", B * args.steps / (ms / 1e3),
           "conv/s", args, ms, {"workload": "loss = 1/2||f * rho(sigma, sigma_theta) - target||^2, grads wrt f and "
                                "(sigma, sigma_theta); includes kernel sampling, 3 coefficient transforms, forward, adjoint",
                                "grid": [M, N, N], "global_batch": B},
-          {"clocks": clocks, "gpu_launches": launched})
+          {"cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launched})
 
 
 if __name__ == "__main__":
