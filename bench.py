@@ -808,6 +808,7 @@ def run_batch(args):
     runner.build_tables()
     runner.tune()
     lanes, lane_of, lane_ms = runner.lanes()
+    one_on, one_ms = runner.one_launch()
     runner.capture()
     ms, clocks, _ = _clock_and_time(runner.replay, args.steps, args.warmup, dev)
     pts = runner.points()
@@ -817,10 +818,13 @@ def run_batch(args):
     _line("SE(2) convolutions/s, 4096 uneven problems with separable kernel chains (FP32)",
           args.problems * args.steps / (ms / 1e3), "conv/s", args, ms,
           {"workload": "4096 problems, N~U{32,64,128,256}, M~U{16,32,64}, chains k~U{1..16}, 3..16 bumps; "
-                       "per-size-class plans on tuned stream lanes in one CUDA graph", "points_per_step": pts,
+                       "per-size-class plans on tuned stream lanes or one persistent launch, in one CUDA graph",
+                       "points_per_step": pts,
            "classes": {f"{N}x{M}": [len(v), runner.config[(N, M)][0], runner.config[(N, M)][1]]
                        for (N, M), v in runner.classes.items()},
-           "lanes": lanes, "tuned_ms_by_lanes": {str(L): round(v, 4) for L, v in lane_ms.items()}},
+           "lanes": lanes, "tuned_ms_by_lanes": {str(L): round(v, 4) for L, v in lane_ms.items()},
+           "schedule": "one persistent launch" if one_on else f"{lanes} stream lane(s)",
+           "one_launch_tuned_ms": round(one_ms, 4)},
           {"points_per_s": pts * args.steps / (ms / 1e3),
            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "traffic": None, "peak_source": src, "alg_bytes_per_step": alg},

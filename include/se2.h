@@ -55,7 +55,7 @@ typedef enum {
     SE2_ERR_OOM = 3,          /* plan allocation failed (nothing leaked)      */
     SE2_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed         */
     SE2_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up           */
-    SE2_ERR_NUMERIC = 6       /* reserved: non-finite result detected         */
+    SE2_ERR_NUMERIC = 6       /* non-finite output (flag SE2_CHECK_FINITE)    */
 } se2_status;
 
 typedef enum {
@@ -311,7 +311,8 @@ se2_status se2_convolve_separable(se2_plan_t plan, const void* f, int B, const v
  * schedules (`reps` calls each, on the given data, on `stream`) and keep the
  * fastest: FP32 fast path with pipeline depth 1 or depth 2 with groups of
  * 1, 2, 4, .. 64 problems, or the persistent dataflow kernel.  Then time the
- * whole batch on 1, 2, 3, 4 and n_classes lanes and keep the fastest.
+ * whole batch on 1, 2, 3, 4 and n_classes lanes and keep the fastest, then
+ * the one-launch kernel (below), kept if faster still.
  * Synchronous; not for stream capture.  se2_batch_plan_config reports per
  * class (host arrays of n_classes, each may be NULL): shape, count, pipeline
  * depth (0 for the persistent kernel), group, persistent (0/1) and the tuned
@@ -324,6 +325,37 @@ se2_status se2_convolve_separable(se2_plan_t plan, const void* f, int B, const v
  * lane_of_class[n_classes]; lane_ms[n_classes], entry L - 1 the tuner's
  * whole-batch ms on L lanes (0 where not timed).  Host only.
  * se2_batch_plan_launches: kernels launched through the plan so far.
+ *
+ * se2_batch_plan_one_launch -- the whole batch as one persistent kernel: every
+ * unit (x+theta pass, y pass, inverse theta+x pass) of every problem of every
+ * class in one launch, ordered by a work list built at enabling (classes
+ * largest first, each a pipeline of problems with per-problem completion
+ * counters and a ring of scratch slots), after one memset of the counters.
+ * FP32; classes N in {32, 64, 128, 256} x M in {16, 32, 64}, at most 16
+ * classes and 65535 problems per class (else SE2_ERR_UNSUPPORTED).
+ * mode 1 enables it (allocating its work list and scratch: not a convolve
+ * call), 0 disables it, -1 leaves it; *current receives 1 if in force,
+ * *tuned_ms the tuner's time for it (0 if not timed).  The tuner enables it
+ * only when it beats the best lane schedule.  Every wait of the kernel is
+ * bounded; one that gives up makes se2_batch_plan_status return
+ * SE2_ERR_TIMEOUT.
+ *
+ * se2_batch_plan_status -- synchronises `stream`, then reports (and clears) a
+ * timed-out wait of the one-launch kernel, then each class plan's status.
+ *
+ * se2_debug_batch_wait_timeout -- test hook: runs the one-launch kernel on the
+ * given buffers with every y-pass wait asking for one unit more than exists,
+ * so each such wait gives up after 4096 polls; the next
+ * se2_batch_plan_status returns SE2_ERR_TIMEOUT and the plan stays usable.
+ * out is overwritten with partial results.  Asynchronous on `stream`.
+ *
+ * se2_debug_batch_work_list -- the one-launch kernel's work list for classes
+ * shapes[c] with counts[c] problems (in plan order) and `grid` resident
+ * blocks, on the host (no device): with units == NULL, *n_units receives the
+ * length; else units (host, *n_units entries) receives the codes, class << 28
+ * | stage << 26 | block << 16 | problem in class (stage 0 x+theta, 1 y,
+ * 2 inverse theta+x).  slots[c], lag[c] (each may be NULL) receive the ring
+ * size D and lag L of each class.  For tests of the schedule.
  */
 typedef struct { int N, M; } se2_shape;
 typedef struct se2_batch_plan_s* se2_batch_plan_t;
@@ -339,6 +371,12 @@ se2_status se2_batch_tune(se2_batch_plan_t plan, const void* f, const void* tabl
 se2_status se2_batch_plan_config(se2_batch_plan_t plan, int* n_classes, se2_shape* shape, int* count, int* depth,
                                  int* group, int* persistent, double* tuned_ms);
 se2_status se2_batch_plan_lanes(se2_batch_plan_t plan, int lanes, int* current, int* lane_of_class, double* lane_ms);
+se2_status se2_batch_plan_one_launch(se2_batch_plan_t plan, int mode, int* current, double* tuned_ms);
+se2_status se2_batch_plan_status(se2_batch_plan_t plan, void* stream);
+se2_status se2_debug_batch_wait_timeout(se2_batch_plan_t plan, const void* f, const void* tables, void* out,
+                                        void* stream);
+se2_status se2_debug_batch_work_list(const se2_shape* shapes, const int* counts, int n_classes, int grid,
+                                     unsigned* units, long long* n_units, int* slots, int* lag);
 unsigned long long se2_batch_plan_launches(se2_batch_plan_t plan);
 
 /*

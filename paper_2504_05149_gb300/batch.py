@@ -49,10 +49,14 @@ def _bind(lib):
                                           ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip),
                                           ctypes.POINTER(ctypes.c_double)]
     lib.se2_batch_plan_lanes.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_double)]
+    lib.se2_batch_plan_one_launch.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_double)]
+    lib.se2_batch_plan_status.argtypes = [vp, vp]
+    lib.se2_debug_batch_wait_timeout.argtypes = [vp, vp, vp, vp, vp]
     lib.se2_batch_plan_launches.argtypes = [vp]
     lib.se2_batch_plan_launches.restype = ctypes.c_ulonglong
     for name in ("se2_batch_plan_create", "se2_batch_plan_destroy", "se2_batch_plan_layout", "se2_batch_separable_tables",
-                 "se2_batch_convolve_separable", "se2_batch_tune", "se2_batch_plan_config", "se2_batch_plan_lanes"):
+                 "se2_batch_convolve_separable", "se2_batch_tune", "se2_batch_plan_config", "se2_batch_plan_lanes",
+                 "se2_batch_plan_one_launch", "se2_batch_plan_status", "se2_debug_batch_wait_timeout"):
         getattr(lib, name).restype = ctypes.c_int
     lib._se2_batch_bound = True
     return lib
@@ -170,7 +174,9 @@ class BatchRunner:
             self.config[c] = (path, group)
             record[f"{gpu}|N={c[0]}|M={c[1]}|n={n}|f32"] = [path, depth, group, ms]
         lanes, _, lane_ms = self.lanes()
-        record[f"{gpu}|batch|classes={len(self.order)}|n={len(self.shapes)}|f32"] = ["lanes", lanes, lane_ms]
+        one, one_ms = self.one_launch()
+        record[f"{gpu}|batch|classes={len(self.order)}|n={len(self.shapes)}|f32"] = \
+            ["one launch" if one else "lanes", lanes, lane_ms, one_ms]
         try:
             os.makedirs(os.path.dirname(self.cache_path) or ".", exist_ok=True)
             old = {}
@@ -193,6 +199,22 @@ class BatchRunner:
         ms = (ctypes.c_double * m)()
         _check(self.lib.se2_batch_plan_lanes(self._h, int(n) if n else 0, ctypes.byref(cur), lane, ms))
         return cur.value, list(lane), {L + 1: ms[L] for L in range(m) if ms[L] > 0}
+
+    def one_launch(self, enable: Optional[bool] = None):
+        """Enable (True) or disable (False) the one-launch kernel for the whole
+        batch, or leave it (None); returns (in force, tuner's ms for it)."""
+        cur = ctypes.c_int()
+        ms = ctypes.c_double()
+        mode = -1 if enable is None else int(bool(enable))
+        with torch.cuda.device(self.dev):
+            _check(self.lib.se2_batch_plan_one_launch(self._h, mode, ctypes.byref(cur), ctypes.byref(ms)))
+        if enable is not None:
+            self.graph = None          # a captured graph holds the other schedule
+        return bool(cur.value), ms.value
+
+    def status(self):
+        """se2_batch_plan_status on the current stream (raises on a timed-out wait)."""
+        _check(self.lib.se2_batch_plan_status(self._h, _stream(self.dev)))
 
     # -- execution --------------------------------------------------------------
     def run(self):

@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdint>
@@ -1553,13 +1554,37 @@ struct se2_batch_plan_s {
     cudaEvent_t fork = nullptr;
     int lanes = 1;                                // concurrent stream lanes (1: classes one after another)
     std::vector<double> lane_ms;                  // tuned whole-batch ms per lane count (index = lanes)
+    // the whole batch as one persistent launch (kf_batch_persist)
+    struct OneLaunch {
+        bool ready = false, on = false;
+        se2::BClass* cls = nullptr;               // device [n_classes]
+        unsigned* units = nullptr;                // device work list
+        unsigned n_units = 0;
+        unsigned* ctr = nullptr;                  // device [1 + 3 n]
+        void* ring = nullptr;                     // scratch rings of all classes
+        int* err = nullptr;
+        int grid = 0;
+        double tuned_ms = 0;
+        unsigned long long launches = 0;
+    } one;
 };
 
 namespace {
 
 constexpr size_t kBatchScratch = (size_t)512 << 20;   // scratch cap of one class's sub-plan
 
+void batch_one_free(se2_batch_plan_s* b) {
+    auto& o = b->one;
+    if (o.cls) dev_free(o.cls);
+    if (o.units) dev_free(o.units);
+    if (o.ctr) dev_free(o.ctr);
+    if (o.ring) dev_free(o.ring);
+    if (o.err) dev_free(o.err);
+    o = se2_batch_plan_s::OneLaunch{};
+}
+
 void batch_free(se2_batch_plan_s* b) {
+    batch_one_free(b);
     for (auto& c : b->cls) {
         if (c.plan) se2_plan_destroy(c.plan);
         if (c.alt) se2_plan_destroy(c.alt);
@@ -1614,6 +1639,154 @@ se2_status batch_run_class(se2_batch_plan_s* b, se2_batch_plan_s::Class& c, cons
                            unsigned char* out, cudaStream_t s) {
     const size_t re = b->prec == SE2_F64 ? sizeof(double) : sizeof(float);
     return se2_convolve_separable(c.plan, f + c.goff * re, c.count, tab + c.toff * 2 * re, out + c.goff * re, s);
+}
+
+// The one-launch path: per class its unit counts, lag L (rounds; at least
+// ~1.5 waves of units between a producer and its consumer) and ring of
+// D = 3L + 1 scratch slots; the work list merges the classes' rounds (a
+// class starts when the one before it stops issuing units A).  Allocates
+// (not a convolve call).  SE2_ERR_UNSUPPORTED where the kernel carries a
+// class's (N, M) not, or for FP64.
+struct OneClass { unsigned nA, nB, nC; long long s4; int L, D, n, start; };
+
+// The work list of the one-launch kernel for classes (N, M, count) in plan
+// order and `grid` resident blocks (host only).  Fills per class its unit
+// counts, lag L, ring slots D and first round; SE2_ERR_UNSUPPORTED where the
+// kernel carries a class not.
+se2_status batch_work_list(const se2_shape* shapes, const int* counts, int nc, int grid, std::vector<OneClass>& ci,
+                           std::vector<unsigned>& units) {
+    if (nc > 16) return fail(SE2_ERR_UNSUPPORTED, "the one-launch batch kernel carries at most 16 classes");
+    if (grid < 1) return fail(SE2_ERR_INVALID_ARG, "grid=%d must be >= 1", grid);
+    ci.assign(nc, OneClass{});
+    for (int c = 0; c < nc; ++c) {
+        OneClass& x = ci[c];
+        if (counts[c] < 1 || counts[c] > 65535 || !batch_persist_units(shapes[c].N, shapes[c].M, &x.nA, &x.nB, &x.nC, &x.s4))
+            return fail(SE2_ERR_UNSUPPORTED, "class N=%d, M=%d (%d problems) is not carried by the one-launch kernel",
+                        shapes[c].N, shapes[c].M, counts[c]);
+        const unsigned upr = x.nA + x.nB + x.nC;
+        x.L = (int)((3u * (unsigned)grid / 2u + upr - 1) / upr);
+        if (x.L < 1) x.L = 1;
+        x.D = 3 * x.L + 1 < counts[c] ? 3 * x.L + 1 : counts[c];
+        x.n = counts[c];
+        x.start = c == 0 ? 0 : ci[c - 1].start + ci[c - 1].n;
+    }
+    // rounds: class c's round r = R - start holds A of r, B of r - L, C of r - 2L
+    units.clear();
+    int last = 0;
+    for (int c = 0; c < nc; ++c) last = std::max(last, ci[c].start + ci[c].n + 2 * ci[c].L);
+    for (int R = 0; R < last; ++R) {
+        for (int c = 0; c < nc; ++c) {
+            const OneClass& x = ci[c];
+            const int r = R - x.start;
+            if (r < 0 || r >= x.n + 2 * x.L) continue;
+            if (r < x.n)
+                for (unsigned u = 0; u < x.nA; ++u) units.push_back(unit_code(c, 0, (int)u, r));
+            if (r - x.L >= 0 && r - x.L < x.n)
+                for (unsigned u = 0; u < x.nB; ++u) units.push_back(unit_code(c, 1, (int)u, r - x.L));
+            if (r - 2 * x.L >= 0 && r - 2 * x.L < x.n)
+                for (unsigned u = 0; u < x.nC; ++u) units.push_back(unit_code(c, 2, (int)u, r - 2 * x.L));
+        }
+    }
+    return SE2_OK;
+}
+
+se2_status batch_one_init(se2_batch_plan_s* b) {
+    auto& o = b->one;
+    if (o.ready) return SE2_OK;
+    if (b->prec != SE2_F32) return fail(SE2_ERR_UNSUPPORTED, "the one-launch batch kernel is FP32 only");
+    const int nc = (int)b->cls.size();
+    int bps = 0, nsm = 0;
+    cudaError_t e = batch_persist_prepare(&bps);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->dev);
+    if (e != cudaSuccess) return cuda_fail(e, "one-launch kernel attributes");
+    if (bps < 1) return fail(SE2_ERR_UNSUPPORTED, "the one-launch batch kernel does not fit an SM");
+    const int grid = bps * nsm;
+    std::vector<se2_shape> shp(nc);
+    std::vector<int> cnt(nc);
+    for (int c = 0; c < nc; ++c) {
+        shp[c] = se2_shape{b->cls[c].N, b->cls[c].M};
+        cnt[c] = b->cls[c].count;
+    }
+    std::vector<OneClass> ci;
+    std::vector<unsigned> units;
+    se2_status st = batch_work_list(shp.data(), cnt.data(), nc, grid, ci, units);
+    if (st != SE2_OK) return st;
+    size_t ring_bytes = 0;
+    for (int c = 0; c < nc; ++c) ring_bytes += (size_t)ci[c].D * (size_t)ci[c].s4 * 16;
+    // device state
+    std::vector<BClass> hc(nc);
+    {
+        e = dev_alloc((void**)&o.cls, sizeof(BClass) * nc);
+        if (e == cudaSuccess) e = dev_alloc((void**)&o.units, sizeof(unsigned) * units.size());
+        if (e == cudaSuccess) e = dev_alloc((void**)&o.ctr, sizeof(unsigned) * (1 + 3 * (size_t)b->n));
+        if (e == cudaSuccess) e = dev_alloc(&o.ring, ring_bytes);
+        if (e == cudaSuccess) e = dev_alloc((void**)&o.err, sizeof(int));
+        if (e != cudaSuccess) {
+            batch_one_free(b);
+            return fail(SE2_ERR_OOM, "one-launch batch state: %s", cudaGetErrorString(e));
+        }
+    }
+    size_t at = 0;
+    for (int c = 0; c < nc; ++c) {
+        const auto& k = b->cls[c];
+        const se2_plan_s* p = k.plan;
+        BClass& h = hc[c];
+        h = BClass{};
+        h.a.s = (float4*)((unsigned char*)o.ring + at);
+        h.a.s_pstride = ci[c].s4;
+        h.a.twN = (const float2*)p->twN;
+        h.a.twM = (const float2*)p->twM;
+        h.a.k = 1;
+        h.a.inv_L = 1.0 / ((double)k.N * k.N * k.M);
+        h.a.wsign = (b->flags & SE2_GRID_ORIGIN_ZERO) ? 0 : 1;
+        h.a.err = o.err;
+        h.goff = k.goff;
+        h.toff = k.toff;
+        h.grid = (long long)k.N * k.N * k.M;
+        h.tabs = (long long)(k.N / 2 + 1 + k.N + k.M);
+        h.kind = batch_kind(k.N, k.M);
+        h.first = k.first;
+        h.slots = ci[c].D;
+        h.nA = ci[c].nA;
+        h.nB = ci[c].nB;
+        h.nC = ci[c].nC;
+        at += (size_t)ci[c].D * (size_t)ci[c].s4 * 16;
+    }
+    e = cudaMemcpy(o.cls, hc.data(), sizeof(BClass) * nc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(o.units, units.data(), sizeof(unsigned) * units.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(o.err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        batch_one_free(b);
+        return cuda_fail(e, "one-launch batch state");
+    }
+    o.n_units = (unsigned)units.size();
+    o.grid = grid;
+    o.ready = true;
+    return SE2_OK;
+}
+
+se2_status batch_one_run(se2_batch_plan_s* b, const unsigned char* f, const unsigned char* tab, unsigned char* out,
+                         cudaStream_t s, unsigned dep_extra, long long spin_limit) {
+    auto& o = b->one;
+    cudaError_t e = cudaMemsetAsync(o.ctr, 0, sizeof(unsigned) * (1 + 3 * (size_t)b->n), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    BPArgs a{};
+    a.cls = o.cls;
+    a.units = o.units;
+    a.n_units = o.n_units;
+    a.f = (const float*)f;
+    a.out = (float*)out;
+    a.tables = (const float2*)tab;
+    a.work = o.ctr;
+    a.cnt = o.ctr + 1;
+    a.err = o.err;
+    a.spin_limit = spin_limit;
+    a.dep_extra = dep_extra;
+    launch_batch_persist((int)std::min<unsigned>(o.n_units, (unsigned)o.grid), s, a);
+    ++o.launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SE2_OK;
 }
 
 // Every class, on its lane: lane 0 is the caller's stream, lanes 1.. are
@@ -1776,6 +1949,7 @@ se2_status se2_batch_convolve_separable(se2_batch_plan_t b, const void* f, const
     const auto* fb = static_cast<const unsigned char*>(f);
     const auto* tb = static_cast<const unsigned char*>(tables);
     auto* ob = static_cast<unsigned char*>(out);
+    if (b->one.on) return batch_one_run(b, fb, tb, ob, s, 0, kSpinLimit);
     return batch_run(b, fb, tb, ob, s);
 }
 
@@ -1894,10 +2068,108 @@ se2_status se2_batch_tune(se2_batch_plan_t b, const void* f, const void* tables,
             if (L == nc) break;
         }
         batch_assign_lanes(b, best_l);
+        // and the whole batch as one persistent launch, where the kernel
+        // carries every class; kept only if it beats the best lanes
+        b->one.on = false;
+        if (st == SE2_OK && batch_one_init(b) == SE2_OK) {
+            st = batch_one_run(b, fb, tb, ob, s, 0, kSpinLimit);   // warm-up
+            cudaEventRecord(e0, s);
+            for (int i = 0; i < reps && st == SE2_OK; ++i) st = batch_one_run(b, fb, tb, ob, s, 0, kSpinLimit);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (st == SE2_OK) {
+                e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) st = cuda_fail(e, "tuning events");
+            }
+            int h = 0;
+            if (st == SE2_OK && cudaMemcpy(&h, b->one.err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && h == 0) {
+                b->one.tuned_ms = ms / reps;
+                b->one.on = b->one.tuned_ms < best_ms;
+            }
+            if (!b->one.on) {   // keep the measurement, drop the state
+                const double t = b->one.tuned_ms;
+                batch_one_free(b);
+                b->one.tuned_ms = t;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+se2_status se2_batch_plan_one_launch(se2_batch_plan_t b, int mode, int* current, double* tuned_ms) {
+    SE2_RANGE("se2_batch_plan_one_launch");
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    if (mode > 0) {
+        DeviceGuard guard(b->dev);
+        st = batch_one_init(b);
+        if (st != SE2_OK) return st;
+        b->one.on = true;
+    } else if (mode == 0) {
+        b->one.on = false;
+    }
+    if (current) *current = b->one.on ? 1 : 0;
+    if (tuned_ms) *tuned_ms = b->one.tuned_ms;
+    return SE2_OK;
+}
+
+se2_status se2_batch_plan_status(se2_batch_plan_t b, void* stream) {
+    SE2_RANGE("se2_batch_plan_status");
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    DeviceGuard guard(b->dev);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (b->one.err != nullptr) {
+        int h = 0;
+        e = cudaMemcpy(&h, b->one.err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+        if (h != 0) {
+            e = cudaMemset(b->one.err, 0, sizeof(int));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+            return fail(SE2_ERR_TIMEOUT, "a bounded wait of the one-launch batch kernel gave up (code %d)", h);
+        }
+    }
+    for (auto& c : b->cls) {
+        st = se2_plan_status(c.plan, stream);
+        if (st != SE2_OK) return st;
+    }
+    return SE2_OK;
+}
+
+se2_status se2_debug_batch_work_list(const se2_shape* shapes, const int* counts, int n_classes, int grid,
+                                     unsigned* units, long long* n_units, int* slots, int* lag) {
+    if (shapes == nullptr || counts == nullptr || n_units == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    std::vector<OneClass> ci;
+    std::vector<unsigned> list;
+    se2_status st = batch_work_list(shapes, counts, n_classes, grid, ci, list);
+    if (st != SE2_OK) return st;
+    if (units != nullptr) {
+        if (*n_units < (long long)list.size()) return fail(SE2_ERR_INVALID_ARG, "units holds %lld codes, %zu needed", *n_units, list.size());
+        std::copy(list.begin(), list.end(), units);
+    }
+    *n_units = (long long)list.size();
+    for (int c = 0; c < n_classes; ++c) {
+        if (slots) slots[c] = ci[c].D;
+        if (lag) lag[c] = ci[c].L;
+    }
+    return SE2_OK;
+}
+
+se2_status se2_debug_batch_wait_timeout(se2_batch_plan_t b, const void* f, const void* tables, void* out, void* stream) {
+    SE2_RANGE("se2_debug_batch_wait_timeout");
+    se2_status st = batch_check(b);
+    if (st != SE2_OK) return st;
+    if (f == nullptr || tables == nullptr || out == nullptr) return fail(SE2_ERR_INVALID_ARG, "NULL pointer argument");
+    DeviceGuard guard(b->dev);
+    st = batch_one_init(b);
+    if (st != SE2_OK) return st;
+    // every unit B waits for one more unit A than its problem has; 4096 polls end the wait
+    return batch_one_run(b, static_cast<const unsigned char*>(f), static_cast<const unsigned char*>(tables),
+                         static_cast<unsigned char*>(out), (cudaStream_t)stream, 1u, 4096);
 }
 
 se2_status se2_batch_plan_lanes(se2_batch_plan_t b, int lanes, int* current, int* lane_of_class, double* lane_ms) {
@@ -1932,7 +2204,7 @@ se2_status se2_batch_plan_config(se2_batch_plan_t b, int* n_classes, se2_shape* 
 
 unsigned long long se2_batch_plan_launches(se2_batch_plan_t b) {
     if (b == nullptr) return 0;
-    unsigned long long n = 0;
+    unsigned long long n = b->one.launches;
     for (const auto& c : b->cls) n += c.plan->launches;
     return n;
 }

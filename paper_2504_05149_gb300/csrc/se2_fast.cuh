@@ -308,8 +308,10 @@ template <int N, int M> __host__ __device__ constexpr int fast_yr() {
 // into row spectra, then the paired angular FFT of the slab columns; the DC
 // and Nyquist columns (both real along x) travel as one complex column.
 // ---------------------------------------------------------------------------
+// Body of unit A for block bx of one problem: fp its grid f, sp its scratch
+// rows (the kernel passes the problem's slot; the batch kernel a ring slot).
 template <int N, int M>
-__global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
+__device__ __forceinline__ void fwd_xt_body(const FArgs& a, int bx, const float* fp, float4* sp, float4* fsm) {
     constexpr int YR = fast_yr<N, M>(), MR = YR * M;   // slab rows: YR y rows of M theta rows
     constexpr int Q = N / 4, P = fpitch<N>(), TP4 = ftp4<N>();
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
@@ -319,12 +321,11 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
     constexpr size_t NN = (size_t)N * N;
     static_assert(Q % R1 == 0 && Q % R2 == 0, "pairing needs N/4 divisible by the radices");
     static_assert(M % 8 == 0 && MR <= kThreads && N % YR == 0, "slab of whole y rows");
-    extern __shared__ float4 fsm[];
     float4* S = fsm;
     float4* TW = fsm + fslab4<N, MR>();
     float2* TWM = reinterpret_cast<float2*>(TW + N);
-    const int tid = threadIdx.x, j0 = blockIdx.x * YR, b = blockIdx.y;
-    const float* fb = a.f + (size_t)b * NN * M + (size_t)j0 * N;
+    const int tid = threadIdx.x, j0 = bx * YR;
+    const float* fb = fp + (size_t)j0 * N;
     const int team = tid / TS, lane = tid % TS;
     for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
         const int q = q0 + team;            // slab rows 4q .. 4q + 3: y row q / JY, theta rows 4 (q % JY) ..
@@ -423,12 +424,18 @@ __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
     __syncthreads();
     {
         constexpr int E = Q + 1;
-        float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j0 * TP4;
+        float4* sb = sp + (size_t)j0 * TP4;
         for (int e = tid; e < MR * E; e += kThreads) {
             const int r = e / E, u = e - r * E;      // slab row r: theta row r % M of y row j0 + r / M
             __stcg(sb + (size_t)(r / M) * TP4 + (size_t)(r % M) * N * TP4 + u, S[frow(r, P) + u]);
         }
     }
+}
+
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
+    extern __shared__ float4 fsm[];
+    fwd_xt_body<N, M>(a, blockIdx.x, a.f + (size_t)blockIdx.y * N * N * M, a.s + (size_t)blockIdx.y * a.s_pstride, fsm);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,27 +455,28 @@ template <int N> __host__ __device__ constexpr int fast_xs() {
 constexpr int kLineThreads = 256;
 template <int N> __host__ __device__ constexpr int fast_lines() { return kLineThreads / team_size<N>(); }
 
+// Body of unit B for block bx of problem b: sp its scratch, tsep its
+// separable tables (FL_SEP).
 template <int N, int M, int MODE>
-__global__ void __launch_bounds__(kLineThreads, 2 * kThreads / kLineThreads) kf_lines(FArgs a) {
+__device__ __forceinline__ void lines_body(const FArgs& a, int bx, int b, float4* sp, const float2* tsep, float4* fsm) {
     constexpr bool SEP = MODE == FL_SEP;
     constexpr int Q = N / 4, P1 = Q + 1, CP = N / 2 + 1, TP4 = ftp4<N>();
     constexpr int TL = N / 2 + 1 + N + M;    // separable table length
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, RM = reg_count<N>();
     constexpr int LINES = fast_lines<N>(), XS = fast_xs<N>();
     static_assert(R1 % 2 == 0, "ky parity is the lane parity");
-    extern __shared__ float4 fsm[];
     float4* XB = fsm;
     float4* TWF = fsm + LINES * XS;     // forward (R1 x R2) and inverse (R2 x R1) tables
     float4* TWI = TWF + N;
     float2* TSEP = reinterpret_cast<float2*>(TWI + N);   // this problem's separable tables
     __shared__ double sh_scale;
     __shared__ double red[kLineThreads / 32];
-    const int tid = threadIdx.x, b = blockIdx.y;
+    const int tid = threadIdx.x;
     const int c = tid % LINES, t = tid / LINES;
-    const int pl = blockIdx.x * LINES + c;
+    const int pl = bx * LINES + c;
     const bool act = pl < M * P1;
     const int o = act ? pl / P1 : 0, u = act ? pl - (pl / P1) * P1 : 0;
-    float4* base = a.s + (size_t)b * a.s_pstride + (size_t)o * N * TP4 + u + (size_t)t * TP4;
+    float4* base = sp + (size_t)o * N * TP4 + u + (size_t)t * TP4;
     float4* xb = XB + c * XS;
     float2 re[RM], im[RM];
 #pragma unroll
@@ -494,7 +502,7 @@ __global__ void __launch_bounds__(kLineThreads, 2 * kThreads / kLineThreads) kf_
     fill_tw4<R1, R2>(TWF, a.twN);
     fill_tw4<R2, R1>(TWI, a.twN);
     if constexpr (SEP) {
-        copy_tw(TSEP, a.sep + (size_t)b * a.sep_pstride, TL);
+        copy_tw(TSEP, tsep, TL);
         if (tid == 0) sh_scale = 0.5 * a.inv_L;
     } else if (tid == 0) {
         double lsum = 0;
@@ -653,6 +661,13 @@ __global__ void __launch_bounds__(kLineThreads, 2 * kThreads / kLineThreads) kf_
     }
 }
 
+template <int N, int M, int MODE>
+__global__ void __launch_bounds__(kLineThreads, 2 * kThreads / kLineThreads) kf_lines(FArgs a) {
+    extern __shared__ float4 fsm[];
+    lines_body<N, M, MODE>(a, blockIdx.x, blockIdx.y, a.s + (size_t)blockIdx.y * a.s_pstride,
+                           MODE == FL_SEP ? a.sep + (size_t)blockIdx.y * a.sep_pstride : nullptr, fsm);
+}
+
 // Unit C is the last reader of a y row's scratch rows (m, j): once the block
 // holds them in shared memory they can be dropped from L2 without being
 // written back (discard.global.L2; the slot is rewritten by a later unit A
@@ -676,8 +691,9 @@ __device__ __forceinline__ void discard_scratch_rows(const float4* row0) {
 // columns recombined into one complex column first), then the inverse x FFTs
 // of row pairs (4q, 4q+1) and (4q+2, 4q+3) as the two halves.
 // ---------------------------------------------------------------------------
+// Body of unit C for block bx of one problem: sp its scratch, op its grid out.
 template <int N, int M>
-__global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
+__device__ __forceinline__ void inv_tx_body(const FArgs& a, int bx, const float4* sp, float* op, float4* fsm) {
     constexpr int YR = fast_yr<N, M>(), MR = YR * M;   // slab rows: YR y rows of M theta rows
     constexpr int Q = N / 4, P = fpitch<N>(), TP4 = ftp4<N>(), E = Q + 1;
     constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
@@ -686,15 +702,14 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
     constexpr size_t NN = (size_t)N * N;
     constexpr int LOADS = (MR * E + kThreads - 1) / kThreads;
     static_assert(M % 8 == 0 && MR <= kThreads && N % YR == 0, "slab of whole y rows");
-    extern __shared__ float4 fsm[];
     float4* S = fsm;
     float4* TW = fsm + fslab4<N, MR>();
     float2* TWM = reinterpret_cast<float2*>(TW + N);
-    const int tid = threadIdx.x, j0 = blockIdx.x * YR, b = blockIdx.y;
+    const int tid = threadIdx.x, j0 = bx * YR;
     {
         // batches of at most ~20 loads in flight per thread (registers)
         constexpr int CH = LOADS <= 20 ? LOADS : (LOADS + 1) / 2;
-        const float4* sb = a.s + (size_t)b * a.s_pstride + (size_t)j0 * TP4;
+        const float4* sb = sp + (size_t)j0 * TP4;
         for (int i0 = 0; i0 < LOADS; i0 += CH) {
             float4 v[CH];
 #pragma unroll
@@ -721,7 +736,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
     }
     __syncthreads();
     if (a.discard)
-        for (int yr = 0; yr < YR; ++yr) discard_scratch_rows<N, M>(a.s + (size_t)b * a.s_pstride + (size_t)(j0 + yr) * TP4);
+        for (int yr = 0; yr < YR; ++yr) discard_scratch_rows<N, M>(sp + (size_t)(j0 + yr) * TP4);
     if (tid < MR) {   // DC column + i * Nyquist column
         float4 e = S[frow(tid, P)];
         const float4 ny = S[frow(tid, P) + Q];
@@ -745,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
     // entry (m, 0) now holds (X_m[0], X_m[Q].re, X_m[N/2], X_m[Q].im) with
     // X_m[0], X_m[N/2] real
     const int team = tid / TS, lane = tid % TS;
-    float* ob = a.out + (size_t)b * NN * M + (size_t)j0 * N;
+    float* ob = op + (size_t)j0 * N;
     for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
         const int q = q0 + team;
         const bool act = q < JOBS;
@@ -802,6 +817,12 @@ __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
             }
         }
     }
+}
+
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
+    extern __shared__ float4 fsm[];
+    inv_tx_body<N, M>(a, blockIdx.x, a.s + (size_t)blockIdx.y * a.s_pstride, a.out + (size_t)blockIdx.y * N * N * M, fsm);
 }
 
 template <int N, int M> constexpr size_t fast_xt_smem() {

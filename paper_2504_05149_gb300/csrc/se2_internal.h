@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "se2_flow.cuh"
+#include "se2_batch_persist.cuh"
 
 namespace se2 {
 
@@ -80,6 +81,12 @@ struct TcArgs;
 using TcKernel = void (*)(TcArgs);
 bool tc_kernel(int M, int dir, int split, int fmt, TcKernel* out, size_t* smem);
 void tc_dft_matrix(int dir, int fmt, std::vector<unsigned char>& img);
+
+// The one-launch batch kernel (se2_batch.cu): its launch, and its unit
+// counts per problem for (N, M) (false where the kernel has no such class).
+void launch_batch_persist(int grid, cudaStream_t s, const BPArgs& a);
+cudaError_t batch_persist_prepare(int* blocks_per_sm);
+bool batch_persist_units(int N, int M, unsigned* nA, unsigned* nB, unsigned* nC, long long* s_pstride4);
 
 // Device allocations of the library (plans, grid plans): counted, and made
 // to fail on request (se2_debug_alloc_stats, se2_debug_fail_alloc).

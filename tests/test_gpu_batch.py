@@ -168,3 +168,83 @@ def _run_untuned(runner):
     from paper_2504_05149_gb300 import _check, _ptr, _stream
     _check(runner.lib.se2_batch_convolve_separable(runner._h, _ptr(runner.f_packed), _ptr(runner.tab_packed),
                                                    _ptr(runner.out_packed), _stream(runner.dev)))
+
+
+def _c4_sample(se2, n, tmp_path, seed_offset=0):
+    from paper_2504_05149_gb300.batch import BatchRunner
+    rng = synth.SplitMix64(synth.config_seed(4, seed_offset))
+    shapes, bumps, chains = [], [], []
+    for i in range(n):
+        N = [32, 64, 128, 256][rng.randint(0, 3)]
+        M = [16, 32, 64][rng.randint(0, 2)]
+        k = rng.randint(1, 16)
+        nb = rng.randint(3, 16)
+        shapes.append((N, M))
+        bumps.append(synth.draw_bumps(rng, nb))
+        chains.append([synth.draw_kernel(rng) for _ in range(k)])
+    runner = BatchRunner(shapes, cache_path=str(tmp_path / "tune.json"), autotune=False)
+    for i in range(n):
+        N, M = shapes[i]
+        runner.f_of(i).copy_(torch.from_numpy(synth.sample_bumps(N, M, bumps[i]).astype(np.float32)))
+        runner.set_chain(i, [(kp.sigma, kp.sigma_theta, kp.nu) for kp in chains[i]])
+    runner.build_tables()
+    return runner, shapes, bumps, chains
+
+
+def test_one_launch_matches_lanes_bit_for_bit_and_is_one_kernel(se2, tmp_path):
+    """The whole batch as one persistent kernel (work list over every class,
+    per-problem counters, scratch rings) gives the lane schedule's outputs
+    bit for bit, eagerly and from a CUDA graph, as one launch per run; two
+    problems are also checked against the FP64 oracle."""
+    runner, shapes, bumps, chains = _c4_sample(se2, 96, tmp_path)
+    assert len(runner.order) >= 10
+    runner.run()
+    runner.status()
+    torch.cuda.synchronize()
+    ref = runner.out_packed.cpu().clone()
+    assert runner.one_launch(True)[0]
+    for rep in range(2):
+        runner.out_packed.zero_()
+        n0 = runner.launches()
+        runner.run()
+        runner.status()
+        torch.cuda.synchronize()
+        assert runner.launches() - n0 == 1
+        assert torch.equal(runner.out_packed.cpu(), ref)
+    runner.capture()
+    runner.out_packed.zero_()
+    runner.replay()
+    torch.cuda.synchronize()
+    assert runner.launches_per_run() == 1
+    assert torch.equal(runner.out_packed.cpu(), ref)
+    for i in (0, len(shapes) - 1):
+        N, M = shapes[i]
+        F = synth.sample_bumps(N, M, bumps[i]).astype(np.float32).astype(np.float64)
+        C = _oracle_chain_coeffs(N, M, chains[i])
+        want = O.convolve_chain(F, None, coeffs=[C] if len(chains[i]) % 2 else [C, 1.0])
+        assert _rel(runner.out_of(i).double().cpu().numpy(), want) < 1e-5
+    assert not runner.one_launch(False)[0]
+
+
+def test_one_launch_bounded_wait_reports_timeout(se2, tmp_path):
+    """A wait of the one-launch kernel that can never be met gives up after a
+    bounded number of polls; se2_batch_plan_status returns SE2_ERR_TIMEOUT,
+    and the plan then runs normally."""
+    from paper_2504_05149_gb300 import _ptr, _stream, SE2Error
+    runner, _, _, _ = _c4_sample(se2, 12, tmp_path, seed_offset=7)
+    runner.run()
+    torch.cuda.synchronize()
+    ref = runner.out_packed.cpu().clone()
+    st = runner.lib.se2_debug_batch_wait_timeout(runner._h, _ptr(runner.f_packed), _ptr(runner.tab_packed),
+                                                 _ptr(runner.out_packed), _stream(runner.dev))
+    assert st == 0
+    with pytest.raises(SE2Error) as ei:
+        runner.status()
+    assert ei.value.status == 5          # SE2_ERR_TIMEOUT
+    runner.status()                      # cleared
+    runner.one_launch(True)
+    runner.out_packed.zero_()
+    runner.run()
+    runner.status()
+    torch.cuda.synchronize()
+    assert torch.equal(runner.out_packed.cpu(), ref)
