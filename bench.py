@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--N", type=int, default=N_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c2chain", "c2all", "c3", "c4", "c5", "e4"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c2sep", "c2chain", "c2all", "c3", "c4", "c5", "e4"],
                     help="c2: single convolutions at 256^2x64 (the headline); c2chain: 8-fold chains; "
                          "c2all: 8-fold chains emitting every intermediate (Algorithm 6); "
                          "c4: 4096 uneven problems with separable chains (CUDA graph); c5: forward+adjoint; "
@@ -275,7 +275,7 @@ def main():
         return
     if args.config != "c2":
         from functools import partial
-        {"c2chain": run_chain8, "c2all": partial(run_chain8, emit_all=True), "c3": run_precision,
+        {"c2sep": run_separable, "c2chain": run_chain8, "c2all": partial(run_chain8, emit_all=True), "c3": run_precision,
          "c4": run_batch, "c5": run_adjoint, "e4": run_grid_e4}[args.config](args)
         return
     import torch
@@ -712,6 +712,43 @@ def run_chain8(args, emit_all=False):
           {"workload": what, "grid": [M, N, N]},
           {"roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "traffic": None, "peak_source": src, "alg_bytes_per_chain": alg / B},
+           "cpu_baseline": cpu, "gpu_launches": launched, "clocks": clocks})
+
+
+def run_separable(args):
+    """The separable-kernel path at 256^2 x 64: each problem's chain of 8
+    radial kernels (Gaussian x wrapped normal) kept as three 1-D tables, so
+    the step moves only f in and out back (8 B per point)."""
+    import torch
+    import paper_2504_05149_gb300 as se2
+    import synth
+    N, M, B, k = args.N, args.M, args.batch, 8
+    dev = torch.device("cuda", 0)
+    plan = se2.Plan(N, M, batch=B)
+    params = torch.zeros((B, 16, 3), dtype=torch.float64)
+    Fs = []
+    for b in range(B):
+        prob = synth.make_problem(2, 700 + b, N, M, n_bumps=16, n_kernels=k)
+        Fs.append(torch.from_numpy(synth.sample_bumps(N, M, prob.bumps).astype(np.float32)))
+        for j, kp in enumerate(prob.kernels):
+            params[b, j] = torch.tensor([kp.sigma, kp.sigma_theta, kp.nu], dtype=torch.float64)
+    f = torch.stack(Fs).to(dev)
+    tab = se2.separable_tables(plan, params.to(dev), torch.full((B,), k, dtype=torch.int32, device=dev))
+    out = torch.empty_like(f)
+    fn = lambda: se2.convolve_separable(plan, f, tab, out)                        # noqa: E731
+    ms, clocks, launched = _clock_and_time(fn, args.steps, args.warmup, dev, plans=(plan,))
+    plan.status()
+    hbm, src = peaks()
+    L = N * N * M
+    alg = B * 8 * L
+    ach = alg / (ms / args.steps / 1e3) / 1e9
+    cpu = None if args.no_cpu_baseline else cpu_baseline(N, M, k=k, unit="conv/s")
+    _line("SE(2) convolutions/s at N=256, M=64 with an 8-fold separable kernel chain (FP32)",
+          B * args.steps / (ms / 1e3), "conv/s", args, ms,
+          {"workload": f"se2_convolve_separable, batch {B}, 8-kernel chain per problem as three 1-D tables",
+           "grid": [M, N, N], "l2": f"inputs larger than L2 ({alg / 1e6:.0f} MB moved per step)"},
+          {"roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "traffic": None, "peak_source": src, "alg_bytes_per_conv": 8 * L},
            "cpu_baseline": cpu, "gpu_launches": launched, "clocks": clocks})
 
 

@@ -70,23 +70,23 @@ __host__ __device__ constexpr unsigned unit_code(int cls, int stage, int u, int 
 // g: the problem's grid (f for unit A, out for unit C) or tables (unit B);
 // sp: its ring slot.
 template <int N, int M>
-__device__ __noinline__ void batch_unit_a(const BClass& c, int u, const float* g, float4* sp, float4* fsm) {
-    fwd_xt_body<N, M>(c.a, u, g, sp, fsm);
+__device__ __noinline__ void batch_unit_a(const BClass& c, int u, const float* g, float4* sp) {
+    fwd_xt_body<N, M, false>(c.a, u, 0, g, sp);
 }
 template <int N, int M>
-__device__ __noinline__ void batch_unit_b(const BClass& c, int u, int p, const float2* t, float4* sp, float4* fsm) {
-    lines_body<N, M, FL_SEP>(c.a, u, p, sp, t, fsm);
+__device__ __noinline__ void batch_unit_b(const BClass& c, int u, int p, const float2* t, float4* sp) {
+    lines_body<N, M, FL_SEP, false>(c.a, u, p, sp, t);
 }
 template <int N, int M>
-__device__ __noinline__ void batch_unit_c(const BClass& c, int u, float* g, const float4* sp, float4* fsm) {
-    inv_tx_body<N, M>(c.a, u, sp, g, fsm);
+__device__ __noinline__ void batch_unit_c(const BClass& c, int u, float* g, const float4* sp) {
+    inv_tx_body<N, M, false>(c.a, u, 0, sp, g);
 }
 template <int N, int M>
-__device__ __forceinline__ void batch_unit(const BPArgs& ba, const BClass& c, int stage, int u, int p, float4* fsm) {
+__device__ __forceinline__ void batch_unit(const BPArgs& ba, const BClass& c, int stage, int u, int p) {
     float4* sp = c.a.s + (size_t)(p % c.slots) * c.a.s_pstride;
-    if (stage == 0) batch_unit_a<N, M>(c, u, ba.f + c.goff + (size_t)p * c.grid, sp, fsm);
-    else if (stage == 1) batch_unit_b<N, M>(c, u, p, ba.tables + c.toff + (size_t)p * c.tabs, sp, fsm);
-    else batch_unit_c<N, M>(c, u, ba.out + c.goff + (size_t)p * c.grid, sp, fsm);
+    if (stage == 0) batch_unit_a<N, M>(c, u, ba.f + c.goff + (size_t)p * c.grid, sp);
+    else if (stage == 1) batch_unit_b<N, M>(c, u, p, ba.tables + c.toff + (size_t)p * c.tabs, sp);
+    else batch_unit_c<N, M>(c, u, ba.out + c.goff + (size_t)p * c.grid, sp);
 }
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -129,7 +129,6 @@ __device__ __forceinline__ const unsigned* unit_dep(const BPArgs& ba, unsigned c
 // compiles it (se2_batch.cu).
 template <int UNUSED = 0>
 __global__ void __launch_bounds__(kThreads, 2) kf_batch_persist(BPArgs ba) {
-    extern __shared__ float4 fsm[];
     __shared__ unsigned sh_code;
     __shared__ int sh_go;
     const int tid = threadIdx.x;
@@ -185,18 +184,18 @@ __global__ void __launch_bounds__(kThreads, 2) kf_batch_persist(BPArgs ba) {
         const int u = (int)((cd >> 16) & 0x3ffu), p = (int)(cd & 0xffffu);
         const BClass& c = ba.cls[ci];
         switch (c.kind) {
-            case 0: batch_unit<32, 16>(ba, c, stage, u, p, fsm); break;
-            case 1: batch_unit<32, 32>(ba, c, stage, u, p, fsm); break;
-            case 2: batch_unit<32, 64>(ba, c, stage, u, p, fsm); break;
-            case 3: batch_unit<64, 16>(ba, c, stage, u, p, fsm); break;
-            case 4: batch_unit<64, 32>(ba, c, stage, u, p, fsm); break;
-            case 5: batch_unit<64, 64>(ba, c, stage, u, p, fsm); break;
-            case 6: batch_unit<128, 16>(ba, c, stage, u, p, fsm); break;
-            case 7: batch_unit<128, 32>(ba, c, stage, u, p, fsm); break;
-            case 8: batch_unit<128, 64>(ba, c, stage, u, p, fsm); break;
-            case 9: batch_unit<256, 16>(ba, c, stage, u, p, fsm); break;
-            case 10: batch_unit<256, 32>(ba, c, stage, u, p, fsm); break;
-            default: batch_unit<256, 64>(ba, c, stage, u, p, fsm); break;
+            case 0: batch_unit<32, 16>(ba, c, stage, u, p); break;
+            case 1: batch_unit<32, 32>(ba, c, stage, u, p); break;
+            case 2: batch_unit<32, 64>(ba, c, stage, u, p); break;
+            case 3: batch_unit<64, 16>(ba, c, stage, u, p); break;
+            case 4: batch_unit<64, 32>(ba, c, stage, u, p); break;
+            case 5: batch_unit<64, 64>(ba, c, stage, u, p); break;
+            case 6: batch_unit<128, 16>(ba, c, stage, u, p); break;
+            case 7: batch_unit<128, 32>(ba, c, stage, u, p); break;
+            case 8: batch_unit<128, 64>(ba, c, stage, u, p); break;
+            case 9: batch_unit<256, 16>(ba, c, stage, u, p); break;
+            case 10: batch_unit<256, 32>(ba, c, stage, u, p); break;
+            default: batch_unit<256, 64>(ba, c, stage, u, p); break;
         }
         __syncthreads();   // every thread's stores are issued; the slab is free
         if (tid == kThreads - 32) {   // publish this unit

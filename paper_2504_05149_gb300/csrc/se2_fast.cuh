@@ -308,134 +308,25 @@ template <int N, int M> __host__ __device__ constexpr int fast_yr() {
 // into row spectra, then the paired angular FFT of the slab columns; the DC
 // and Nyquist columns (both real along x) travel as one complex column.
 // ---------------------------------------------------------------------------
-// Body of unit A for block bx of one problem: fp its grid f, sp its scratch
-// rows (the kernel passes the problem's slot; the batch kernel a ring slot).
-template <int N, int M>
-__device__ __forceinline__ void fwd_xt_body(const FArgs& a, int bx, const float* fp, float4* sp, float4* fsm) {
-    constexpr int YR = fast_yr<N, M>(), MR = YR * M;   // slab rows: YR y rows of M theta rows
-    constexpr int Q = N / 4, P = fpitch<N>(), TP4 = ftp4<N>();
-    constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
-    constexpr int TEAMS = kThreads / TS, JOBS = MR / 4, JY = M / 4;
-    constexpr int QK = Q / R1;            // register distance between x bins u and u + Q
-    constexpr int HK = N / (2 * R1);      // register of bin N/2 on lane 0
-    constexpr size_t NN = (size_t)N * N;
-    static_assert(Q % R1 == 0 && Q % R2 == 0, "pairing needs N/4 divisible by the radices");
-    static_assert(M % 8 == 0 && MR <= kThreads && N % YR == 0, "slab of whole y rows");
-    float4* S = fsm;
-    float4* TW = fsm + fslab4<N, MR>();
-    float2* TWM = reinterpret_cast<float2*>(TW + N);
-    const int tid = threadIdx.x, j0 = bx * YR;
-    const float* fb = fp + (size_t)j0 * N;
-    const int team = tid / TS, lane = tid % TS;
-    for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
-        const int q = q0 + team;            // slab rows 4q .. 4q + 3: y row q / JY, theta rows 4 (q % JY) ..
-        const bool act = q < JOBS;
-        float2 re[RM], im[RM];
-#pragma unroll
-        for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
-        if (act && lane < R2) {
-            const float* r0 = fb + (size_t)(q / JY) * N + (size_t)(4 * (q % JY)) * NN;
-#pragma unroll
-            for (int jj = 0; jj < R1; ++jj) {
-                const int x = lane + R2 * jj;
-                re[jj] = pf(__ldcs(r0 + x), __ldcs(r0 + 2 * NN + x));
-                im[jj] = pf(__ldcs(r0 + NN + x), __ldcs(r0 + 3 * NN + x));
-            }
-        }
-        if (q0 == 0) {   // the table fills overlap the first loads
-            fill_tw4<R1, R2>(TW, a.twN);
-            copy_tw(TWM, a.twM, M);
-            __syncthreads();
-        }
-        float4* xb = S + frow(4 * (act ? q : 0), P);
-        team_fft2<R1, R2, -1>(re, im, lane, act, xb, TW, SyncWarp());
-        // lane s < R1 holds Z[s + R1 k], k < R2 (half a: rows 4q/4q+1, b: 4q+2/4q+3)
-        if (act && lane < R1) {
-#pragma unroll
-            for (int k = 0; k < R2; ++k) xb[lane + R1 * k] = make_float4(re[k].x, re[k].y, im[k].x, im[k].y);
-            if (lane == 0) xb[N] = make_float4(re[0].x, re[0].y, im[0].x, im[0].y);   // Z[N] = Z[0]
-        }
-        __syncwarp();
-        float4 zm[HK + 1];
-        if (act && lane < R1) {
-            const float4* zb = xb + (N - lane);
-#pragma unroll
-            for (int k = 0; k < HK; ++k) zm[k] = zb[-R1 * k];
-            zm[HK] = lane == 0 ? xb[N / 2] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        __syncwarp();   // every read of Z is done before the rows take the spectra
-        if (act && lane < R1) {
-            // X0 = Z + conj Z[N-k], X1 = -i (Z - conj Z[N-k]): twice the spectra of the two rows
-            float4* row0 = S + frow(4 * q, P);
-            const float2 n0 = padd(re[HK], pf(zm[HK].x, zm[HK].y));   // Re X0[N/2] (lane 0)
-            const float2 n1 = padd(im[HK], pf(zm[HK].z, zm[HK].w));   // Re X1[N/2]
-#pragma unroll
-            for (int k = 0; k < QK; ++k) {
-                const int u = lane + R1 * k, h = k + QK;
-                const float2 lr = pf(zm[k].x, zm[k].y), li = pf(zm[k].z, zm[k].w);
-                const float2 hr = pf(zm[h].x, zm[h].y), hi = pf(zm[h].z, zm[h].w);
-                const float2 a0r = padd(re[k], lr), a0i = psub(im[k], li), a1r = padd(im[k], li), a1i = psub(lr, re[k]);
-                const float2 b0r = padd(re[h], hr), b0i = psub(im[h], hi), b1r = padd(im[h], hi), b1i = psub(hr, re[h]);
-                float4 e0 = make_float4(a0r.x, b0r.x, a0i.x, b0i.x);
-                float4 e1 = make_float4(a1r.x, b1r.x, a1i.x, b1i.x);
-                float4 e2 = make_float4(a0r.y, b0r.y, a0i.y, b0i.y);
-                float4 e3 = make_float4(a1r.y, b1r.y, a1i.y, b1i.y);
-                if (k == 0 && lane == 0) {   // X[0], X[N/2] are real: one complex DC entry
-                    e0.z = n0.x;
-                    e1.z = n1.x;
-                    e2.z = n0.y;
-                    e3.z = n1.y;
-                }
-                row0[u] = e0;
-                row0[P + u] = e1;
-                row0[2 * P + u] = e2;
-                row0[3 * P + u] = e3;
-            }
-        }
-    }
-    __syncthreads();
-    {
-        constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
-        const int tm = tid / TSM, lm = tid % TSM;
-        float2 wr[Fac<M>::R1], wi[Fac<M>::R1];
-        angular_twiddles<M>(TWM, lm, wr, wi);
-        for (int c0 = 0; c0 < YR * Q; c0 += TEAMSM) {
-            const int c = c0 + tm;          // column u = c % Q of y row c / Q (M % 8 == 0: frow adds)
-            const bool act = c < YR * Q;
-            column_fft2<M, P, -1>(S + frow((act ? c / Q : 0) * M, P), act ? c % Q : 0, lm, act, wr, wi, SyncWarp());
-        }
-    }
-    __syncthreads();
-    // split the DC column's transform Y = F(X[.,0] + i X[.,N/2]) into the two
-    // real columns' transforms: (Y + conj Y[-m]) / 2 and (Y - conj Y[-m]) / 2i
-    float4 yv = make_float4(0.f, 0.f, 0.f, 0.f), ym = yv;
-    if (tid < MR) {
-        yv = S[frow(tid, P)];
-        ym = S[frow((tid & ~(M - 1)) + ((M - tid) & (M - 1)), P)];
-    }
-    __syncthreads();
-    if (tid < MR) {
-        float4 e = yv;
-        e.x = 0.5f * (yv.x + ym.x);
-        e.z = 0.5f * (yv.z - ym.z);
-        S[frow(tid, P)] = e;
-        S[frow(tid, P) + Q] = make_float4(0.5f * (yv.z + ym.z), 0.f, 0.5f * (ym.x - yv.x), 0.f);
-    }
-    __syncthreads();
-    {
-        constexpr int E = Q + 1;
-        float4* sb = sp + (size_t)j0 * TP4;
-        for (int e = tid; e < MR * E; e += kThreads) {
-            const int r = e / E, u = e - r * E;      // slab row r: theta row r % M of y row j0 + r / M
-            __stcg(sb + (size_t)(r / M) * TP4 + (size_t)(r % M) * N * TP4 + u, S[frow(r, P) + u]);
-        }
-    }
+// Unit A's body (se2_unit_a.inc), for the batch kernel: K = false, block
+// bx_ of one problem whose grid f is fp and scratch slot sp.  With K = true
+// (the kernel below) the block and problem come from the grid and the
+// addresses from a, where they are used.
+template <int N, int M, bool K>
+__device__ __forceinline__ void fwd_xt_body(const FArgs& a, int bx_, int b_, const float* fp, float4* sp) {
+#include "se2_unit_a.inc"
 }
 
+// The kernel expands the same body with K = true: its own parameter a, and
+// block and problem from the grid (a function that takes a by reference
+// measured 2% more instructions).
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads, 2) kf_fwd_xt(FArgs a) {
-    extern __shared__ float4 fsm[];
-    fwd_xt_body<N, M>(a, blockIdx.x, a.f + (size_t)blockIdx.y * N * N * M, a.s + (size_t)blockIdx.y * a.s_pstride, fsm);
+    constexpr bool K = true;
+    const int bx_ = 0, b_ = 0;
+    const float* fp = nullptr;
+    float4* sp = nullptr;
+#include "se2_unit_a.inc"
 }
 
 // ---------------------------------------------------------------------------
@@ -455,217 +346,20 @@ template <int N> __host__ __device__ constexpr int fast_xs() {
 constexpr int kLineThreads = 256;
 template <int N> __host__ __device__ constexpr int fast_lines() { return kLineThreads / team_size<N>(); }
 
-// Body of unit B for block bx of problem b: sp its scratch, tsep its
-// separable tables (FL_SEP).
-template <int N, int M, int MODE>
-__device__ __forceinline__ void lines_body(const FArgs& a, int bx, int b, float4* sp, const float2* tsep, float4* fsm) {
-    constexpr bool SEP = MODE == FL_SEP;
-    constexpr int Q = N / 4, P1 = Q + 1, CP = N / 2 + 1, TP4 = ftp4<N>();
-    constexpr int TL = N / 2 + 1 + N + M;    // separable table length
-    constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, RM = reg_count<N>();
-    constexpr int LINES = fast_lines<N>(), XS = fast_xs<N>();
-    static_assert(R1 % 2 == 0, "ky parity is the lane parity");
-    float4* XB = fsm;
-    float4* TWF = fsm + LINES * XS;     // forward (R1 x R2) and inverse (R2 x R1) tables
-    float4* TWI = TWF + N;
-    float2* TSEP = reinterpret_cast<float2*>(TWI + N);   // this problem's separable tables
-    __shared__ double sh_scale;
-    __shared__ double red[kLineThreads / 32];
-    const int tid = threadIdx.x;
-    const int c = tid % LINES, t = tid / LINES;
-    const int pl = bx * LINES + c;
-    const bool act = pl < M * P1;
-    const int o = act ? pl / P1 : 0, u = act ? pl - (pl / P1) * P1 : 0;
-    float4* base = sp + (size_t)o * N * TP4 + u + (size_t)t * TP4;
-    float4* xb = XB + c * XS;
-    float2 re[RM], im[RM];
-#pragma unroll
-    for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
-    if constexpr (MODE == FL_ACC) {
-        if (act && t < R1) {
-#pragma unroll
-            for (int k = 0; k < R2; ++k) {
-                const float4 v = __ldcg(base + (size_t)(R1 * k) * TP4);
-                re[k] = pf(v.x, v.y);
-                im[k] = pf(v.z, v.w);
-            }
-        }
-    } else if (act && t < R2) {
-#pragma unroll
-        for (int jj = 0; jj < R1; ++jj) {
-            const float4 v = __ldcg(base + (size_t)(R2 * jj) * TP4);
-            re[jj] = pf(v.x, v.y);
-            im[jj] = pf(v.z, v.w);
-        }
-    }
-    // table fills and the scale overlap the loads
-    fill_tw4<R1, R2>(TWF, a.twN);
-    fill_tw4<R2, R1>(TWI, a.twN);
-    if constexpr (SEP) {
-        copy_tw(TSEP, tsep, TL);
-        if (tid == 0) sh_scale = 0.5 * a.inv_L;
-    } else if (tid == 0) {
-        double lsum = 0;
-        const int upto = MODE == FL_ACC ? a.p : a.k;
-        for (int i = 0; i < upto; ++i)
-            if (a.ls[i] != nullptr) lsum += a.ls[i][b * a.ls_pstride];
-        sh_scale = 0.5 * a.inv_L * exp(lsum);
-    }
-    __syncthreads();
-    if constexpr (MODE != FL_ACC) team_fft2<R1, R2, -1>(re, im, t, act, xb, TWF, SyncBlock());
-    // lane s < R1 holds ky = s + R1 k, k < R2
-    if constexpr (MODE == FL_FWD) {
-        if (act && t < R1) {
-#pragma unroll
-            for (int k = 0; k < R2; ++k)
-                __stcg(base + (size_t)(R1 * k) * TP4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y));
-        }
-        return;
-    }
-    if constexpr (MODE == FL_ADJ) {
-        // parameter partials sum_k m_k W Re(dC_i conj(G) F) over this lane's bins
-        // (m_k = 1 at x bins 0 and N/2, 2 elsewhere; both spectra are doubled)
-        float2 acc[kMaxParams];
-#pragma unroll
-        for (int i = 0; i < kMaxParams; ++i) acc[i] = pf(0.f, 0.f);
-        if (a.n_params > 0 && act && t < R1) {
-            const bool hasb = u < Q;
-            const int kxa = hasb ? u : N / 2;
-            const float sg = (a.wsign && ((u + t) & 1)) ? -1.f : 1.f;
-            const float2 mw = pf(sg * ((u == 0 || u == Q) ? 1.f : 2.f), sg * 2.f);
-            // F at this lane's bins, staged in the (now idle) exchange area
-            const float4* fb2 = a.s2 + (size_t)b * a.s_pstride + (size_t)o * N * TP4 + u + (size_t)t * TP4;
-#pragma unroll
-            for (int k = 0; k < R2; ++k)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                             :: "r"((unsigned)__cvta_generic_to_shared(xb + t + R1 * k)), "l"(fb2 + (size_t)(R1 * k) * TP4)
-                             : "memory");
-            asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
-            const size_t coff = (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa + (size_t)t * CP;
-#pragma unroll
-            for (int i = 0; i < kMaxParams; ++i) {
-                if (i < a.n_params) {
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        constexpr int KH = R2 / 4;
-                        float2 da[KH], dq[KH];
-#pragma unroll
-                        for (int kk = 0; kk < KH; ++kk) {
-                            const float2* db = a.dC[i] + coff + (size_t)(R1 * (h * KH + kk)) * CP;
-                            da[kk] = __ldcs(db);
-                            dq[kk] = hasb ? __ldcs(db + Q) : pf(0.f, 0.f);
-                        }
-#pragma unroll
-                        for (int kk = 0; kk < KH; ++kk) {
-                            const int k = h * KH + kk;
-                            const float4 v = xb[t + R1 * k];
-                            const float2 fr = pf(v.x, v.y), fi = pf(v.z, v.w);
-                            const float2 pr = pfma(re[k], fr, pmul(im[k], fi));      // conj(G) F
-                            const float2 pi = pfma(re[k], fi, pneg(pmul(im[k], fr)));
-                            const float2 vv = pfma(pf(da[kk].x, dq[kk].x), pr, pneg(pmul(pf(da[kk].y, dq[kk].y), pi)));
-                            acc[i] = pfma(vv, mw, acc[i]);
-                        }
-                        asm volatile("" ::: "memory");   // bounds the loads in flight
-                    }
-                }
-            }
-        }
-        __syncthreads();   // the exchange area is free again before the inverse FFT
-#pragma unroll
-        for (int i = 0; i < kMaxParams; ++i) {
-            if (i < a.n_params) {   // uniform over the block
-                double v = (double)acc[i].x + (double)acc[i].y;
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if ((tid & 31) == 0) red[tid >> 5] = v;
-                __syncthreads();
-                if (tid == 0) {
-                    double tsum = 0;
-                    for (int w = 0; w < kLineThreads / 32; ++w) tsum += red[w];
-                    atomicAdd(a.grad_params + i, 0.25 * a.inv_L * tsum);
-                }
-                __syncthreads();
-            }
-        }
-        if (!a.want_grad) return;
-    }
-    if (act && t < R1) {
-        const bool hasb = u < Q;
-        const int kxa = hasb ? u : N / 2;
-        const float sc = (float)sh_scale;
-        const int kpar = MODE == FL_ACC ? a.p : a.k;
-        const bool neg = a.wsign && (SEP || (kpar & 1)) && ((u + t) & 1);   // W^k at (kx, ky), both halves alike
-        const float2 s2 = bc2(neg ? -sc : sc);
-        if constexpr (SEP) {
-            // C = (tx[kx] tt[m]) ty[ky]: the x and theta factors once per lane
-            const float2 ct = TSEP[N / 2 + 1 + N + o];
-            const float2 xa = TSEP[kxa], xq = hasb ? TSEP[kxa + Q] : pf(0.f, 0.f);
-            const float2 xr = pf(xa.x * ct.x - xa.y * ct.y, xq.x * ct.x - xq.y * ct.y);
-            const float2 xi = pf(xa.x * ct.y + xa.y * ct.x, xq.x * ct.y + xq.y * ct.x);
-#pragma unroll
-            for (int k = 0; k < R2; ++k) {
-                const float2 ty = TSEP[N / 2 + 1 + t + R1 * k];
-                const float2 tyr = bc2(ty.x), tyi = bc2(ty.y);
-                const float2 cr = pfma(xr, tyr, pneg(pmul(xi, tyi))), ci = pfma(xr, tyi, pmul(xi, tyr));
-                const float2 r = pfma(re[k], cr, pneg(pmul(im[k], ci)));
-                im[k] = pfma(re[k], ci, pmul(im[k], cr));
-                re[k] = r;
-            }
-        }
-        // coefficient loads in chunks of CK bins (the adjoint keeps fewer in flight)
-        constexpr int CK = MODE == FL_ADJ ? R2 / 2 : R2;
-        const int i0 = MODE == FL_ACC ? a.p - 1 : 0, i1 = SEP ? 0 : (MODE == FL_ACC ? a.p : a.k);
-        const bool ym = a.ymirror != 0;
-        for (int i = i0; i < i1; ++i) {
-            const float2* cb = a.C[i] + (size_t)b * a.c_pstride + (size_t)o * N * CP + kxa;
-#pragma unroll
-            for (int k0 = 0; k0 < R2; k0 += CK) {
-                float2 ca[CK], cq[CK];
-#pragma unroll
-                for (int kk = 0; kk < CK; ++kk) {
-                    // row ky of this lane's bin, folded to N - ky for mirror-symmetric kernels
-                    int row = t + R1 * (k0 + kk);
-                    if (ym && row > N / 2) row = N - row;
-                    ca[kk] = __ldcs(cb + (size_t)row * CP);
-                    cq[kk] = hasb ? __ldcs(cb + (size_t)row * CP + Q) : pf(0.f, 0.f);
-                }
-#pragma unroll
-                for (int kk = 0; kk < CK; ++kk) {
-                    const int k = k0 + kk;
-                    const float2 cr = pf(ca[kk].x, cq[kk].x);
-                    // the adjoint multiplies by conj(C)
-                    const float2 ci = MODE == FL_ADJ ? pf(-ca[kk].y, -cq[kk].y) : pf(ca[kk].y, cq[kk].y);
-                    const float2 r = pfma(re[k], cr, pneg(pmul(im[k], ci)));
-                    im[k] = pfma(re[k], ci, pmul(im[k], cr));
-                    re[k] = r;
-                }
-                if (CK < R2) asm volatile("" ::: "memory");
-            }
-        }
-        if constexpr (MODE == FL_ACC) {   // keep the running product R_p (unscaled, no W)
-#pragma unroll
-            for (int k = 0; k < R2; ++k)
-                __stcg(base + (size_t)(R1 * k) * TP4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y));
-        }
-#pragma unroll
-        for (int k = 0; k < R2; ++k) {
-            re[k] = pmul(re[k], s2);
-            im[k] = pmul(im[k], s2);
-        }
-    }
-    team_fft2<R2, R1, +1>(re, im, t, act, xb, TWI, SyncBlock());
-    if (act && t < R2) {
-        float4* dst = MODE == FL_ACC ? a.sout + (base - a.s) : base;
-#pragma unroll
-        for (int k = 0; k < R1; ++k)
-            __stcg(dst + (size_t)(R2 * k) * TP4, make_float4(re[k].x, re[k].y, im[k].x, im[k].y));
-    }
+// Unit B's body (se2_unit_b.inc), for the batch kernel: K = false, block
+// bx_ of problem b_ with scratch slot sp and separable tables tsep (FL_SEP).
+template <int N, int M, int MODE, bool K>
+__device__ __forceinline__ void lines_body(const FArgs& a, int bx_, int b_, float4* sp, const float2* tsep) {
+#include "se2_unit_b.inc"
 }
 
 template <int N, int M, int MODE>
 __global__ void __launch_bounds__(kLineThreads, 2 * kThreads / kLineThreads) kf_lines(FArgs a) {
-    extern __shared__ float4 fsm[];
-    lines_body<N, M, MODE>(a, blockIdx.x, blockIdx.y, a.s + (size_t)blockIdx.y * a.s_pstride,
-                           MODE == FL_SEP ? a.sep + (size_t)blockIdx.y * a.sep_pstride : nullptr, fsm);
+    constexpr bool K = true;
+    const int bx_ = 0, b_ = 0;
+    float4* sp = nullptr;
+    const float2* tsep = nullptr;
+#include "se2_unit_b.inc"
 }
 
 // Unit C is the last reader of a y row's scratch rows (m, j): once the block
@@ -691,138 +385,20 @@ __device__ __forceinline__ void discard_scratch_rows(const float4* row0) {
 // columns recombined into one complex column first), then the inverse x FFTs
 // of row pairs (4q, 4q+1) and (4q+2, 4q+3) as the two halves.
 // ---------------------------------------------------------------------------
-// Body of unit C for block bx of one problem: sp its scratch, op its grid out.
-template <int N, int M>
-__device__ __forceinline__ void inv_tx_body(const FArgs& a, int bx, const float4* sp, float* op, float4* fsm) {
-    constexpr int YR = fast_yr<N, M>(), MR = YR * M;   // slab rows: YR y rows of M theta rows
-    constexpr int Q = N / 4, P = fpitch<N>(), TP4 = ftp4<N>(), E = Q + 1;
-    constexpr int R1 = Fac<N>::R1, R2 = Fac<N>::R2, TS = team_size<N>(), RM = reg_count<N>();
-    constexpr int TEAMS = kThreads / TS, JOBS = MR / 4, JY = M / 4;
-    constexpr int QJ = Q / R2, HJ = N / (2 * R2);
-    constexpr size_t NN = (size_t)N * N;
-    constexpr int LOADS = (MR * E + kThreads - 1) / kThreads;
-    static_assert(M % 8 == 0 && MR <= kThreads && N % YR == 0, "slab of whole y rows");
-    float4* S = fsm;
-    float4* TW = fsm + fslab4<N, MR>();
-    float2* TWM = reinterpret_cast<float2*>(TW + N);
-    const int tid = threadIdx.x, j0 = bx * YR;
-    {
-        // batches of at most ~20 loads in flight per thread (registers)
-        constexpr int CH = LOADS <= 20 ? LOADS : (LOADS + 1) / 2;
-        const float4* sb = sp + (size_t)j0 * TP4;
-        for (int i0 = 0; i0 < LOADS; i0 += CH) {
-            float4 v[CH];
-#pragma unroll
-            for (int i = 0; i < CH; ++i) {
-                const int e = tid + kThreads * (i0 + i);
-                if (i0 + i < LOADS && e < MR * E) {
-                    const int r = e / E, u = e - r * E;
-                    v[i] = __ldcg(sb + (size_t)(r / M) * TP4 + (size_t)(r % M) * N * TP4 + u);
-                }
-            }
-            if (i0 == 0) {   // the table fills overlap the loads
-                fill_tw4<R1, R2>(TW, a.twN);
-                copy_tw(TWM, a.twM, M);
-            }
-#pragma unroll
-            for (int i = 0; i < CH; ++i) {
-                const int e = tid + kThreads * (i0 + i);
-                if (i0 + i < LOADS && e < MR * E) {
-                    const int r = e / E, u = e - r * E;
-                    S[frow(r, P) + u] = v[i];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (a.discard)
-        for (int yr = 0; yr < YR; ++yr) discard_scratch_rows<N, M>(sp + (size_t)(j0 + yr) * TP4);
-    if (tid < MR) {   // DC column + i * Nyquist column
-        float4 e = S[frow(tid, P)];
-        const float4 ny = S[frow(tid, P) + Q];
-        e.x -= ny.z;
-        e.z += ny.x;
-        S[frow(tid, P)] = e;
-    }
-    __syncthreads();
-    {
-        constexpr int TSM = team_size<M>(), TEAMSM = kThreads / TSM;
-        const int tm = tid / TSM, lm = tid % TSM;
-        float2 wr[Fac<M>::R1], wi[Fac<M>::R1];
-        angular_twiddles<M>(TWM, lm, wr, wi);
-        for (int c0 = 0; c0 < YR * Q; c0 += TEAMSM) {
-            const int c = c0 + tm;          // column u = c % Q of y row c / Q
-            const bool act = c < YR * Q;
-            column_fft2<M, P, +1>(S + frow((act ? c / Q : 0) * M, P), act ? c % Q : 0, lm, act, wr, wi, SyncWarp());
-        }
-    }
-    __syncthreads();
-    // entry (m, 0) now holds (X_m[0], X_m[Q].re, X_m[N/2], X_m[Q].im) with
-    // X_m[0], X_m[N/2] real
-    const int team = tid / TS, lane = tid % TS;
-    float* ob = op + (size_t)j0 * N;
-    for (int q0 = 0; q0 < JOBS; q0 += TEAMS) {
-        const int q = q0 + team;
-        const bool act = q < JOBS;
-        float2 re[RM], im[RM];
-#pragma unroll
-        for (int i = 0; i < RM; ++i) { re[i] = pf(0.f, 0.f); im[i] = pf(0.f, 0.f); }
-        const float4* row0 = S + frow(4 * (act ? q : 0), P);
-        if (act && lane < R2) {
-            // Z_a[kk] = X_{4q}[kk] + i X_{4q+1}[kk], Z_b likewise with rows 4q+2, 4q+3,
-            // kk = lane + R2 jj; bins above N/2 are conjugates of N - kk
-#pragma unroll
-            for (int jj = 0; jj < QJ; ++jj) {
-                const int e = lane + R2 * jj;
-                const float4 v0 = row0[e], v1 = row0[P + e], v2 = row0[2 * P + e], v3 = row0[3 * P + e];
-                const bool dc = (jj == 0) && lane == 0;
-                // kk = e (low half; the DC entry's imaginary slot holds X[N/2])
-                const float i0 = dc ? 0.f : v0.z, i1 = dc ? 0.f : v1.z, i2 = dc ? 0.f : v2.z, i3 = dc ? 0.f : v3.z;
-                re[jj] = pf(v0.x - i1, v2.x - i3);
-                im[jj] = pf(i0 + v1.x, i2 + v3.x);
-                // kk = e + Q (high half)
-                re[jj + QJ] = pf(v0.y - v1.w, v2.y - v3.w);
-                im[jj + QJ] = pf(v0.w + v1.y, v2.w + v3.y);
-            }
-#pragma unroll
-            for (int jj = HJ; jj < HJ + QJ; ++jj) {
-                // kk = lane + R2 jj in [N/2, N/2 + Q): X[kk] = conj X[N - kk], N - kk - Q < Q
-                const bool ny = (jj == HJ) && lane == 0;
-                const int e = ny ? 0 : N - lane - R2 * jj - Q;
-                const float4 v0 = row0[e], v1 = row0[P + e], v2 = row0[2 * P + e], v3 = row0[3 * P + e];
-                // kk: high half of entry e, conjugated; the Nyquist bin is the DC entry's z
-                const float r0 = ny ? v0.z : v0.y, r1 = ny ? v1.z : v1.y, r2 = ny ? v2.z : v2.y, r3 = ny ? v3.z : v3.y;
-                const float n0 = ny ? 0.f : -v0.w, n1 = ny ? 0.f : -v1.w, n2 = ny ? 0.f : -v2.w, n3 = ny ? 0.f : -v3.w;
-                re[jj] = pf(r0 - n1, r2 - n3);
-                im[jj] = pf(n0 + r1, n2 + r3);
-                // kk + Q: low half of entry e, conjugated (Nyquist lane: X[Q] = high half of entry 0)
-                const float s0 = ny ? v0.y : v0.x, s1 = ny ? v1.y : v1.x, s2 = ny ? v2.y : v2.x, s3 = ny ? v3.y : v3.x;
-                const float m0 = ny ? -v0.w : -v0.z, m1 = ny ? -v1.w : -v1.z, m2 = ny ? -v2.w : -v2.z, m3 = ny ? -v3.w : -v3.z;
-                re[jj + QJ] = pf(s0 - m1, s2 - m3);
-                im[jj + QJ] = pf(m0 + s1, m2 + s3);
-            }
-        }
-        __syncwarp();   // every read of the team's rows is done before the exchange reuses them
-        float4* xb = S + frow(4 * (act ? q : 0), P);
-        team_fft2<R1, R2, +1>(re, im, lane, act, xb, TW, SyncWarp());
-        if (act && lane < R1) {
-            float* o0 = ob + (size_t)(q / JY) * N + (size_t)(4 * (q % JY)) * NN;
-#pragma unroll
-            for (int k = 0; k < R2; ++k) {
-                const int x = lane + R1 * k;
-                __stcs(o0 + x, re[k].x);
-                __stcs(o0 + NN + x, im[k].x);
-                __stcs(o0 + 2 * NN + x, re[k].y);
-                __stcs(o0 + 3 * NN + x, im[k].y);
-            }
-        }
-    }
+// Unit C's body (se2_unit_c.inc), for the batch kernel: K = false, block
+// bx_ of one problem with scratch slot sp and grid out op.
+template <int N, int M, bool K>
+__device__ __forceinline__ void inv_tx_body(const FArgs& a, int bx_, int b_, const float4* sp, float* op) {
+#include "se2_unit_c.inc"
 }
 
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads, 2) kf_inv_tx(FArgs a) {
-    extern __shared__ float4 fsm[];
-    inv_tx_body<N, M>(a, blockIdx.x, a.s + (size_t)blockIdx.y * a.s_pstride, a.out + (size_t)blockIdx.y * N * N * M, fsm);
+    constexpr bool K = true;
+    const int bx_ = 0, b_ = 0;
+    const float4* sp = nullptr;
+    float* op = nullptr;
+#include "se2_unit_c.inc"
 }
 
 template <int N, int M> constexpr size_t fast_xt_smem() {
