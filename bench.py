@@ -529,18 +529,19 @@ def mixed_vs_fp32(se2, torch, dev, stream, N, M, B, F, P, f, f32_value, f32_out0
 
 # DRAM bytes of the FP32 paired kernels at 256^2 x 64 per launch (2 problems):
 # dram__bytes_read.sum + dram__bytes_write.sum of kf_fwd_xt, kf_lines and
-# kf_inv_tx from one `ncu --set full` capture (profiles/kf_units_*).  ncu
-# flushes the caches before each kernel, so the scratch that the live run keeps
-# in L2 is counted as DRAM traffic: an upper bound.  None where the kernel has
-# changed since the capture.
-NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.602304 + 0.463360) * 1e6, (71.602688 + 1.382656) * 1e6,
-                                             (37.777408 + 1.117184) * 1e6)}
+# kf_inv_tx, means over 8 launches of one one-pass ncu capture of the current
+# kernels (profiles/kf_units_f32_256x256x64_b16_dram_cold_warm.md).  ncu
+# flushes the caches before each kernel, so the scratch that the live run
+# keeps in L2 is counted as DRAM traffic: an upper bound.  None where the
+# kernel has changed since the capture.
+NCU_TRAFFIC_PER_LAUNCH = {(256, 64, "f32"): ((33.603232 + 0.051648) * 1e6, (71.606432 + 0.042944) * 1e6,
+                                             (37.783840 + 0.013664) * 1e6)}
 NCU_TRAFFIC_PER_CONV = {k: (None if any(x is None for x in v) else sum(v) / 2) for k, v in NCU_TRAFFIC_PER_LAUNCH.items()}
-# The same counters with the cache left warm (`ncu --cache-control none`, one
-# pass, launches 49-72 of a batch-16 bench run; profiles/kf_units_*_warm_*):
-# the scratch stays in L2 as in the live run, so this is the live-like figure.
-NCU_TRAFFIC_WARM_PER_LAUNCH = {(256, 64, "f32"): ((33.787168 + 27.261472) * 1e6, (36.289920 + 6.271296) * 1e6,
-                                                  (0.024800 + 30.836576) * 1e6)}
+# The same counters with the cache left warm (`ncu --cache-control none`, same
+# capture): the scratch stays in L2 as in the live run, so this is the
+# live-like figure.
+NCU_TRAFFIC_WARM_PER_LAUNCH = {(256, 64, "f32"): ((33.772224 + 27.140896) * 1e6, (36.260768 + 6.264480) * 1e6,
+                                                  (0.023904 + 30.791264) * 1e6)}
 UNIT_NAMES = ("kf_fwd_xt", "kf_lines", "kf_inv_tx")
 
 
@@ -612,11 +613,11 @@ def kernel_roofline(unit_stats, N, M, B, steps, hbm, src, step_achieved, step_by
     return {"bound": "hbm", "achieved": dom["achieved"], "peak": hbm, "unit": "GB/s", "frac": dom["frac"],
             "peak_source": src, "kernel": dom["kernel"], "avg_launch_ms": dom["avg_launch_ms"],
             "alg_bytes_per_launch": dom["alg_bytes_per_launch"], "traffic": traffic,
-            "traffic_source": "ncu --set full, caches flushed (upper bound), per launch of 2 problems; "
-                              "profiles/kf_units_f32_256x256x64_b4_full.md",
+            "traffic_source": "ncu one-pass dram counters, caches flushed (upper bound), per launch of 2 problems; "
+                              "profiles/kf_units_f32_256x256x64_b16_dram_cold_warm.md",
             "traffic_warm_cache": warm,
             "traffic_warm_cache_source": "ncu --cache-control none (L2 as the previous launch left it), per launch of "
-                                         "2 problems; profiles/kf_units_f32_256x256x64_b16_warm_l2_traffic.md",
+                                         "2 problems; profiles/kf_units_f32_256x256x64_b16_dram_cold_warm.md",
             "timing": "CUDA events around each launch, serialised pass (one stream, 2 problems per launch, "
                       "no other kernel running); the pipelined step is roofline.step",
             "kernels": kern, "kernels_overlapped": over, "step": step}
@@ -628,11 +629,11 @@ def traffic_fields(N, M, precision):
         return {"traffic": None}
     tw = NCU_TRAFFIC_WARM_PER_LAUNCH.get((N, M, precision))
     return {"traffic": t, "traffic_unit": "bytes per convolution",
-            "traffic_source": "ncu --set full, caches flushed per kernel (upper bound); "
-                              "profiles/kf_units_f32_256x256x64_b4_full.md",
+            "traffic_source": "ncu one-pass dram counters, caches flushed per kernel (upper bound); "
+                              "profiles/kf_units_f32_256x256x64_b16_dram_cold_warm.md",
             "traffic_warm_cache": None if tw is None else sum(tw) / 2,
             "traffic_warm_cache_source": "ncu --cache-control none; "
-                                         "profiles/kf_units_f32_256x256x64_b16_warm_l2_traffic.md"}
+                                         "profiles/kf_units_f32_256x256x64_b16_dram_cold_warm.md"}
 
 
 def _clock_and_time(fn, steps, warmup, dev, settle=0.6, plans=()):

@@ -16,8 +16,8 @@ def test_kernel_roofline_picks_the_dominant_unit_and_counts_algorithmic_bytes():
     assert r["avg_launch_ms"] == pytest.approx(0.032)
     assert r["achieved"] == pytest.approx(r["alg_bytes_per_launch"] / 0.032e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6780.7)
-    assert r["traffic"] == pytest.approx((71.602688 + 1.382656) * 1e6)
-    assert r["traffic_warm_cache"] == pytest.approx((36.289920 + 6.271296) * 1e6)
+    assert r["traffic"] == pytest.approx((71.606432 + 0.042944) * 1e6)
+    assert r["traffic_warm_cache"] == pytest.approx((36.260768 + 6.264480) * 1e6)
     # warm-cache traffic of the whole step: 1.33x the algorithmic 12 bytes per point
     assert r["step"]["traffic_warm_cache"] / (12 * L) == pytest.approx(1.33, abs=0.01)
     assert [k["kernel"] for k in r["kernels"]] == ["kf_fwd_xt", "kf_lines", "kf_inv_tx"]
@@ -54,7 +54,7 @@ def test_kernel_roofline_reports_serialised_kernels_and_the_overlapped_pass():
     over = ([(0.030 * 640, 640), (0.032 * 640, 640), (0.027 * 640, 640), (0.0, 0)], 20)
     r = bench.kernel_roofline(serial, N, M, B, 10, 6780.7, "measured", 2100.0, B * 12 * L, "f32", overlapped=over)
     assert r["kernel"] == "kf_fwd_xt"
-    assert r["traffic"] == pytest.approx((33.602304 + 0.463360) * 1e6)
+    assert r["traffic"] == pytest.approx((33.603232 + 0.051648) * 1e6)
     assert r["avg_launch_ms"] == pytest.approx(0.020)
     assert [k["kernel"] for k in r["kernels_overlapped"]] == ["kf_fwd_xt", "kf_lines", "kf_inv_tx"]
     assert r["kernels_overlapped"][1]["avg_launch_ms"] == pytest.approx(0.032)
