@@ -2073,6 +2073,9 @@ se2_status se2_batch_tune(se2_batch_plan_t b, const void* f, const void* tables,
         b->one.on = false;
         if (st == SE2_OK && batch_one_init(b) == SE2_OK) {
             st = batch_one_run(b, fb, tb, ob, s, 0, kSpinLimit);   // warm-up
+            // its first launch may also set up the kernel's local memory
+            // (about 4 KB of stack per thread): keep that out of the timing
+            if (st == SE2_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "warm-up");
             cudaEventRecord(e0, s);
             for (int i = 0; i < reps && st == SE2_OK; ++i) st = batch_one_run(b, fb, tb, ob, s, 0, kSpinLimit);
             cudaEventRecord(e1, s);
