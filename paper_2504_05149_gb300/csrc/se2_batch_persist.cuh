@@ -95,8 +95,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     return v;
 }
 
-// A template so that only the translation unit that takes its address
-// compiles it (se2_batch.cu).
 // Dependency of a unit: the counter it waits on and the count it needs
 // (nullptr: none).
 __device__ __forceinline__ const unsigned* unit_dep(const BPArgs& ba, unsigned code, unsigned* target) {
